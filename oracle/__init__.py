@@ -70,7 +70,7 @@ def lib():
             dp = ctypes.c_void_p
             L.or_dim.argtypes = [P]; L.or_dim.restype = ctypes.c_int
             L.or_theta_from_u.argtypes = [P, dp, dp]; L.or_theta_from_u.restype = None
-            L.or_pn_phi.argtypes = [ctypes.c_double] * 4 + [dp]; L.or_pn_phi.restype = None
+            L.or_pn_phi.argtypes = [ctypes.c_double] * 5 + [dp]; L.or_pn_phi.restype = None
             L.or_fisco.argtypes = [dp]; L.or_fisco.restype = ctypes.c_double
             L.or_phase.argtypes = [dp, ctypes.c_double]; L.or_phase.restype = ctypes.c_double
             L.or_amplitude.argtypes = [dp, ctypes.c_double]; L.or_amplitude.restype = ctypes.c_double
@@ -206,9 +206,9 @@ class Problem:
 
 
 # -- single-quantity helpers (used by the pins) ------------------------------
-def pn_phi(eta, chi1, chi2, v) -> np.ndarray:
+def pn_phi(eta, delta, chi1, chi2, v) -> np.ndarray:
     out = np.zeros(8)
-    lib().or_pn_phi(float(eta), float(chi1), float(chi2), float(v), _ptr(out))
+    lib().or_pn_phi(float(eta), float(delta), float(chi1), float(chi2), float(v), _ptr(out))
     return out
 
 

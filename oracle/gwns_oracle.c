@@ -102,13 +102,12 @@ void or_theta_from_u(const or_problem *pb, const double *u, double *theta)
 
 /* TaylorF2 phasing coefficients phi_k(v), k = 0..7, such that
  *   Psi(f) = 2 pi f t_c - phi_c - pi/4 + 3/(128 eta v^5) sum_k phi_k v^k,
- * with v = (pi M f)^(1/3). The log(v) dependence of the 2.5PN and 3PN terms is
+ * with v = (pi M f)^(1/3) and delta = (m1 - m2)/M. The log(v) dependence of the 2.5PN and 3PN terms is
  * folded into phi_5 and phi_6. Spin terms: beta (1.5PN spin-orbit), sigma
  * (2PN spin-spin, aligned), gamma (2.5PN spin-orbit). */
-void or_pn_phi(double eta, double chi1, double chi2, double v, double phi[8])
+void or_pn_phi(double eta, double delta, double chi1, double chi2, double v, double phi[8])
 {
     double pi = OR_PI;
-    double delta = sqrt(1.0 - 4.0 * eta);   /* (m1 - m2)/M with m1 >= m2 */
     double chis = 0.5 * (chi1 + chi2), chia = 0.5 * (chi1 - chi2);
     double beta = (113.0 / 12.0) * (chis + delta * chia - (76.0 / 113.0) * eta * chis);
     double sigma = (79.0 / 8.0) * eta * chi1 * chi2;
@@ -131,7 +130,7 @@ void or_pn_phi(double eta, double chi1, double chi2, double v, double phi[8])
 static void source_masses(const double *th, double *eta, double *mtot_s, double *mc_s)
 {
     double q = th[P_Q];
-    *eta = q / ((1.0 + q) * (1.0 + q));
+    *eta = q / ((1.0 + q) * (1.0 + q));     /* m1 m2 / M^2 with q = m2/m1 */
     *mc_s = th[P_MC] * OR_TSUN;
     *mtot_s = *mc_s * pow(*eta, -0.6);        /* M = Mc eta^(-3/5) */
 }
@@ -149,8 +148,10 @@ double or_phase(const double *th, double f)
     double eta, mt, mc;
     source_masses(th, &eta, &mt, &mc);
     double v = cbrt(OR_PI * mt * f);
+    double q = th[P_Q];
+    double delta = (1.0 - q) / (1.0 + q);    /* (m1 - m2)/M, exact in q */
     double phi[8];
-    or_pn_phi(eta, th[P_CHI1], th[P_CHI2], v, phi);
+    or_pn_phi(eta, delta, th[P_CHI1], th[P_CHI2], v, phi);
     double sum = 0.0, vk = 1.0;
     for (int k = 0; k < 8; k++) { sum += phi[k] * vk; vk *= v; }
     double v5 = v * v * v * v * v;

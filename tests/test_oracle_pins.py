@@ -116,7 +116,7 @@ def test_newtonian_phase_spa_time():
     h = 1e-3
     def psi_n(ff):
         v = np.cbrt(math.pi * M * ff)
-        return 3.0 / (128 * eta * v ** 5) * oracle.pn_phi(eta, 0, 0, v)[0]
+        return 3.0 / (128 * eta * v ** 5) * oracle.pn_phi(eta, math.sqrt(1 - 4 * eta), 0, 0, v)[0]
     dpsi = np.array([(psi_n(x + h) - psi_n(x - h)) / (2 * h) for x in f])
     t = -(5.0 / 256.0) * tmc * (math.pi * tmc * f) ** (-8.0 / 3.0)
     np.testing.assert_allclose(dpsi, 2 * math.pi * t, rtol=1e-6)
@@ -131,8 +131,9 @@ def test_spin_terms_mass_weighted_form():
         beta = (113 * m1 ** 2 + 75 * eta) * c1 / 12 + (113 * m2 ** 2 + 75 * eta) * c2 / 12
         sigma = eta / 48 * (721 - 247) * c1 * c2
         v = 0.2
-        p = oracle.pn_phi(eta, c1, c2, v)
-        p0 = oracle.pn_phi(eta, 0.0, 0.0, v)
+        delta = (1 - q) / (1 + q)
+        p = oracle.pn_phi(eta, delta, c1, c2, v)
+        p0 = oracle.pn_phi(eta, delta, 0.0, 0.0, v)
         assert p[3] - p0[3] == pytest.approx(4 * beta, rel=1e-13, abs=1e-13)
         assert p[4] - p0[4] == pytest.approx(-10 * sigma, rel=1e-13, abs=1e-13)
 
@@ -152,6 +153,18 @@ def test_amplitude_matches_time_domain_chirp():
         assert abs(hp) == pytest.approx(h0 / (2 * math.sqrt(fdot)), rel=1e-12, abs=0)
         # circular polarisation face-on: h_x = -i h_+
         assert hc == pytest.approx(-1j * hp, rel=1e-12, abs=0)
+
+
+def test_equal_mass_limit_is_finite():
+    """q -> 1: (m1 - m2)/M -> 0 and the likelihood stays finite."""
+    w = gi.workload("c1")
+    w.N = 200
+    pb, th = oracle.make_problem(w)
+    u = np.full((1, pb.dim), 1.0 - 1e-12)
+    assert np.isfinite(pb.loglike(u)[0])
+    th2 = th.copy()
+    th2[gi.P_Q] = 1.0
+    assert np.isfinite(pb.loglike_theta(th2)[0])
 
 
 def test_isco_frequency():
