@@ -1,0 +1,355 @@
+"""Benchmark: likelihood evaluations per second inside nested-sampling
+iterations on one GB300 (plus time-to-logZ, per-step latency and the mixed
+precision form), on the 3-detector / 11-parameter / 4017-bin workload with
+1000 live points and 500 chains per iteration.
+
+A step is one ns_step: selection of the 500 lowest live points, evidence
+update, survivors' covariance and Cholesky factor, 500 slice-sampling chains
+of 55 steps each (every candidate's TaylorF2 likelihood on the GPU), and the
+stopping test. Inputs are synthetic and seeded (gwinputs); the injection is
+made with the library's own waveform.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the CPU oracle (plain FP64 C, all host cores) on a
+bounded sample of the same workload. Under torchrun each rank runs an
+independent replica (different seeds); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import gwinputs as gi  # noqa: E402
+
+METRIC = "logL evals/sec (FP64, in nested-sampling iterations)"
+UNIT = "evals/s"
+WORKLOAD = "c1"
+CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+# FP64 pipe peak derived from the unit count: 2 FP64 FMA per clock per SM
+# (1.25 TFLOP/s nominal over 152 SMs at 2070 MHz).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# Algorithmic FP64 work of one point-bin of the FP64 likelihood with D
+# detectors, in FMA-equivalents: 8 basis FMAs + one sincos (32 FMA-equivalents
+# on this GPU) + per detector 4 (phasor product) + 4 (complex MAC) + 4
+# (phasor rotation). 1 FMA = 2 flops.
+def fp64_flops_per_point_bin(n_det: int) -> float:
+    return 2.0 * (8 + 32 + 12 * n_det)
+
+
+def world():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+def init_dist(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        return dist
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={CLOCK_QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def build_workload(g, precision, seed_offset=0):
+    w = gi.workload(WORKLOAD)
+    w.seed_sampler += 100 * seed_offset
+    w.seed_noise += 100 * seed_offset
+    w.seed_injection += 100 * seed_offset
+    return w
+
+
+def run_gpu(args):
+    import torch
+    ws, rank = world()
+    dist = init_dist(ws)
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dev = torch.cuda.current_device()
+    import paper_2509_24949_gb300 as g
+    from paper_2509_24949_gb300 import _build
+    if not _build.up_to_date():
+        _build.build()
+    stream = torch.cuda.Stream()
+    w = build_workload(g, g.NS_FP64, rank)
+    sp, th_inj = g.make_analysis(w, precision=g.NS_FP64, stream=stream.cuda_stream)
+    l2_flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def flush():
+        with torch.cuda.stream(stream):
+            l2_flush.fill_(1.0)
+
+    for _ in range(args.warmup):
+        sp.step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    st0 = sp.stats()
+    evals0 = st0["evals"]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clk:
+        for i in range(args.steps):
+            flush()
+            ev[i][0].record(stream)
+            sp.step()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    st1 = sp.stats()
+    evals = st1["evals"] - evals0
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e = torch.tensor([float(evals)], dtype=torch.float64)
+        dist.all_reduce(e, op=dist.ReduceOp.SUM)
+        total_ms_max, evals_all = float(t.item()), float(e.item())
+    else:
+        total_ms_max, evals_all = total_ms, float(evals)
+    value = evals_all / (total_ms_max / 1e3)
+
+    roof = slice_kernel_roofline(st0, st1, args.steps, w.n_det)
+    sp.close()
+
+    # time-to-logZ, FP64 and mixed, full runs from ns_init to ns_result
+    ttl = {}
+    for name, prec in (("fp64", g.NS_FP64), ("mixed", g.NS_MIXED)):
+        ttl[name] = time_to_logz(g, w, prec, stream)
+
+    # end-to-end through the C ABI with host buffers: ns_init from host arrays,
+    # then K ns_step_host calls that copy each iteration's dead points to host
+    e2e = e2e_run(g, w, args.steps, stream)
+
+    if rank == 0:
+        cpu = cpu_baseline() if ws == 1 else None
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded noise, TaylorF2 injection at SNR 20, seeded detectors)",
+            "config": {"workload": "c1: 3 detectors, 11 parameters, 20-1024 Hz at df=0.25 (4017 bins), "
+                                   "n_live=1000, k=500, 55 slice steps per chain, FP64",
+                       "parallelism": f"replicas{ws}", "l2": "flushed before every timed step (256 MB write)"},
+            "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
+            "time_to_logZ": ttl,
+            "e2e": e2e,
+            "gpu_launches": 5 * args.steps + 1,   # 5 kernels per ns_step + the L2 flush fill
+            "kernel_ms_per_step": [(b - a) / args.steps for a, b in zip(st0["kernel_ms"], st1["kernel_ms"])],
+            "roofline": roof,
+            "clocks": clk.summary(),
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+def slice_kernel_roofline(st0, st1, steps, n_det):
+    """Roofline of the fused slice-update kernel over the timed region: its
+    average launch duration from the CUDA events recorded around it inside the
+    iteration's graph (on the library's stream), and its algorithmic FP64 work
+    = point-bins processed (device-side count of jcut+1 per evaluation) x the
+    FMA-equivalents of one point-bin."""
+    ms = (st1["kernel_ms"][3] - st0["kernel_ms"][3]) / steps
+    pb = (st1["point_bins"] - st0["point_bins"]) / steps
+    ev = (st1["evals"] - st0["evals"]) / steps
+    flops = pb * fp64_flops_per_point_bin(n_det)
+    achieved = flops / (ms / 1e3) / 1e12 if ms > 0 else None
+    share = ms / (sum(st1["kernel_ms"]) - sum(st0["kernel_ms"])) * steps if ms > 0 else None
+    return {"bound": "alu", "kernel": "k_slice<FP64,3 det> (fused slice update + likelihood)",
+            "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS if achieved else None, "traffic": None,
+            "peak_source": "derived (not measured): 2 FP64 FMA/clk/SM x 152 SMs x 2070 MHz",
+            "per_launch": {"ms": ms, "evals": ev, "point_bins": pb,
+                           "flops_per_point_bin": fp64_flops_per_point_bin(n_det),
+                           "share_of_step_kernels": share}}
+
+
+def time_to_logz(g, w, precision, stream):
+    import torch
+    t0 = time.perf_counter()
+    sp, _ = g.make_analysis(w, precision=precision, stream=stream.cuda_stream)
+    t_setup = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    it = sp.run()
+    r = sp.result(samples=False)
+    t2 = time.perf_counter()
+    s = sp.stats()
+    sp.close()
+    return {"seconds": t2 - t1, "setup_s": t_setup, "iterations": it, "evals": s["evals"],
+            "evals_per_s": s["evals"] / (t2 - t1), "logZ": r["logZ"], "dlogZ": r["dlogZ"]}
+
+
+def e2e_run(g, w, steps, stream):
+    import torch
+    probe, th = g.make_analysis(w, precision=g.NS_FP64, stream=stream.cuda_stream)
+    # host inputs of the analysis (pinned copies not needed: the ABI copies them)
+    f = w.freqs()
+    psd = np.tile(gi.psd_analytic(f), (w.n_det, 1))
+    data = probe.waveform(th) + gi.noise(w.seed_noise, psd, w.df)
+    probe.close()
+    pos, xarm, yarm = gi.detectors(w.seed_geometry, w.n_det)
+    k, d = w.k, w.dim
+    du, dl, dw = np.zeros((k, d)), np.zeros(k), np.zeros(k)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sp = g.Sampler(kind=w.kind, lo=w.lo, hi=w.hi, data=data, psd=psd, f0=w.f0, df=w.df, pos=pos,
+                   xarm=xarm, yarm=yarm, n_live=w.n_live, k=k, steps_per_dim=w.steps_per_dim,
+                   precision=g.NS_FP64, seed=w.seed_sampler, stream=stream.cuda_stream)
+    for _ in range(steps):
+        sp.step_host(k, du, dl, dw)
+    t1 = time.perf_counter()
+    ev = sp.stats()["evals"]
+    sp.close()
+    h2d = (2 * data.size + psd.size) * 8
+    return {"value": ev / (t1 - t0), "unit": UNIT, "h2d_bytes_per_step": h2d / steps,
+            "d2h_bytes_per_step": k * (d + 2) * 8,
+            "note": "ns_init from host arrays (data, PSD upload amortised over the steps) + ns_step_host"}
+
+
+def oracle_sample(chains: int):
+    """One bounded sample of the workload on the oracle: the first iteration's
+    selection, evidence and covariance, then `chains` of its 500 chains."""
+    import oracle
+    from oracle import ns as ons
+    w = gi.workload(WORKLOAD)
+    if not hasattr(oracle_sample, "cache"):
+        pb, th = oracle.make_problem(w)
+        st0 = ons.initial_state(pb, w.n_live, w.seed_sampler)
+        oracle_sample.cache = (pb, st0)
+    pb, st0 = oracle_sample.cache
+    d = pb.dim
+    order = np.argsort(st0.live_logl, kind="stable")
+    k = w.k
+    surv = np.ascontiguousarray(st0.live_u[order[k:]])
+    surv_l = np.ascontiguousarray(st0.live_logl[order[k:]])
+    chol = np.ascontiguousarray(ons.survivor_cholesky(surv))
+    lstar = float(st0.live_logl[order[k - 1]])
+    new_u = np.zeros((chains, d))
+    new_l = np.zeros(chains)
+    caps = np.zeros(1, dtype=np.int32)
+    nt = oracle.max_threads()
+    t0 = time.perf_counter()
+    ev = oracle.lib().or_evolve(pb.c, nt, w.seed_sampler, 0, chains, oracle._ptr(surv), oracle._ptr(surv_l),
+                                w.n_live - k, oracle._ptr(chol), lstar, w.steps_per_dim * d, 64, 64,
+                                oracle._ptr(new_u), oracle._ptr(new_l), oracle._ptr(caps))
+    return ev, time.perf_counter() - t0, nt
+
+
+def cpu_baseline(chains: int = 64):
+    ev, sec, nt = oracle_sample(chains)
+    return {"value": ev / sec, "unit": UNIT, "cores": nt, "kind": "oracle",
+            "sample": f"{chains} of the 500 slice-sampling chains of the first iteration "
+                      f"({ev} evaluations, {sec:.1f} s), plain FP64 C, OpenMP over chains"}
+
+
+def run_reference(args):
+    ws, rank = world()
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_sample(16)
+    tot_ev, tot_s, nt = 0, 0.0, 1
+    per = []
+    for _ in range(args.steps):
+        ev, sec, nt = oracle_sample(16)
+        tot_ev += ev
+        tot_s += sec
+        per.append(sec * 1e3)
+    value = tot_ev / tot_s
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_s * 1e3 / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": "c1: 3 detectors, 11 parameters, 4017 bins, "
+                                                      "n_live=1000, k=500, 55 slice steps, FP64"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": nt, "kind": "oracle",
+                            "sample": "16 of the 500 chains of the first iteration per step"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gwns", choices=["gwns", "reference"])
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

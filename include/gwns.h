@@ -1,0 +1,233 @@
+/*
+ * gwns.h -- C ABI of the GB300 nested-slice-sampling library for
+ * gravitational-wave parameter estimation.
+ *
+ * The calls follow the paper's statement of the problem (Sec. 2 and Sec. 3 of
+ * "Parallel Nested Slice Sampling for Gravitational Wave Parameter
+ * Estimation"): set up a likelihood from data, noise PSD and frequency grid
+ * (ns_init), run nested-sampling iterations that each delete the k
+ * lowest-likelihood live points and replace them with slice-sampling chains
+ * (ns_step), and read back the evidence with its error and the weighted
+ * posterior samples (ns_result).
+ *
+ * Conventions for every call:
+ *   - return NS_OK (0) on success, a negative NS_ERR_* code otherwise; no C++
+ *     exception crosses this boundary; ns_strerror() names each code;
+ *   - "host" pointers are read (or written) before the call returns; inputs are
+ *     copied, so the caller keeps ownership and may free them afterwards;
+ *   - "device" pointers are CUDA global-memory pointers of the current device,
+ *     accessed asynchronously on the context's stream;
+ *   - all device state (tables, live set, dead list, scratch) is owned by the
+ *     context and released by ns_free();
+ *   - one context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef GWNS_H
+#define GWNS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- codes */
+enum {
+    NS_OK = 0,
+    NS_ERR_INVALID_ARG = -1,   /* a null pointer, a size out of range, a bad enum */
+    NS_ERR_PSD_NONPOS = -2,    /* a PSD value <= 0 or not finite */
+    NS_ERR_K_RANGE = -3,       /* k outside 1 .. n_live-1 */
+    NS_ERR_OOM = -4,           /* a device allocation failed */
+    NS_ERR_CAPACITY = -5,      /* the caller's output buffer is too small */
+    NS_ERR_TIMEOUT = -6,       /* a bounded device-side wait gave up */
+    NS_ERR_CANCELLED = -7,     /* the request was cancelled */
+    NS_ERR_CUDA = -8,          /* a CUDA runtime call failed */
+    NS_ERR_STATE = -9          /* call not valid in the context's state */
+};
+
+/* --------------------------------------------------------- parameters */
+/* The 11 physical parameters, in this order everywhere (theta[11]):
+ * detector-frame chirp mass [Msun], mass ratio q = m2/m1 <= 1, aligned spins
+ * chi1, chi2, luminosity distance [Mpc], cos(inclination), polarisation
+ * angle [rad], coalescence phase [rad], geocentre coalescence time [s],
+ * right ascension [rad] (Greenwich sidereal time 0), sin(declination). */
+enum {
+    NS_MC = 0, NS_Q, NS_CHI1, NS_CHI2, NS_DL, NS_COSI, NS_PSI, NS_PHIC, NS_TC, NS_RA,
+    NS_SINDEC, NS_NPARAM
+};
+
+enum { NS_PRIOR_FIXED = 0, NS_PRIOR_UNIFORM = 1, NS_PRIOR_VOLUME = 2 };
+enum { NS_FP64 = 0, NS_MIXED = 1 };
+enum { NS_MODEL_GW = 0, NS_MODEL_TOY = 1 };
+
+#define NS_MAX_DET 4
+#define NS_MAX_DIM 16
+
+/* Prior over the 11 parameters. FIXED: theta = lo. UNIFORM on [lo, hi].
+ * VOLUME: p(x) ~ x^2 on [lo, hi] (distance uniform in comoving volume).
+ * The sampled dimension d is the number of non-FIXED entries; a unit-cube
+ * point u[d] maps to the non-fixed parameters in parameter order. */
+typedef struct {
+    int kind[NS_NPARAM];
+    double lo[NS_NPARAM];
+    double hi[NS_NPARAM];
+} ns_prior;
+
+/* Strain data and detector geometry (host, copied at ns_init).
+ * re/im: [n_det][N] frequency-domain data d_d(f_j); both NULL means zero data
+ * (used to build injections, see ns_waveform / ns_set_data).
+ * pos: [n_det][3] detector positions in metres (Earth-fixed frame);
+ * xarm, yarm: [n_det][3] unit vectors of the two arms.
+ * ideal = 1 replaces every detector by an idealised one with F+ = 1,
+ * Fx = 0 and no time delay (pos/xarm/yarm may then be NULL). */
+typedef struct {
+    int n_det;
+    int ideal;
+    const double *re;
+    const double *im;
+    const double *pos;
+    const double *xarm;
+    const double *yarm;
+} ns_data;
+
+/* One-sided noise PSD S_d(f_j) [1/Hz], [n_det][N], host, copied, all > 0. */
+typedef struct {
+    const double *S;
+} ns_psd;
+
+/* Uniform frequency grid f_j = f0 + j df, j = 0 .. N-1 (both ends included). */
+typedef struct {
+    int N;
+    double f0;
+    double df;
+} ns_grid;
+
+/* Run options. Zero-initialise and set what you need; zero fields take the
+ * defaults in brackets. */
+typedef struct {
+    int n_live;          /* live points n (required, >= 2) */
+    int k;               /* points deleted per iteration [n/2] (paper Sec. 2) */
+    int steps_per_dim;   /* slice steps per chain = steps_per_dim * d [5] */
+    int precision;       /* NS_FP64 or NS_MIXED */
+    int no_cutoff;       /* 0: waveform zero above f_ISCO; 1: no cutoff */
+    int max_stepout;     /* per side [64] */
+    int max_shrink;      /* shrink draws per slice step [64] */
+    int model;           /* NS_MODEL_GW, or NS_MODEL_TOY (correlated Gaussian) */
+    int toy_dim;         /* toy dimension d (model = NS_MODEL_TOY) */
+    int warps_per_point; /* warps cooperating on one likelihood [0: tuned] */
+    double dlogz_stop;   /* stop when log(Z + X Lmax) - log Z < this [0.1] */
+    uint64_t seed;       /* Philox key */
+    void *stream;        /* cudaStream_t to run on [NULL: library-owned stream] */
+} ns_options;
+
+typedef struct ns_ctx ns_ctx;
+
+/* Create a context: validate, copy data and PSD to the device, build the
+ * per-grid tables (basis functions of f, weighted data 4 df f^(-7/6) d / S,
+ * prefix sums of 4 df f^(-7/3) / S), draw the n initial live points from the
+ * prior and evaluate them. The likelihood is the Whittle log-likelihood ratio
+ * against noise, log L = sum_d [<d_d|h_d> - <h_d|h_d>/2] with
+ * <a|b> = 4 df Re sum_j a_j b_j^* / S_j, for a TaylorF2 signal projected on
+ * each detector (paper Sec. 3 uses the same likelihood with another waveform).
+ * Errors: INVALID_ARG, PSD_NONPOS, K_RANGE, OOM, CUDA. On error *out = NULL. */
+int ns_init(ns_ctx **out, const ns_prior *prior, const ns_data *data, const ns_psd *psd,
+            const ns_grid *grid, const ns_options *opts);
+
+/* Replace the strain data (host [n_det][N] arrays) and re-evaluate the live
+ * points. Errors: INVALID_ARG, CUDA. */
+int ns_set_data(ns_ctx *ctx, const double *re, const double *im);
+
+/* One nested-sampling iteration (paper Sec. 2): delete the k lowest live
+ * points (the k-th lowest log L is the new threshold L*), update log X and
+ * log Z, and replace them by k slice-sampling chains of steps_per_dim * d
+ * steps each, started at uniformly chosen survivors and moving along
+ * directions drawn from the survivors' covariance, with stepping out and
+ * shrinkage (Neal 2003). *done (may be NULL) is set to 1 once the remaining
+ * evidence fraction is below dlogz_stop. 1 <= k <= n_live - 1 (K_RANGE). */
+int ns_step(ns_ctx *ctx, int k, int *done);
+
+/* ns_step with the iteration's k dead points copied to host buffers
+ * (each may be NULL): u [k][d], logl [k], logw [k] (log prior-mass weight). */
+int ns_step_host(ns_ctx *ctx, int k, int *done, double *dead_u, double *dead_logl,
+                 double *dead_logw);
+
+/* Iterate ns_step(opts.k) until done or max_iter iterations. */
+int ns_run(ns_ctx *ctx, int max_iter, int *iterations);
+
+/* Weighted samples: the dead points in deletion order followed by the final
+ * live points in ascending log L. All arrays host, caller-owned, cap entries.
+ * theta may be NULL; u, logl, logw may be NULL. */
+typedef struct {
+    int cap;          /* capacity (entries) provided by the caller */
+    int count;        /* entries written (or needed, on NS_ERR_CAPACITY) */
+    double *theta;    /* [cap][11] physical parameters */
+    double *u;        /* [cap][d] unit-cube coordinates */
+    double *logl;     /* [cap] */
+    double *logw;     /* [cap] log prior-mass weight; log posterior weight = logw + logl - logZ */
+} ns_samples;
+
+/* Finish the run: add the final live points to the evidence, then return
+ * log Z (log Bayes factor signal vs noise), its error dlogZ (standard deviation
+ * over 200 replicate shrinkage sequences t ~ Beta(n_j, 1)) and the weighted
+ * samples. samples may be NULL. Does not end the run: ns_step may continue.
+ * Errors: CAPACITY (samples->count = entries needed), CUDA. */
+int ns_result(ns_ctx *ctx, double *logZ, double *dlogZ, ns_samples *samples);
+
+typedef struct {
+    long long iterations;
+    long long evals;        /* likelihood evaluations so far (initial draw included) */
+    long long cap_hits;     /* slice steps that ended at the shrink cap */
+    double logZ;            /* running log Z (dead points only) */
+    double logX;            /* log prior volume enclosed by the live set */
+    double lstar;           /* last threshold */
+    double logl_max;        /* largest live log L */
+    int done;
+    int d;                  /* sampled dimension */
+    int n_live;
+    int n_dead;
+    long long point_bins;   /* sum over slice-update evaluations of the bins each one read */
+    double kernel_ms[5];    /* cumulative device time of the iteration's kernels, from CUDA
+                               events recorded on the context's stream inside the iteration's
+                               graph: select, evidence, covariance, slice update, finish */
+} ns_stats;
+
+int ns_get_stats(ns_ctx *ctx, ns_stats *st);
+
+/* Batched likelihood of m unit-cube points, device pointers: u [m][d] in,
+ * logl [m] out, on the context's stream (asynchronous). 0 <= m. */
+int ns_eval_lnl(ns_ctx *ctx, const double *u, int m, double *logl);
+
+/* Same with host pointers (copies in, evaluates, copies out, synchronises). */
+int ns_eval_lnl_host(ns_ctx *ctx, const double *u, int m, double *logl);
+
+/* Batched likelihood of m physical parameter vectors theta [m][11] (device). */
+int ns_eval_lnl_theta(ns_ctx *ctx, const double *theta, int m, double *logl);
+
+/* Detector strain h_d(f_j) of one physical parameter vector (host theta[11]),
+ * written to host h_re, h_im [n_det][N]; zero above f_ISCO unless no_cutoff. */
+int ns_waveform(ns_ctx *ctx, const double *theta, double *h_re, double *h_im);
+
+/* Prior transform of m unit-cube points (host u [m][d]) to physical
+ * parameters (host theta [m][11]). */
+int ns_prior_transform(ns_ctx *ctx, const double *u, int m, double *theta);
+
+/* Network optimal SNR^2 = sum_d <h_d|h_d> of one parameter vector (host
+ * theta[11]), from the closed form A^2 |Q_d|^2 P_d(jcut). */
+int ns_optimal_snr2(ns_ctx *ctx, const double *theta, double *rho2);
+
+/* Live set (host, each may be NULL): u [n][d], logl [n]. */
+int ns_get_live(ns_ctx *ctx, double *u, double *logl);
+
+/* Overwrite the live set (host u [n][d], logl [n]); used to resume. */
+int ns_set_live(ns_ctx *ctx, const double *u, const double *logl);
+
+/* Synchronise the context's stream. */
+int ns_sync(ns_ctx *ctx);
+
+void ns_free(ns_ctx *ctx);
+const char *ns_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GWNS_H */

@@ -1,0 +1,365 @@
+"""Python binding of libgwns.so (the C ABI in include/gwns.h).
+
+Argument marshalling only: every step of the likelihood and of the nested
+sampling iteration runs in the library's CUDA kernels. Importing this package
+loads the in-tree shared library and raises if it has not been built
+(``python -c "import __graft_entry__ as g; g.build()"``); there is no CPU path.
+PyTorch is used only for device buffers (tensor ``data_ptr()``) and streams.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import _build
+
+_LIB = None
+
+NS_OK = 0
+NS_FP64, NS_MIXED = 0, 1
+NS_MODEL_GW, NS_MODEL_TOY = 0, 1
+NPARAM = 11
+NS_MAX_DET = 4
+
+
+class GWNSError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {lib().ns_strerror(code).decode()} ({code})")
+
+
+class _Prior(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int * NPARAM), ("lo", ctypes.c_double * NPARAM),
+                ("hi", ctypes.c_double * NPARAM)]
+
+
+class _Data(ctypes.Structure):
+    _fields_ = [("n_det", ctypes.c_int), ("ideal", ctypes.c_int), ("re", ctypes.c_void_p),
+                ("im", ctypes.c_void_p), ("pos", ctypes.c_void_p), ("xarm", ctypes.c_void_p),
+                ("yarm", ctypes.c_void_p)]
+
+
+class _Psd(ctypes.Structure):
+    _fields_ = [("S", ctypes.c_void_p)]
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("f0", ctypes.c_double), ("df", ctypes.c_double)]
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("n_live", ctypes.c_int), ("k", ctypes.c_int), ("steps_per_dim", ctypes.c_int),
+                ("precision", ctypes.c_int), ("no_cutoff", ctypes.c_int),
+                ("max_stepout", ctypes.c_int), ("max_shrink", ctypes.c_int),
+                ("model", ctypes.c_int), ("toy_dim", ctypes.c_int),
+                ("warps_per_point", ctypes.c_int), ("dlogz_stop", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p)]
+
+
+class _Samples(ctypes.Structure):
+    _fields_ = [("cap", ctypes.c_int), ("count", ctypes.c_int), ("theta", ctypes.c_void_p),
+                ("u", ctypes.c_void_p), ("logl", ctypes.c_void_p), ("logw", ctypes.c_void_p)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_longlong), ("evals", ctypes.c_longlong),
+                ("cap_hits", ctypes.c_longlong), ("logZ", ctypes.c_double),
+                ("logX", ctypes.c_double), ("lstar", ctypes.c_double),
+                ("logl_max", ctypes.c_double), ("done", ctypes.c_int), ("d", ctypes.c_int),
+                ("n_live", ctypes.c_int), ("n_dead", ctypes.c_int), ("point_bins", ctypes.c_longlong),
+                ("kernel_ms", ctypes.c_double * 5)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libgwns.so (raises if it was not built)."""
+    global _LIB
+    if _LIB is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise ImportError(f"libgwns.so is not built ({path}); run __graft_entry__.build()")
+        L = ctypes.CDLL(path)
+        vp, ip, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        P = ctypes.POINTER
+        L.ns_strerror.argtypes = [ip]; L.ns_strerror.restype = ctypes.c_char_p
+        L.ns_init.argtypes = [P(vp), P(_Prior), P(_Data), P(_Psd), P(_Grid), P(_Options)]
+        L.ns_set_data.argtypes = [vp, vp, vp]
+        L.ns_step.argtypes = [vp, ip, P(ip)]
+        L.ns_step_host.argtypes = [vp, ip, P(ip), vp, vp, vp]
+        L.ns_run.argtypes = [vp, ip, P(ip)]
+        L.ns_result.argtypes = [vp, P(dp), P(dp), P(_Samples)]
+        L.ns_get_stats.argtypes = [vp, P(_Stats)]
+        L.ns_eval_lnl.argtypes = [vp, vp, ip, vp]
+        L.ns_eval_lnl_host.argtypes = [vp, vp, ip, vp]
+        L.ns_eval_lnl_theta.argtypes = [vp, vp, ip, vp]
+        L.ns_waveform.argtypes = [vp, vp, vp, vp]
+        L.ns_prior_transform.argtypes = [vp, vp, ip, vp]
+        L.ns_optimal_snr2.argtypes = [vp, vp, P(dp)]
+        L.ns_get_live.argtypes = [vp, vp, vp]
+        L.ns_set_live.argtypes = [vp, vp, vp]
+        L.ns_sync.argtypes = [vp]
+        L.ns_free.argtypes = [vp]; L.ns_free.restype = None
+        for name in ("ns_init", "ns_set_data", "ns_step", "ns_step_host", "ns_run", "ns_result",
+                     "ns_get_stats", "ns_eval_lnl", "ns_eval_lnl_host", "ns_eval_lnl_theta",
+                     "ns_waveform", "ns_prior_transform", "ns_optimal_snr2", "ns_get_live", "ns_set_live", "ns_sync"):
+            getattr(L, name).restype = ctypes.c_int
+        _LIB = L
+    return _LIB
+
+
+def _check(rc: int, what: str):
+    if rc != NS_OK:
+        raise GWNSError(rc, what)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _ptr(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data
+
+
+class Sampler:
+    """One nested-sampling context (ns_init .. ns_free)."""
+
+    def __init__(self, *, kind=None, lo=None, hi=None, data=None, psd=None, f0=20.0, df=1.0,
+                 pos=None, xarm=None, yarm=None, ideal=False, n_live=100, k=0, steps_per_dim=5,
+                 precision=NS_FP64, no_cutoff=False, max_stepout=0, max_shrink=0,
+                 model=NS_MODEL_GW, toy_dim=0, warps_per_point=0, dlogz_stop=0.1, seed=0,
+                 stream=None):
+        L = lib()
+        self._keep = []
+        pr = _Prior()
+        dt = _Data()
+        ps = _Psd()
+        gr = _Grid()
+        if model == NS_MODEL_GW:
+            kind = np.asarray(kind, dtype=np.int32)
+            for p in range(NPARAM):
+                pr.kind[p] = int(kind[p])
+                pr.lo[p] = float(lo[p])
+                pr.hi[p] = float(hi[p])
+            psd = _f64(psd)
+            n_det, N = psd.shape
+            self._keep.append(psd)
+            ps.S = _ptr(psd)
+            dt.n_det = n_det
+            dt.ideal = int(bool(ideal))
+            if data is not None:
+                data = np.asarray(data, dtype=np.complex128).reshape(n_det, N)
+                re, im = _f64(data.real), _f64(data.imag)
+                self._keep += [re, im]
+                dt.re, dt.im = _ptr(re), _ptr(im)
+            if not ideal:
+                arrs = [_f64(pos).reshape(n_det, 3), _f64(xarm).reshape(n_det, 3), _f64(yarm).reshape(n_det, 3)]
+                self._keep += arrs
+                dt.pos, dt.xarm, dt.yarm = (_ptr(a) for a in arrs)
+            gr.N, gr.f0, gr.df = N, float(f0), float(df)
+            self.n_det, self.N = n_det, N
+        else:
+            self.n_det, self.N = 0, 0
+        opt = _Options(n_live, k, steps_per_dim, precision, int(bool(no_cutoff)), max_stepout,
+                       max_shrink, model, toy_dim, warps_per_point, dlogz_stop, seed,
+                       None if stream is None else int(stream))
+        ctx = ctypes.c_void_p()
+        _check(L.ns_init(ctypes.byref(ctx), ctypes.byref(pr), ctypes.byref(dt), ctypes.byref(ps),
+                         ctypes.byref(gr), ctypes.byref(opt)), "ns_init")
+        self._ctx = ctx
+        self._keep = []
+        self.n_live = n_live
+        self.k = k if k else n_live // 2
+        self.precision = precision
+        self.model = model
+        st = self.stats()
+        self.dim = st["d"]
+
+    # ------------------------------------------------------------ lifetime
+    def close(self):
+        if getattr(self, "_ctx", None):
+            lib().ns_free(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ------------------------------------------------------------ sampling
+    def set_data(self, data):
+        data = np.asarray(data, dtype=np.complex128).reshape(self.n_det, self.N)
+        re, im = _f64(data.real), _f64(data.imag)
+        _check(lib().ns_set_data(self._ctx, _ptr(re), _ptr(im)), "ns_set_data")
+
+    def step(self, k: Optional[int] = None) -> bool:
+        done = ctypes.c_int(0)
+        _check(lib().ns_step(self._ctx, int(k if k else self.k), ctypes.byref(done)), "ns_step")
+        return bool(done.value)
+
+    def step_host(self, k: Optional[int] = None, out_u=None, out_logl=None, out_logw=None) -> bool:
+        done = ctypes.c_int(0)
+        _check(lib().ns_step_host(self._ctx, int(k if k else self.k), ctypes.byref(done), _ptr(out_u),
+                                  _ptr(out_logl), _ptr(out_logw)), "ns_step_host")
+        return bool(done.value)
+
+    def run(self, max_iter: int = 100000) -> int:
+        it = ctypes.c_int(0)
+        _check(lib().ns_run(self._ctx, max_iter, ctypes.byref(it)), "ns_run")
+        return it.value
+
+    def stats(self) -> dict:
+        s = _Stats()
+        _check(lib().ns_get_stats(self._ctx, ctypes.byref(s)), "ns_get_stats")
+        out = {name: getattr(s, name) for name, _ in _Stats._fields_}
+        out["kernel_ms"] = list(s.kernel_ms)
+        return out
+
+    def result(self, samples: bool = True) -> dict:
+        lz, dlz = ctypes.c_double(), ctypes.c_double()
+        if not samples:
+            _check(lib().ns_result(self._ctx, ctypes.byref(lz), ctypes.byref(dlz), None), "ns_result")
+            return dict(logZ=lz.value, dlogZ=dlz.value)
+        st = self.stats()
+        cap = st["n_dead"] + self.n_live
+        u = np.zeros((cap, self.dim))
+        logl = np.zeros(cap)
+        logw = np.zeros(cap)
+        theta = np.zeros((cap, NPARAM)) if self.model == NS_MODEL_GW else None
+        sm = _Samples(cap, 0, _ptr(theta), _ptr(u), _ptr(logl), _ptr(logw))
+        _check(lib().ns_result(self._ctx, ctypes.byref(lz), ctypes.byref(dlz), ctypes.byref(sm)), "ns_result")
+        out = dict(logZ=lz.value, dlogZ=dlz.value, u=u, logl=logl, logw=logw, count=sm.count)
+        if theta is not None:
+            out["theta"] = theta
+        return out
+
+    # ---------------------------------------------------------- likelihood
+    def eval_lnl(self, u, out=None):
+        """Device batched log L: u is a CUDA float64 tensor [m, d] (or a host array)."""
+        if isinstance(u, np.ndarray):
+            u = _f64(u).reshape(-1, self.dim)
+            res = np.zeros(u.shape[0])
+            _check(lib().ns_eval_lnl_host(self._ctx, _ptr(u), u.shape[0], _ptr(res)), "ns_eval_lnl_host")
+            return res
+        import torch
+        assert u.is_cuda and u.dtype == torch.float64 and u.is_contiguous()
+        m = u.shape[0]
+        if out is None:
+            out = torch.empty(m, dtype=torch.float64, device=u.device)
+        # order torch's producers before the library's stream, and the
+        # library's writes before torch's consumers
+        torch.cuda.current_stream(u.device).synchronize()
+        _check(lib().ns_eval_lnl(self._ctx, u.data_ptr(), m, out.data_ptr()), "ns_eval_lnl")
+        self.sync()
+        return out
+
+    def eval_lnl_theta(self, theta, out=None):
+        import torch
+        assert theta.is_cuda and theta.dtype == torch.float64 and theta.is_contiguous()
+        m = theta.shape[0]
+        if out is None:
+            out = torch.empty(m, dtype=torch.float64, device=theta.device)
+        torch.cuda.current_stream(theta.device).synchronize()
+        _check(lib().ns_eval_lnl_theta(self._ctx, theta.data_ptr(), m, out.data_ptr()), "ns_eval_lnl_theta")
+        self.sync()
+        return out
+
+    def waveform(self, theta) -> np.ndarray:
+        th = _f64(theta)
+        re = np.zeros((self.n_det, self.N))
+        im = np.zeros((self.n_det, self.N))
+        _check(lib().ns_waveform(self._ctx, _ptr(th), _ptr(re), _ptr(im)), "ns_waveform")
+        return re + 1j * im
+
+    def theta(self, u) -> np.ndarray:
+        u = _f64(u).reshape(-1, self.dim)
+        th = np.zeros((u.shape[0], NPARAM))
+        _check(lib().ns_prior_transform(self._ctx, _ptr(u), u.shape[0], _ptr(th)), "ns_prior_transform")
+        return th
+
+    def snr2(self, theta) -> float:
+        r = ctypes.c_double()
+        _check(lib().ns_optimal_snr2(self._ctx, _ptr(_f64(theta)), ctypes.byref(r)), "ns_optimal_snr2")
+        return r.value
+
+    def live(self):
+        u = np.zeros((self.n_live, self.dim))
+        l = np.zeros(self.n_live)
+        _check(lib().ns_get_live(self._ctx, _ptr(u), _ptr(l)), "ns_get_live")
+        return u, l
+
+    def set_live(self, u, logl):
+        u, l = _f64(u), _f64(logl)
+        _check(lib().ns_set_live(self._ctx, _ptr(u), _ptr(l)), "ns_set_live")
+
+    def sync(self):
+        _check(lib().ns_sync(self._ctx), "ns_sync")
+
+
+def sampler_for_workload(w, data=None, precision=NS_FP64, **kw) -> Sampler:
+    """A Sampler for a gwinputs.Workload (seeded detectors and analytic PSD)."""
+    import gwinputs as gi
+    f = w.freqs()
+    psd = np.tile(gi.psd_analytic(f), (w.n_det, 1))
+    if w.ideal:
+        pos = xarm = yarm = None
+    else:
+        pos, xarm, yarm = gi.detectors(w.seed_geometry, w.n_det)
+    args = dict(kind=w.kind, lo=w.lo, hi=w.hi, data=data, psd=psd, f0=w.f0, df=w.df, pos=pos,
+                xarm=xarm, yarm=yarm, ideal=w.ideal, n_live=w.n_live, k=w.k,
+                steps_per_dim=w.steps_per_dim, precision=precision, dlogz_stop=w.dlogz_stop,
+                seed=w.seed_sampler)
+    args.update(kw)
+    return Sampler(**args)
+
+
+def make_analysis(w, precision=NS_FP64, max_draws: int = 1000, **kw):
+    """Build a workload's synthetic data with the library's own waveform
+    (injection drawn from the prior, distance scaled to the target SNR) and
+    return (sampler, theta_inj)."""
+    import gwinputs as gi
+    probe = sampler_for_workload(w, data=None, precision=NS_FP64, n_live=2, k=1, **{
+        k_: v for k_, v in kw.items() if k_ not in ("n_live", "k")})
+    kind, lo, hi = w.kind.copy(), w.lo.copy(), w.hi.copy()
+
+    def snr(th):
+        return float(np.sqrt(probe.snr2(th)))
+
+    if w.fixed_injection is not None:
+        th = w.fixed_injection.copy()
+        th[gi.P_DL] *= snr(th) / w.snr
+        if w.dl_from_snr:
+            lo[gi.P_DL] = hi[gi.P_DL] = th[gi.P_DL]
+    else:
+        th = None
+        cands = probe.theta(gi.unit_cube(w.seed_injection, max_draws, w.dim))
+        for t in cands:
+            t = t.copy()
+            dl = t[gi.P_DL] * snr(t) / w.snr
+            if lo[gi.P_DL] <= dl <= hi[gi.P_DL]:
+                t[gi.P_DL] = dl
+                th = t
+                break
+        if th is None:
+            raise RuntimeError("no injection candidate reaches the target SNR inside the prior")
+    data = probe.waveform(th)
+    probe.close()
+    if w.noise:
+        f = w.freqs()
+        data = data + gi.noise(w.seed_noise, np.tile(gi.psd_analytic(f), (w.n_det, 1)), w.df)
+    import copy
+    w2 = copy.copy(w)
+    w2.kind, w2.lo, w2.hi = kind, lo, hi
+    return sampler_for_workload(w2, data=data, precision=precision, **kw), th

@@ -1,0 +1,616 @@
+// gwns_abi.cu -- host implementation of the C ABI declared in include/gwns.h:
+// context lifetime, input validation, device buffers, CUDA-graph capture of
+// one nested-sampling iteration, and result assembly.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/gwns.h"
+#include "gwns_kernels.cuh"
+
+using namespace gwns;
+
+struct ns_ctx {
+    Model M;
+    Tables T;
+    int n = 0, d = 0, k_default = 0, steps = 0, precision = 0, max_so = 64, max_sh = 64, warps = 0;
+    double dlogz = 0.1;
+    uint64_t seed = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    // device buffers
+    double *d_re = nullptr, *d_im = nullptr, *d_psd = nullptr;
+    double *basis64 = nullptr, *f64 = nullptr, *prefix = nullptr;
+    double2 *w64 = nullptr;
+    float2 *basis32 = nullptr, *f32 = nullptr, *w32 = nullptr;
+    double *live_u = nullptr, *live_logl = nullptr;
+    int *order = nullptr;
+    double *chol = nullptr;
+    double *dead_u = nullptr, *dead_logl = nullptr, *dead_logw = nullptr, *dead_nlive = nullptr;
+    long long dead_cap = 0;
+    RunState *state = nullptr;
+    RunState *h_state = nullptr;     // pinned
+    double *scratch = nullptr;       // eval / waveform scratch
+    size_t scratch_bytes = 0;
+    // result buffers
+    double *fin_u = nullptr, *fin_logl = nullptr, *fin_logw = nullptr, *fin_nlive = nullptr;
+    double *res = nullptr;           // [R + 8]
+    // graph of one iteration, with timing events between its kernels
+    cudaGraphExec_t graph = nullptr;
+    int graph_k = -1;
+    cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    bool timing = false;
+    double kernel_ms[5] = {0, 0, 0, 0, 0};
+    long long n_dead = 0;
+};
+
+namespace {
+
+constexpr int kReplicates = 200;
+
+int cuda_fail(cudaError_t e) {
+    if (e == cudaErrorMemoryAllocation) return NS_ERR_OOM;
+    return NS_ERR_CUDA;
+}
+
+#define CK(call)                                   \
+    do {                                           \
+        cudaError_t e_ = (call);                   \
+        if (e_ != cudaSuccess) return cuda_fail(e_); \
+    } while (0)
+
+template <class T>
+int dalloc(T **p, size_t count) {
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+    if (e != cudaSuccess) { *p = nullptr; return cuda_fail(e); }
+    return NS_OK;
+}
+
+void dfree(void *p) {
+    if (p) cudaFree(p);
+}
+
+bool is_fin(double x) { return std::isfinite(x); }
+
+int choose_warps(const ns_ctx *c) {
+    if (c->warps > 0) return c->warps;
+    if (c->M.model == M_TOY) return 1;
+    // FP64: the FP64 pipe binds, so one warp per point keeps the per-point
+    // overheads lowest once every SM sub-partition has a chain; mixed: more
+    // warps per point hide FP32 latency. Tuned values come from the autotuner.
+    const int bins = c->M.N;
+    if (c->precision == NS_FP64) return bins > 32768 ? 2 : 1;
+    return bins > 16384 ? 8 : (bins > 2048 ? 4 : 2);
+}
+
+StepArgs step_args(ns_ctx *c, int k) {
+    StepArgs A;
+    A.live_u = c->live_u;
+    A.live_logl = c->live_logl;
+    A.order = c->order;
+    A.chol = c->chol;
+    A.dead_u = c->dead_u;
+    A.dead_logl = c->dead_logl;
+    A.dead_logw = c->dead_logw;
+    A.dead_nlive = c->dead_nlive;
+    A.state = c->state;
+    A.seed = c->seed;
+    A.n = c->n;
+    A.k = k;
+    A.steps = c->steps;
+    A.max_stepout = c->max_so;
+    A.max_shrink = c->max_sh;
+    A.dlogz_stop = c->dlogz;
+    return A;
+}
+
+int ensure_dead_capacity(ns_ctx *c, long long need) {
+    if (need <= c->dead_cap) return NS_OK;
+    long long cap = std::max<long long>(need, std::max<long long>(2 * c->dead_cap, 64LL * c->n));
+    double *u = nullptr, *l = nullptr, *w = nullptr, *nl = nullptr;
+    int rc;
+    if ((rc = dalloc(&u, (size_t)cap * c->d)) || (rc = dalloc(&l, cap)) || (rc = dalloc(&w, cap)) ||
+        (rc = dalloc(&nl, cap))) {
+        dfree(u); dfree(l); dfree(w); dfree(nl);
+        return rc;
+    }
+    if (c->n_dead > 0) {
+        CK(cudaMemcpyAsync(u, c->dead_u, sizeof(double) * c->n_dead * c->d, cudaMemcpyDeviceToDevice, c->stream));
+        CK(cudaMemcpyAsync(l, c->dead_logl, sizeof(double) * c->n_dead, cudaMemcpyDeviceToDevice, c->stream));
+        CK(cudaMemcpyAsync(w, c->dead_logw, sizeof(double) * c->n_dead, cudaMemcpyDeviceToDevice, c->stream));
+        CK(cudaMemcpyAsync(nl, c->dead_nlive, sizeof(double) * c->n_dead, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    dfree(c->dead_u); dfree(c->dead_logl); dfree(c->dead_logw); dfree(c->dead_nlive);
+    c->dead_u = u; c->dead_logl = l; c->dead_logw = w; c->dead_nlive = nl;
+    c->dead_cap = cap;
+    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; c->graph_k = -1; }
+    return NS_OK;
+}
+
+int ensure_scratch(ns_ctx *c, size_t bytes) {
+    if (bytes <= c->scratch_bytes) return NS_OK;
+    CK(cudaStreamSynchronize(c->stream));
+    dfree(c->scratch);
+    c->scratch = nullptr;
+    c->scratch_bytes = 0;
+    int rc = dalloc((char **)&c->scratch, bytes);
+    if (rc) return rc;
+    c->scratch_bytes = bytes;
+    return NS_OK;
+}
+
+// Record timing event i on the stream (as an event-record node when capturing).
+int mark(ns_ctx *c, int i) {
+    if (!c->timing) return NS_OK;
+    CK(cudaEventRecordWithFlags(c->ev[i], c->stream, cudaEventRecordExternal));
+    return NS_OK;
+}
+
+// Enqueue the five kernels of one iteration.
+int enqueue_iteration(ns_ctx *c, int k) {
+    StepArgs A = step_args(c, k);
+    int rc;
+    if ((rc = mark(c, 0))) return rc;
+    CK(launch_select(c->live_logl, c->n, c->order, c->stream));
+    if ((rc = mark(c, 1))) return rc;
+    CK(launch_evidence(c->M, A, c->stream));
+    if ((rc = mark(c, 2))) return rc;
+    CK(launch_cov_chol(c->M, A, c->stream));
+    if ((rc = mark(c, 3))) return rc;
+    CK(launch_slice(c->M, c->T, c->precision, choose_warps(c), A, c->stream));
+    if ((rc = mark(c, 4))) return rc;
+    CK(launch_finish(A, c->stream));
+    if ((rc = mark(c, 5))) return rc;
+    return NS_OK;
+}
+
+int capture_iteration(ns_ctx *c, int k) {
+    if (c->graph && c->graph_k == k) return NS_OK;
+    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_iteration(c, k);
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = cudaGraphInstantiate(&c->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { c->graph = nullptr; return cuda_fail(e); }
+    c->graph_k = k;
+    return NS_OK;
+}
+
+int eval_points(ns_ctx *c, const double *in, int is_theta, int m, double *logl) {
+    CK(launch_eval(c->M, c->T, c->precision, choose_warps(c), in, is_theta, m, logl, c->stream));
+    return NS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ns_strerror(int code) {
+    switch (code) {
+        case NS_OK: return "ok";
+        case NS_ERR_INVALID_ARG: return "invalid argument";
+        case NS_ERR_PSD_NONPOS: return "PSD value not positive and finite";
+        case NS_ERR_K_RANGE: return "k outside 1 .. n_live-1";
+        case NS_ERR_OOM: return "device allocation failed";
+        case NS_ERR_CAPACITY: return "output buffer too small";
+        case NS_ERR_TIMEOUT: return "device-side wait timed out";
+        case NS_ERR_CANCELLED: return "cancelled";
+        case NS_ERR_CUDA: return "CUDA runtime error";
+        case NS_ERR_STATE: return "call not valid in this state";
+        default: return "unknown error";
+    }
+}
+
+void ns_free(ns_ctx *c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    for (cudaEvent_t e : c->ev)
+        if (e) cudaEventDestroy(e);
+    void *bufs[] = {c->d_re, c->d_im, c->d_psd, c->basis64, c->f64, c->prefix, c->w64, c->basis32,
+                    c->f32, c->w32, c->live_u, c->live_logl, c->order, c->chol, c->dead_u,
+                    c->dead_logl, c->dead_logw, c->dead_nlive, c->state, c->scratch, c->fin_u,
+                    c->fin_logl, c->fin_logw, c->fin_nlive, c->res};
+    for (void *p : bufs) dfree(p);
+    if (c->h_state) cudaFreeHost(c->h_state);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+static int validate(const ns_prior *prior, const ns_data *data, const ns_psd *psd, const ns_grid *grid,
+                    const ns_options *o) {
+    if (!o) return NS_ERR_INVALID_ARG;
+    if (o->n_live < 2 || o->n_live > 4096) return NS_ERR_INVALID_ARG;
+    if (o->k != 0 && (o->k < 1 || o->k > o->n_live - 1)) return NS_ERR_K_RANGE;
+    if (o->precision != NS_FP64 && o->precision != NS_MIXED) return NS_ERR_INVALID_ARG;
+    if (o->steps_per_dim < 0 || o->max_stepout < 0 || o->max_shrink < 0) return NS_ERR_INVALID_ARG;
+    if (o->warps_per_point != 0 && o->warps_per_point != 1 && o->warps_per_point != 2 &&
+        o->warps_per_point != 4 && o->warps_per_point != 8)
+        return NS_ERR_INVALID_ARG;
+    if (o->model == NS_MODEL_TOY) {
+        if (o->toy_dim < 1 || o->toy_dim > NS_MAX_DIM) return NS_ERR_INVALID_ARG;
+        return NS_OK;
+    }
+    if (o->model != NS_MODEL_GW) return NS_ERR_INVALID_ARG;
+    if (!prior || !data || !psd || !grid || !psd->S) return NS_ERR_INVALID_ARG;
+    if (grid->N < 1 || !is_fin(grid->f0) || !is_fin(grid->df) || grid->df <= 0.0 || grid->f0 <= 0.0)
+        return NS_ERR_INVALID_ARG;
+    if (data->n_det < 1 || data->n_det > NS_MAX_DET) return NS_ERR_INVALID_ARG;
+    if ((data->re == nullptr) != (data->im == nullptr)) return NS_ERR_INVALID_ARG;
+    if (!data->ideal && (!data->pos || !data->xarm || !data->yarm)) return NS_ERR_INVALID_ARG;
+    int dim = 0;
+    for (int p = 0; p < NS_NPARAM; p++) {
+        int kd = prior->kind[p];
+        if (kd != NS_PRIOR_FIXED && kd != NS_PRIOR_UNIFORM && kd != NS_PRIOR_VOLUME) return NS_ERR_INVALID_ARG;
+        if (!is_fin(prior->lo[p])) return NS_ERR_INVALID_ARG;
+        if (kd != NS_PRIOR_FIXED) {
+            if (!is_fin(prior->hi[p]) || !(prior->hi[p] > prior->lo[p])) return NS_ERR_INVALID_ARG;
+            dim++;
+        }
+    }
+    if (dim < 1 || dim > NS_MAX_DIM) return NS_ERR_INVALID_ARG;
+    // physical ranges the waveform needs
+    double qlo = prior->lo[NS_Q], qhi = prior->kind[NS_Q] == NS_PRIOR_FIXED ? prior->lo[NS_Q] : prior->hi[NS_Q];
+    if (!(qlo > 0.0) || qhi > 1.0) return NS_ERR_INVALID_ARG;
+    if (!(prior->lo[NS_MC] > 0.0) || !(prior->lo[NS_DL] > 0.0)) return NS_ERR_INVALID_ARG;
+    const size_t nn = (size_t)data->n_det * grid->N;
+    for (size_t i = 0; i < nn; i++)
+        if (!(psd->S[i] > 0.0) || !is_fin(psd->S[i])) return NS_ERR_PSD_NONPOS;
+    return NS_OK;
+}
+
+int ns_init(ns_ctx **out, const ns_prior *prior, const ns_data *data, const ns_psd *psd,
+            const ns_grid *grid, const ns_options *o) {
+    if (!out) return NS_ERR_INVALID_ARG;
+    *out = nullptr;
+    int rc = validate(prior, data, psd, grid, o);
+    if (rc) return rc;
+    ns_ctx *c = new (std::nothrow) ns_ctx();
+    if (!c) return NS_ERR_OOM;
+    std::memset(&c->M, 0, sizeof(Model));
+    std::memset(&c->T, 0, sizeof(Tables));
+    cudaGetDevice(&c->device);
+    Model &M = c->M;
+    c->n = o->n_live;
+    c->k_default = o->k ? o->k : o->n_live / 2;
+    c->precision = o->precision;
+    c->max_so = o->max_stepout ? o->max_stepout : 64;
+    c->max_sh = o->max_shrink ? o->max_shrink : 64;
+    c->warps = o->warps_per_point;
+    c->dlogz = o->dlogz_stop > 0.0 ? o->dlogz_stop : 0.1;
+    c->seed = o->seed;
+    if (o->stream) {
+        c->stream = (cudaStream_t)o->stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete c;
+            return NS_ERR_CUDA;
+        }
+        c->own_stream = true;
+    }
+    if (o->model == NS_MODEL_TOY) {
+        M.model = M_TOY;
+        M.dim = o->toy_dim;
+        M.toy_lo = -10.0;
+        M.toy_hi = 10.0;
+        M.toy_rho = o->toy_dim > 1 ? 0.9 : 0.0;
+        // -1/2 log det(2 pi Sigma), det Sigma = (1 - rho^2)^(d-1)
+        M.toy_lognorm = -0.5 * (M.dim * std::log(2.0 * M_PI) + (M.dim - 1) * std::log(1.0 - M.toy_rho * M.toy_rho));
+        M.N = 1;
+        M.n_det = 1;
+    } else {
+        M.model = M_GW;
+        M.n_det = data->n_det;
+        M.N = grid->N;
+        M.ideal = data->ideal;
+        M.cutoff = o->no_cutoff ? 0 : 1;
+        M.f0 = grid->f0;
+        M.df = grid->df;
+        int dim = 0;
+        for (int p = 0; p < NS_NPARAM; p++) {
+            M.kind[p] = prior->kind[p];
+            M.lo[p] = prior->lo[p];
+            M.hi[p] = prior->kind[p] == NS_PRIOR_FIXED ? prior->lo[p] : prior->hi[p];
+            dim += prior->kind[p] != NS_PRIOR_FIXED;
+        }
+        M.dim = dim;
+        if (!data->ideal)
+            for (int dd = 0; dd < M.n_det; dd++)
+                for (int i = 0; i < 3; i++) {
+                    M.pos[dd][i] = data->pos[dd * 3 + i];
+                    M.xarm[dd][i] = data->xarm[dd * 3 + i];
+                    M.yarm[dd][i] = data->yarm[dd * 3 + i];
+                }
+    }
+    c->d = M.dim;
+    c->steps = (o->steps_per_dim ? o->steps_per_dim : 5) * M.dim;
+    const size_t N = M.N, nd = M.n_det, nn = nd * N;
+    if ((rc = dalloc(&c->d_re, nn)) || (rc = dalloc(&c->d_im, nn)) || (rc = dalloc(&c->d_psd, nn)) ||
+        (rc = dalloc(&c->basis64, NB * N)) || (rc = dalloc(&c->f64, N)) || (rc = dalloc(&c->prefix, nn)) ||
+        (rc = dalloc(&c->w64, nn)) || (rc = dalloc(&c->basis32, NB * N)) || (rc = dalloc(&c->f32, N)) ||
+        (rc = dalloc(&c->w32, nn)) || (rc = dalloc(&c->live_u, (size_t)c->n * c->d)) ||
+        (rc = dalloc(&c->live_logl, c->n)) || (rc = dalloc(&c->order, c->n)) ||
+        (rc = dalloc(&c->chol, (size_t)NS_MAX_DIM * NS_MAX_DIM)) || (rc = dalloc(&c->state, 1)) ||
+        (rc = dalloc(&c->fin_u, (size_t)c->n * c->d)) || (rc = dalloc(&c->fin_logl, c->n)) ||
+        (rc = dalloc(&c->fin_logw, c->n)) || (rc = dalloc(&c->fin_nlive, c->n)) ||
+        (rc = dalloc(&c->res, kReplicates + 8))) {
+        ns_free(c);
+        return rc;
+    }
+    if (cudaMallocHost((void **)&c->h_state, sizeof(RunState)) != cudaSuccess) { ns_free(c); return NS_ERR_OOM; }
+    c->timing = true;
+    for (cudaEvent_t &e : c->ev)
+        if (cudaEventCreate(&e) != cudaSuccess) { e = nullptr; c->timing = false; }
+    if ((rc = ensure_dead_capacity(c, 64LL * c->n))) { ns_free(c); return rc; }
+    cudaError_t e = cudaSuccess;
+    if (M.model == M_GW) {
+        e = cudaMemcpyAsync(c->d_psd, psd->S, nn * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess && data->re) {
+            e = cudaMemcpyAsync(c->d_re, data->re, nn * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(c->d_im, data->im, nn * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+        } else if (e == cudaSuccess) {
+            e = cudaMemsetAsync(c->d_re, 0, nn * sizeof(double), c->stream);
+            if (e == cudaSuccess) e = cudaMemsetAsync(c->d_im, 0, nn * sizeof(double), c->stream);
+        }
+        if (e == cudaSuccess)
+            e = launch_build_tables(M, c->d_re, c->d_im, c->d_psd, c->basis64, c->f64, c->w64, c->prefix,
+                                    c->basis32, c->f32, c->w32, c->stream);
+    }
+    if (e != cudaSuccess) { ns_free(c); return cuda_fail(e); }
+    c->T.basis64 = c->basis64;
+    c->T.f64 = c->f64;
+    c->T.w64 = c->w64;
+    c->T.prefix = c->prefix;
+    c->T.basis32 = c->basis32;
+    c->T.f32 = c->f32;
+    c->T.w32 = c->w32;
+    RunState s0;
+    std::memset(&s0, 0, sizeof(s0));
+    s0.logZ = -INFINITY;
+    s0.logX = 0.0;
+    s0.lstar = -INFINITY;
+    s0.evals = (unsigned long long)c->n;
+    *c->h_state = s0;
+    e = cudaMemcpyAsync(c->state, c->h_state, sizeof(RunState), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = launch_init_live(M, c->seed, c->n, c->live_u, c->stream);
+    if (e != cudaSuccess) { ns_free(c); return cuda_fail(e); }
+    if ((rc = eval_points(c, c->live_u, 0, c->n, c->live_logl))) { ns_free(c); return rc; }
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) { ns_free(c); return cuda_fail(e); }
+    *out = c;
+    return NS_OK;
+}
+
+int ns_set_data(ns_ctx *c, const double *re, const double *im) {
+    if (!c || !re || !im || c->M.model != M_GW) return NS_ERR_INVALID_ARG;
+    const size_t nn = (size_t)c->M.n_det * c->M.N;
+    CK(cudaMemcpyAsync(c->d_re, re, nn * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_im, im, nn * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(launch_build_tables(c->M, c->d_re, c->d_im, c->d_psd, c->basis64, c->f64, c->w64, c->prefix,
+                           c->basis32, c->f32, c->w32, c->stream));
+    int rc = eval_points(c, c->live_u, 0, c->n, c->live_logl);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(c->stream));
+    return NS_OK;
+}
+
+static int step_impl(ns_ctx *c, int k, int *done) {
+    if (!c) return NS_ERR_INVALID_ARG;
+    if (k < 1 || k > c->n - 1) return NS_ERR_K_RANGE;
+    int rc = ensure_dead_capacity(c, c->n_dead + k);
+    if (rc) return rc;
+    if ((rc = capture_iteration(c, k))) return rc;
+    CK(cudaGraphLaunch(c->graph, c->stream));
+    c->n_dead += k;
+    CK(cudaMemcpyAsync(c->h_state, c->state, sizeof(RunState), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (c->timing) {
+        for (int i = 0; i < 5; i++) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]) == cudaSuccess) c->kernel_ms[i] += ms;
+            else { cudaGetLastError(); c->timing = false; }
+        }
+    }
+    if (done) *done = c->h_state->done;
+    return NS_OK;
+}
+
+int ns_step(ns_ctx *c, int k, int *done) { return step_impl(c, k, done); }
+
+int ns_step_host(ns_ctx *c, int k, int *done, double *dead_u, double *dead_logl, double *dead_logw) {
+    int rc = step_impl(c, k, done);
+    if (rc) return rc;
+    const long long o = c->n_dead - k;
+    if (dead_u) CK(cudaMemcpyAsync(dead_u, c->dead_u + o * c->d, sizeof(double) * k * c->d, cudaMemcpyDeviceToHost, c->stream));
+    if (dead_logl) CK(cudaMemcpyAsync(dead_logl, c->dead_logl + o, sizeof(double) * k, cudaMemcpyDeviceToHost, c->stream));
+    if (dead_logw) CK(cudaMemcpyAsync(dead_logw, c->dead_logw + o, sizeof(double) * k, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return NS_OK;
+}
+
+int ns_run(ns_ctx *c, int max_iter, int *iterations) {
+    if (!c || max_iter < 0) return NS_ERR_INVALID_ARG;
+    int it = 0, done = 0;
+    while (it < max_iter && !done) {
+        int rc = ns_step(c, c->k_default, &done);
+        if (rc) return rc;
+        it++;
+    }
+    if (iterations) *iterations = it;
+    return NS_OK;
+}
+
+int ns_get_stats(ns_ctx *c, ns_stats *st) {
+    if (!c || !st) return NS_ERR_INVALID_ARG;
+    CK(cudaMemcpyAsync(c->h_state, c->state, sizeof(RunState), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    const RunState &s = *c->h_state;
+    st->iterations = s.iter;
+    st->evals = (long long)s.evals;
+    st->cap_hits = (long long)s.caps;
+    st->logZ = s.logZ;
+    st->logX = s.logX;
+    st->lstar = s.lstar;
+    st->logl_max = s.logl_max;
+    st->done = s.done;
+    st->d = c->d;
+    st->n_live = c->n;
+    st->n_dead = (int)c->n_dead;
+    st->point_bins = (long long)s.point_bins;
+    for (int i = 0; i < 5; i++) st->kernel_ms[i] = c->timing ? c->kernel_ms[i] : -1.0;
+    return NS_OK;
+}
+
+int ns_result(ns_ctx *c, double *logZ, double *dlogZ, ns_samples *smp) {
+    if (!c) return NS_ERR_INVALID_ARG;
+    const long long total = c->n_dead + c->n;
+    if (smp && smp->cap < total) { smp->count = (int)total; return NS_ERR_CAPACITY; }
+    StepArgs A = step_args(c, c->k_default);
+    CK(launch_select(c->live_logl, c->n, c->order, c->stream));
+    double *logz_total = c->res + kReplicates;
+    CK(launch_final_live(c->M, A, c->fin_u, c->fin_logl, c->fin_logw, c->fin_nlive, logz_total, c->stream));
+    double lz = 0.0;
+    CK(cudaMemcpyAsync(&lz, logz_total, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    ResultArgs R;
+    R.dead_logl = c->dead_logl; R.dead_logw = c->dead_logw; R.dead_nlive = c->dead_nlive;
+    R.fin_logl = c->fin_logl; R.fin_logw = c->fin_logw; R.fin_nlive = c->fin_nlive;
+    R.n_dead = c->n_dead; R.n = c->n; R.logZ = lz; R.reps = c->res; R.out = c->res + kReplicates + 1;
+    R.seed = c->seed; R.R = kReplicates;
+    CK(launch_result_stats(R, c->stream));
+    double out4[4];
+    CK(cudaMemcpyAsync(out4, R.out, sizeof(out4), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (logZ) *logZ = lz;
+    if (dlogZ) *dlogZ = out4[0];
+    if (smp) {
+        const long long nd = c->n_dead;
+        const int d = c->d;
+        if (smp->u) {
+            CK(cudaMemcpyAsync(smp->u, c->dead_u, sizeof(double) * nd * d, cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaMemcpyAsync(smp->u + nd * d, c->fin_u, sizeof(double) * c->n * d, cudaMemcpyDeviceToHost, c->stream));
+        }
+        if (smp->logl) {
+            CK(cudaMemcpyAsync(smp->logl, c->dead_logl, sizeof(double) * nd, cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaMemcpyAsync(smp->logl + nd, c->fin_logl, sizeof(double) * c->n, cudaMemcpyDeviceToHost, c->stream));
+        }
+        if (smp->logw) {
+            CK(cudaMemcpyAsync(smp->logw, c->dead_logw, sizeof(double) * nd, cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaMemcpyAsync(smp->logw + nd, c->fin_logw, sizeof(double) * c->n, cudaMemcpyDeviceToHost, c->stream));
+        }
+        if (smp->theta && c->M.model == M_GW) {
+            int rc = ensure_scratch(c, sizeof(double) * (size_t)total * (NS_NPARAM + d));
+            if (rc) return rc;
+            double *u_all = c->scratch, *th = c->scratch + (size_t)total * d;
+            CK(cudaMemcpyAsync(u_all, c->dead_u, sizeof(double) * nd * d, cudaMemcpyDeviceToDevice, c->stream));
+            CK(cudaMemcpyAsync(u_all + nd * d, c->fin_u, sizeof(double) * c->n * d, cudaMemcpyDeviceToDevice, c->stream));
+            CK(launch_theta(c->M, u_all, total, th, c->stream));
+            CK(cudaMemcpyAsync(smp->theta, th, sizeof(double) * total * NS_NPARAM, cudaMemcpyDeviceToHost, c->stream));
+        }
+        CK(cudaStreamSynchronize(c->stream));
+        smp->count = (int)total;
+    }
+    return NS_OK;
+}
+
+int ns_eval_lnl(ns_ctx *c, const double *u, int m, double *logl) {
+    if (!c || m < 0 || (m > 0 && (!u || !logl))) return NS_ERR_INVALID_ARG;
+    return eval_points(c, u, 0, m, logl);
+}
+
+int ns_eval_lnl_theta(ns_ctx *c, const double *theta, int m, double *logl) {
+    if (!c || m < 0 || (m > 0 && (!theta || !logl)) || c->M.model != M_GW) return NS_ERR_INVALID_ARG;
+    return eval_points(c, theta, 1, m, logl);
+}
+
+int ns_eval_lnl_host(ns_ctx *c, const double *u, int m, double *logl) {
+    if (!c || m < 0 || (m > 0 && (!u || !logl))) return NS_ERR_INVALID_ARG;
+    if (m == 0) return NS_OK;
+    int rc = ensure_scratch(c, sizeof(double) * (size_t)m * (c->d + 1));
+    if (rc) return rc;
+    double *du = c->scratch, *dl = c->scratch + (size_t)m * c->d;
+    CK(cudaMemcpyAsync(du, u, sizeof(double) * m * c->d, cudaMemcpyHostToDevice, c->stream));
+    if ((rc = eval_points(c, du, 0, m, dl))) return rc;
+    CK(cudaMemcpyAsync(logl, dl, sizeof(double) * m, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return NS_OK;
+}
+
+int ns_waveform(ns_ctx *c, const double *theta, double *h_re, double *h_im) {
+    if (!c || !theta || !h_re || !h_im || c->M.model != M_GW) return NS_ERR_INVALID_ARG;
+    const size_t nn = (size_t)c->M.n_det * c->M.N;
+    const size_t need = sizeof(double) * (NS_NPARAM + 2 * nn) + sizeof(Coef) + 64;
+    int rc = ensure_scratch(c, need);
+    if (rc) return rc;
+    double *th = c->scratch, *hr = th + NS_NPARAM, *hi = hr + nn;
+    Coef *cf = (Coef *)(((uintptr_t)(hi + nn) + 15) & ~(uintptr_t)15);
+    CK(cudaMemcpyAsync(th, theta, sizeof(double) * NS_NPARAM, cudaMemcpyHostToDevice, c->stream));
+    CK(launch_waveform(c->M, c->T, th, cf, hr, hi, c->stream));
+    CK(cudaMemcpyAsync(h_re, hr, sizeof(double) * nn, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(h_im, hi, sizeof(double) * nn, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return NS_OK;
+}
+
+int ns_prior_transform(ns_ctx *c, const double *u, int m, double *theta) {
+    if (!c || m < 0 || (m > 0 && (!u || !theta)) || c->M.model != M_GW) return NS_ERR_INVALID_ARG;
+    if (m == 0) return NS_OK;
+    int rc = ensure_scratch(c, sizeof(double) * (size_t)m * (c->d + NS_NPARAM));
+    if (rc) return rc;
+    double *du = c->scratch, *dt = c->scratch + (size_t)m * c->d;
+    CK(cudaMemcpyAsync(du, u, sizeof(double) * m * c->d, cudaMemcpyHostToDevice, c->stream));
+    CK(launch_theta(c->M, du, m, dt, c->stream));
+    CK(cudaMemcpyAsync(theta, dt, sizeof(double) * m * NS_NPARAM, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return NS_OK;
+}
+
+int ns_optimal_snr2(ns_ctx *c, const double *theta, double *rho2) {
+    if (!c || !theta || !rho2 || c->M.model != M_GW) return NS_ERR_INVALID_ARG;
+    int rc = ensure_scratch(c, sizeof(double) * NS_NPARAM + sizeof(Coef) + 64);
+    if (rc) return rc;
+    double *th = c->scratch;
+    Coef *cf = (Coef *)(((uintptr_t)(th + NS_NPARAM) + 15) & ~(uintptr_t)15);
+    CK(cudaMemcpyAsync(th, theta, sizeof(double) * NS_NPARAM, cudaMemcpyHostToDevice, c->stream));
+    CK(launch_point_coef(c->M, c->T, th, cf, c->stream));
+    CK(cudaMemcpyAsync(rho2, &cf->hh, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return NS_OK;
+}
+
+int ns_get_live(ns_ctx *c, double *u, double *logl) {
+    if (!c) return NS_ERR_INVALID_ARG;
+    if (u) CK(cudaMemcpyAsync(u, c->live_u, sizeof(double) * c->n * c->d, cudaMemcpyDeviceToHost, c->stream));
+    if (logl) CK(cudaMemcpyAsync(logl, c->live_logl, sizeof(double) * c->n, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return NS_OK;
+}
+
+int ns_set_live(ns_ctx *c, const double *u, const double *logl) {
+    if (!c || !u || !logl) return NS_ERR_INVALID_ARG;
+    CK(cudaMemcpyAsync(c->live_u, u, sizeof(double) * c->n * c->d, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->live_logl, logl, sizeof(double) * c->n, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return NS_OK;
+}
+
+int ns_sync(ns_ctx *c) {
+    if (!c) return NS_ERR_INVALID_ARG;
+    CK(cudaStreamSynchronize(c->stream));
+    return NS_OK;
+}
+
+}  // extern "C"

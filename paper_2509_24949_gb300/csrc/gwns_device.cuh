@@ -1,0 +1,411 @@
+// gwns_device.cuh -- device-side building blocks of the nested-slice-sampling
+// hot path on sm_103a: problem description, Philox4x32-10, prior transform,
+// per-point waveform coefficients, and the per-bin likelihood loops in FP64 and
+// in mixed precision (double-float phase, FP32 sincos and products).
+//
+// The likelihood is the Whittle log-likelihood ratio of a TaylorF2 signal
+// (paper Sec. 3 uses the same likelihood with an IMRPhenomD waveform):
+//   log L = sum_d [ Re(G_d Z_d) - <h_d|h_d>/2 ],
+//   Z_d   = sum_{j <= jcut} w_dj exp(i Psi_dj),  w_dj = 4 df f_j^(-7/6) d_dj / S_dj,
+//   G_d   = A conj(Q_d),  Q_d = F+ (1 + cos^2 i)/2 - i Fx cos i,
+//   Psi_dj = sum_m a_m B_m(f_j) + c0 + 2 pi f_j (t_c + dt_d),
+//   <h_d|h_d> = A^2 |Q_d|^2 P_d(jcut),  P_d(j) = sum_{i <= j} 4 df f_i^(-7/3) / S_di,
+// with the TaylorF2 phase written as a dot product of per-point coefficients
+// a_m with the per-grid basis B = {f^-5/3, f^-1, f^-2/3, f^-1/3, ln f, f^1/3,
+// f^1/3 ln f, f^2/3}, so that no transcendental of f is evaluated per bin.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gwns {
+
+constexpr int NPARAM = 11;
+constexpr int MAXD = 16;
+constexpr int MAXDET = 4;
+constexpr int NB = 8;
+
+enum { P_MC = 0, P_Q, P_CHI1, P_CHI2, P_DL, P_COSI, P_PSI, P_PHIC, P_TC, P_RA, P_SINDEC };
+enum { K_FIXED = 0, K_UNIFORM = 1, K_VOLUME = 2 };
+enum { M_GW = 0, M_TOY = 1 };
+
+constexpr double TSUN = 4.925490947641267e-6;   // G Msun / c^3 [s]
+constexpr double C_SI = 299792458.0;
+constexpr double MPC_SI = 3.085677581491367e22;
+constexpr double GAMMA_E = 0.5772156649015329;
+constexpr double PI_D = 3.141592653589793;
+constexpr double TWO_PI_D = 6.283185307179586;
+constexpr double INV_TWO_PI_D = 0.15915494309189535;
+
+// Problem description passed by value to every kernel.
+struct Model {
+    int model;        // M_GW or M_TOY
+    int n_det, N, ideal, cutoff, dim;
+    double f0, df;
+    int kind[NPARAM];
+    double lo[NPARAM], hi[NPARAM];
+    double pos[MAXDET][3], xarm[MAXDET][3], yarm[MAXDET][3];
+    // toy: x = toy_lo + (toy_hi - toy_lo) u, Sigma_ij = rho^|i-j|
+    double toy_lo, toy_hi, toy_rho, toy_lognorm;
+};
+
+// Device tables of one grid.
+struct Tables {
+    const double *basis64;   // [NB][N]   B_m(f_j)
+    const double *f64;       // [N]       f_j
+    const double2 *w64;      // [n_det][N] weighted data
+    const double *prefix;    // [n_det][N] P_d(j)
+    const float2 *basis32;   // [NB][N]   B_m(f_j) as (hi, lo) floats
+    const float2 *f32;       // [N]       f_j as (hi, lo)
+    const float2 *w32;       // [n_det][N]
+};
+
+// Per-point likelihood coefficients.
+struct Coef {
+    double a[NB];          // phase coefficients [rad per basis unit]
+    double c0;             // constant phase [rad]
+    double tau[MAXDET];    // t_c + dt_d [s]
+    double gre[MAXDET], gim[MAXDET];   // G_d = A conj(Q_d)
+    double hh;             // sum_d <h_d|h_d>
+    double toy;            // toy model log L
+    int jcut;              // last bin with f_j <= f_ISCO (-1: none)
+    int pad;
+};
+
+// Mixed-precision view of the coefficients: phase in turns as (hi, lo) floats.
+struct CoefMixed {
+    float ah[NB], al[NB];
+    float c0h, c0l;
+    float tauh[MAXDET], taul[MAXDET];
+};
+
+// ------------------------------------------------------------------ Philox
+// Philox4x32-10 (Salmon et al. 2011): 10 rounds of the multiply-xor bijection
+// with the Weyl key schedule.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; r++) {
+        uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// Draw-stream layout (key = 64-bit seed): counter = (slot, step, index, iteration).
+constexpr uint32_t SLOT_OFFSET = 16u;
+constexpr uint32_t SLOT_SHRINK0 = 17u;
+constexpr uint32_t STEP_START = 0xFFFFFFFFu;
+constexpr uint32_t ITER_INIT = 0xFFFFFFFFu;
+constexpr uint32_t ITER_REPLICATE = 0xFFFFFFFEu;
+
+__device__ __forceinline__ uint4 draw(uint64_t seed, uint32_t slot, uint32_t step, uint32_t idx,
+                                      uint32_t iter) {
+    return philox4x32_10(make_uint4(slot, step, idx, iter), (uint32_t)seed, (uint32_t)(seed >> 32));
+}
+
+// Uniform in (0,1): 26 + 26 bits of two words, (x + 1/2) 2^-52 (exact in FP64).
+__device__ __forceinline__ double u01(uint32_t a, uint32_t b) {
+    uint64_t x = ((uint64_t)(a >> 6) << 26) | (uint64_t)(b >> 6);
+    return ((double)x + 0.5) * 2.220446049250313e-16;
+}
+
+// ------------------------------------------------------------ prior transform
+__device__ __forceinline__ double prior_one(const Model &M, int p, double u) {
+    double lo = M.lo[p], hi = M.hi[p];
+    if (M.kind[p] == K_UNIFORM) return __dadd_rn(lo, __dmul_rn(__dsub_rn(hi, lo), u));
+    double lo3 = lo * lo * lo, hi3 = hi * hi * hi;
+    return cbrt(__dadd_rn(lo3, __dmul_rn(u, __dsub_rn(hi3, lo3))));
+}
+
+// u[dim] -> theta[11], in parameter order (fixed parameters take lo).
+__device__ __forceinline__ void prior_transform(const Model &M, const double *u, double *th) {
+    int i = 0;
+#pragma unroll
+    for (int p = 0; p < NPARAM; p++) {
+        if (M.kind[p] == K_FIXED) th[p] = M.lo[p];
+        else th[p] = prior_one(M, p, u[i++]);
+    }
+}
+
+// --------------------------------------------------------- point coefficients
+// Last grid index with f0 + j df <= fisco, in [-1, N-1]; the comparison uses the
+// same rounded frequency f0 + j*df as the tables.
+__device__ __forceinline__ int cutoff_index(const Model &M, double fisco) {
+    if (!M.cutoff) return M.N - 1;
+    double jf = floor((fisco - M.f0) / M.df);
+    if (jf < -1.0) return -1;
+    if (jf > (double)(M.N - 1)) return M.N - 1;
+    int j = (int)jf;
+    while (j + 1 <= M.N - 1 && __dadd_rn(M.f0, __dmul_rn((double)(j + 1), M.df)) <= fisco) j++;
+    while (j >= 0 && __dadd_rn(M.f0, __dmul_rn((double)j, M.df)) > fisco) j--;
+    return j;
+}
+
+// Per-point coefficients computed by one warp: parameter-only quantities are
+// computed redundantly by every lane (uniform control flow, so they cost one
+// warp instruction each), transcendentals of independent arguments are packed
+// into different lanes of one call, and the detector terms run on lanes
+// 0 .. n_det-1. Writes *out (shared memory) from lane 0 and the detector lanes.
+// u: the point's unit-cube coordinates (shared or global, read by all lanes).
+__device__ inline void point_coef_warp(const Model &M, const Tables &T, const double *u, Coef *out) {
+    const int lane = threadIdx.x & 31;
+    if (M.model == M_TOY) {
+        // log N(x; 0, Sigma) with Sigma_ij = rho^|i-j|: the inverse is tridiagonal,
+        // (1/(1-rho^2)) [diag(1, 1+rho^2, ..., 1+rho^2, 1), off-diagonal -rho].
+        int d = M.dim;
+        double rho = M.toy_rho;
+        double xi = 0.0, xn = 0.0;
+        if (lane < d) xi = M.toy_lo + (M.toy_hi - M.toy_lo) * u[lane];
+        if (lane + 1 < d) xn = M.toy_lo + (M.toy_hi - M.toy_lo) * u[lane + 1];
+        double diag = (lane == 0 || lane == d - 1) ? 1.0 : 1.0 + rho * rho;
+        double term = 0.0;
+        if (lane < d) term = diag * xi * xi - ((lane + 1 < d) ? 2.0 * rho * xi * xn : 0.0);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) term += __shfl_xor_sync(0xffffffffu, term, o);
+        if (lane == 0) {
+            out->toy = -0.5 * term / (1.0 - rho * rho) + M.toy_lognorm;
+            out->jcut = -1;
+            out->hh = 0.0;
+        }
+        return;
+    }
+    double th[NPARAM];
+    prior_transform(M, u, th);
+    const double q = th[P_Q];
+    const double opq = 1.0 + q;
+    const double eta = q / (opq * opq);
+    const double delta = (1.0 - q) / opq;          // (m1 - m2)/M, m1 >= m2
+    const double chis = 0.5 * (th[P_CHI1] + th[P_CHI2]);
+    const double chia = 0.5 * (th[P_CHI1] - th[P_CHI2]);
+    const double tmc = th[P_MC] * TSUN;
+    // packed logs: lane 0 ln(eta), lane 1 ln(T_Mc)
+    double lg = log(lane == 0 ? eta : tmc);
+    const double ln_eta = __shfl_sync(0xffffffffu, lg, 0);
+    const double ln_tmc = __shfl_sync(0xffffffffu, lg, 1);
+    // ln(pi T_M) with T_M = T_Mc eta^(-3/5); a = (pi T_M)^(1/3)
+    const double ln_x = 1.1447298858494002 + ln_tmc - 0.6 * ln_eta;   // ln(pi) + ...
+    const double ln_a = ln_x * (1.0 / 3.0);
+    // packed exps: lane 0 a = exp(ln_a), lane 1 T_Mc^(5/6), lane 2 1/(pi T_M)
+    double ex_arg = (lane == 0) ? ln_a : (lane == 1 ? (5.0 / 6.0) * ln_tmc : -ln_x);
+    double ex = exp(ex_arg);
+    const double a = __shfl_sync(0xffffffffu, ex, 0);
+    const double tmc56 = __shfl_sync(0xffffffffu, ex, 1);
+    const double inv_pitm = __shfl_sync(0xffffffffu, ex, 2);
+    // f_ISCO = 1/(6^(3/2) pi T_M)
+    const double fisco = inv_pitm * 0.06804138174397717;   // 6^(-3/2)
+    const int jcut = cutoff_index(M, fisco);
+
+    // TaylorF2 phasing coefficients (3.5PN non-spinning + aligned-spin terms)
+    const double pi = PI_D;
+    const double beta = (113.0 / 12.0) * (chis + delta * chia - (76.0 / 113.0) * eta * chis);
+    const double sigma = (79.0 / 8.0) * eta * th[P_CHI1] * th[P_CHI2];
+    const double gamma = (732985.0 / 2268.0 - 24260.0 / 81.0 * eta - 340.0 / 9.0 * eta * eta) * chis
+                       + (732985.0 / 2268.0 + 140.0 / 9.0 * eta) * delta * chia;
+    const double phi2 = 3715.0 / 756.0 + 55.0 / 9.0 * eta;
+    const double phi3 = -16.0 * pi + 4.0 * beta;
+    const double phi4 = 15293365.0 / 508032.0 + 27145.0 / 504.0 * eta + 3085.0 / 72.0 * eta * eta
+                      - 10.0 * sigma;
+    const double phi5 = pi * (38645.0 / 756.0 - 65.0 / 9.0 * eta) - gamma;   // times (1 + 3 ln(v sqrt 6))
+    const double phi6 = 11583231236531.0 / 4694215680.0 - 640.0 / 3.0 * pi * pi
+                      - 6848.0 / 21.0 * GAMMA_E
+                      + eta * (-15737765635.0 / 3048192.0 + 2255.0 / 12.0 * pi * pi)
+                      + 76055.0 / 1728.0 * eta * eta - 127825.0 / 1296.0 * eta * eta * eta;
+    const double phi7 = pi * (77096675.0 / 254016.0 + 378515.0 / 1512.0 * eta - 74045.0 / 756.0 * eta * eta);
+    // v = a f^(1/3): K v^(k-5) = K a^(k-5) f^((k-5)/3), K = 3/(128 eta)
+    const double K = 3.0 / (128.0 * eta);
+    const double ia = 1.0 / a;
+    const double ia2 = ia * ia;
+    const double ia3 = ia2 * ia;
+    const double ia5 = ia3 * ia2;
+    const double ln_sqrt6 = 0.8958797346140275;
+    const double ln4 = 1.3862943611198906;
+    if (lane == 0) {
+        out->a[0] = K * ia5;                       // f^(-5/3)
+        out->a[1] = K * phi2 * ia3;                // f^(-1)
+        out->a[2] = K * phi3 * ia2;                // f^(-2/3)
+        out->a[3] = K * phi4 * ia;                 // f^(-1/3)
+        out->a[4] = K * phi5;                      // ln f   (3 ln v = 3 ln a + ln f)
+        out->a[5] = K * a * (phi6 - 6848.0 / 21.0 * (ln4 + ln_a));   // f^(1/3)
+        out->a[6] = -K * a * (6848.0 / 63.0);      // f^(1/3) ln f
+        out->a[7] = K * phi7 * a * a;              // f^(2/3)
+        double c0 = -th[P_PHIC] - 0.25 * pi + K * phi5 * (1.0 + 3.0 * ln_sqrt6 + 3.0 * ln_a);
+        out->c0 = c0 - TWO_PI_D * rint(c0 * INV_TWO_PI_D);
+        out->jcut = jcut;
+    }
+    // amplitude A = sqrt(5/24) pi^(-2/3) c T_Mc^(5/6) / D_L
+    const double amp = 0.21278751013966343 * C_SI * tmc56 / (th[P_DL] * MPC_SI);
+    const double ci = th[P_COSI];
+    // antenna patterns and delays on detector lanes; packed sincos of ra (lane 0) and psi (lane 1)
+    double sn, cs;
+    sincos(lane == 0 ? th[P_RA] : th[P_PSI], &sn, &cs);
+    const double sa = __shfl_sync(0xffffffffu, sn, 0), ca = __shfl_sync(0xffffffffu, cs, 0);
+    const double sp = __shfl_sync(0xffffffffu, sn, 1), cp = __shfl_sync(0xffffffffu, cs, 1);
+    double hh_part = 0.0;
+    if (lane < M.n_det) {
+        const int dd = lane;
+        double fp, fc, dt;
+        if (M.ideal) {
+            fp = 1.0; fc = 0.0; dt = 0.0;
+        } else {
+            const double sd = th[P_SINDEC];
+            const double cd = sqrt(1.0 - sd * sd);
+            // wave-frame basis X, Y (Anderson et al. 2001) and source direction n
+            const double X0 = sa * cp - sp * ca * sd, X1 = -ca * cp - sp * sa * sd, X2 = sp * cd;
+            const double Y0 = -sa * sp - cp * ca * sd, Y1 = ca * sp - cp * sa * sd, Y2 = cp * cd;
+            const double *x = M.xarm[dd], *y = M.yarm[dd];
+            // D = (x x^T - y y^T)/2: X^T D Y = ((x.X)(x.Y) - (y.X)(y.Y))/2
+            const double xX = x[0] * X0 + x[1] * X1 + x[2] * X2;
+            const double xY = x[0] * Y0 + x[1] * Y1 + x[2] * Y2;
+            const double yX = y[0] * X0 + y[1] * X1 + y[2] * X2;
+            const double yY = y[0] * Y0 + y[1] * Y1 + y[2] * Y2;
+            fp = 0.5 * ((xX * xX - yX * yX) - (xY * xY - yY * yY));
+            fc = (xX * xY - yX * yY);
+            const double *r = M.pos[dd];
+            dt = -(r[0] * cd * ca + r[1] * cd * sa + r[2] * sd) / C_SI;
+        }
+        const double qre = fp * 0.5 * (1.0 + ci * ci);
+        const double qim = -fc * ci;
+        out->tau[dd] = th[P_TC] + dt;
+        out->gre[dd] = amp * qre;
+        out->gim[dd] = -amp * qim;
+        if (jcut >= 0) hh_part = amp * amp * (qre * qre + qim * qim) * T.prefix[(size_t)dd * M.N + jcut];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) hh_part += __shfl_xor_sync(0xffffffffu, hh_part, o);
+    if (lane == 0) out->hh = hh_part;
+}
+
+// Split a double into (hi, lo) floats.
+__device__ __forceinline__ void split_df(double x, float &h, float &l) {
+    h = __double2float_rn(x);
+    l = __double2float_rn(x - (double)h);
+}
+
+// Mixed-precision coefficients (phase in turns), from lane-parallel conversions.
+__device__ __forceinline__ void coef_to_mixed_warp(const Coef &c, int n_det, CoefMixed *m) {
+    const int lane = threadIdx.x & 31;
+    if (lane < NB) split_df(c.a[lane] * INV_TWO_PI_D, m->ah[lane], m->al[lane]);
+    else if (lane == NB) split_df(c.c0 * INV_TWO_PI_D, m->c0h, m->c0l);
+    else if (lane >= 16 && lane < 16 + n_det) split_df(c.tau[lane - 16], m->tauh[lane - 16], m->taul[lane - 16]);
+}
+
+// ------------------------------------------------------------ bin loops
+// FP64: Psi_j from the basis (FP64 FMAs), exp(i Psi_j) by sincos, the detector
+// factor exp(2 pi i f_j tau_d) by a rotation recurrence along the thread's bins
+// (f advances by stride*df per step).
+template <int NDET>
+__device__ __forceinline__ void bins_fp64(const Tables &T, int N, double f0, double df, const Coef &c,
+                                          int tid, int stride, double zr[NDET], double zi[NDET]) {
+    double a[NB];
+#pragma unroll
+    for (int m = 0; m < NB; m++) a[m] = c.a[m];
+    const double c0 = c.c0;
+    double rr[NDET], ri[NDET], pr[NDET], pi_[NDET];
+#pragma unroll
+    for (int d = 0; d < NDET; d++) {
+        zr[d] = 0.0; zi[d] = 0.0;
+        if (tid <= c.jcut) {
+            sincos(TWO_PI_D * (f0 + tid * df) * c.tau[d], &ri[d], &rr[d]);
+            sincos(TWO_PI_D * (stride * df) * c.tau[d], &pi_[d], &pr[d]);
+        }
+    }
+    for (int j = tid; j <= c.jcut; j += stride) {
+        double psi = c0;
+#pragma unroll
+        for (int m = 0; m < NB; m++) psi = fma(a[m], __ldg(T.basis64 + (size_t)m * N + j), psi);
+        double s, co;
+        sincos(psi, &s, &co);
+#pragma unroll
+        for (int d = 0; d < NDET; d++) {
+            const double er = co * rr[d] - s * ri[d];
+            const double ei = co * ri[d] + s * rr[d];
+            const double2 w = __ldg(T.w64 + (size_t)d * N + j);
+            zr[d] = fma(w.x, er, fma(-w.y, ei, zr[d]));
+            zi[d] = fma(w.x, ei, fma(w.y, er, zi[d]));
+            const double nr = rr[d] * pr[d] - ri[d] * pi_[d];
+            ri[d] = rr[d] * pi_[d] + ri[d] * pr[d];
+            rr[d] = nr;
+        }
+    }
+}
+
+// Mixed: the phase in turns accumulated as a double-float dot product
+// (error-free FP32 products via FMA, TwoSum accumulation), reduced mod 1,
+// then FP32 __sincosf and FP32 products. Partial sums are flushed every
+// FLUSH bins into double-float accumulators (compensated summation).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ void df_acc(float &hi, float &lo, float x) {
+    float s, e;
+    two_sum(hi, x, s, e);
+    hi = s;
+    lo += e;
+}
+
+template <int NDET>
+__device__ __forceinline__ void bins_mixed(const Tables &T, int N, const CoefMixed &c, int jcut,
+                                           int tid, int stride, double zr[NDET], double zi[NDET]) {
+    float ah[NB], al[NB];
+#pragma unroll
+    for (int m = 0; m < NB; m++) { ah[m] = c.ah[m]; al[m] = c.al[m]; }
+    float th_[NDET], tl_[NDET];
+#pragma unroll
+    for (int d = 0; d < NDET; d++) { th_[d] = c.tauh[d]; tl_[d] = c.taul[d]; }
+    float zrh[NDET], zrl[NDET], zih[NDET], zil[NDET];
+#pragma unroll
+    for (int d = 0; d < NDET; d++) { zrh[d] = zrl[d] = zih[d] = zil[d] = 0.f; }
+    constexpr int FLUSH = 16;
+    int j = tid;
+    while (j <= jcut) {
+        float pr[NDET], pim[NDET];
+#pragma unroll
+        for (int d = 0; d < NDET; d++) { pr[d] = 0.f; pim[d] = 0.f; }
+        for (int it = 0; it < FLUSH && j <= jcut; it++, j += stride) {
+            float sh = c.c0h, sl = c.c0l;
+#pragma unroll
+            for (int m = 0; m < NB; m++) {
+                const float2 b = __ldg(T.basis32 + (size_t)m * N + j);
+                const float p = ah[m] * b.x;
+                float e = fmaf(ah[m], b.x, -p);
+                e = fmaf(ah[m], b.y, e);
+                e = fmaf(al[m], b.x, e);
+                float s, e2;
+                two_sum(sh, p, s, e2);
+                sh = s;
+                sl += e2 + e;
+            }
+            const float2 fj = __ldg(T.f32 + j);
+#pragma unroll
+            for (int d = 0; d < NDET; d++) {
+                const float p = th_[d] * fj.x;
+                float e = fmaf(th_[d], fj.x, -p);
+                e = fmaf(th_[d], fj.y, e);
+                e = fmaf(tl_[d], fj.x, e);
+                float s, e2;
+                two_sum(sh, p, s, e2);
+                const float n = rintf(s);
+                const float r = (s - n) + (sl + (e2 + e));
+                float sv, cv;
+                __sincosf(r * 6.283185307179586f, &sv, &cv);
+                const float2 w = __ldg(T.w32 + (size_t)d * N + j);
+                pr[d] = fmaf(w.x, cv, fmaf(-w.y, sv, pr[d]));
+                pim[d] = fmaf(w.x, sv, fmaf(w.y, cv, pim[d]));
+            }
+        }
+#pragma unroll
+        for (int d = 0; d < NDET; d++) { df_acc(zrh[d], zrl[d], pr[d]); df_acc(zih[d], zil[d], pim[d]); }
+    }
+#pragma unroll
+    for (int d = 0; d < NDET; d++) {
+        zr[d] = (double)zrh[d] + (double)zrl[d];
+        zi[d] = (double)zih[d] + (double)zil[d];
+    }
+}
+
+}  // namespace gwns

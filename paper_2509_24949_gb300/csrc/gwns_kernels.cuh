@@ -1,0 +1,78 @@
+// gwns_kernels.cuh -- kernel launch interface between the C ABI (gwns_abi.cu)
+// and the kernels (gwns_kernels.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gwns_device.cuh"
+
+namespace gwns {
+
+// Run state kept on the device (read by the kernels of one iteration, so that
+// an iteration can be replayed from a CUDA graph without host arguments).
+struct RunState {
+    double logZ;        // running log evidence of the dead points
+    double logX;        // log prior volume inside the live set
+    double lstar;       // current threshold
+    double logl_max;    // largest live log L (after the last iteration)
+    double remaining;   // log(Z + X Lmax) - log Z
+    unsigned long long evals;
+    unsigned long long caps;
+    unsigned long long point_bins;   // sum over evaluations in k_slice of (jcut + 1)
+    long long n_dead;
+    long long iter;
+    int done;
+    int status;
+};
+
+struct StepArgs {
+    double *live_u;       // [n][d]
+    double *live_logl;    // [n]
+    int *order;           // [n] ascending by (log L, index)
+    double *chol;         // [d][d] lower-triangular factor of the survivors' covariance
+    double *dead_u;       // [cap][d]
+    double *dead_logl;    // [cap]
+    double *dead_logw;    // [cap]
+    double *dead_nlive;   // [cap] live count at removal (n - j + 1)
+    RunState *state;
+    uint64_t seed;
+    int n, k, steps, max_stepout, max_shrink;
+    double dlogz_stop;
+};
+
+struct ResultArgs {
+    const double *dead_logl, *dead_logw, *dead_nlive;
+    const double *fin_logl, *fin_logw, *fin_nlive;   // [n] final live points, ascending
+    long long n_dead;
+    int n;
+    double logZ;          // total log Z
+    double *reps;         // [R]
+    double *out;          // [4]: dlogZ, H, ESS, mean of replicates
+    uint64_t seed;
+    int R;
+};
+
+// Launchers (return cudaGetLastError()).
+cudaError_t launch_build_tables(const Model &M, const double *data_re, const double *data_im,
+                                const double *psd, double *basis64, double *f64, double2 *w64,
+                                double *prefix, float2 *basis32, float2 *f32, float2 *w32,
+                                cudaStream_t s);
+cudaError_t launch_init_live(const Model &M, uint64_t seed, int n, double *live_u, cudaStream_t s);
+cudaError_t launch_eval(const Model &M, const Tables &T, int precision, int warps, const double *in,
+                        int in_is_theta, int m, double *logl, cudaStream_t s);
+cudaError_t launch_select(const double *logl, int n, int *order, cudaStream_t s);
+cudaError_t launch_evidence(const Model &M, const StepArgs &A, cudaStream_t s);
+cudaError_t launch_cov_chol(const Model &M, const StepArgs &A, cudaStream_t s);
+cudaError_t launch_slice(const Model &M, const Tables &T, int precision, int warps, const StepArgs &A,
+                         cudaStream_t s);
+cudaError_t launch_finish(const StepArgs &A, cudaStream_t s);
+cudaError_t launch_final_live(const Model &M, const StepArgs &A, double *fin_u, double *fin_logl,
+                              double *fin_logw, double *fin_nlive, double *logz_total, cudaStream_t s);
+cudaError_t launch_result_stats(const ResultArgs &R, cudaStream_t s);
+cudaError_t launch_theta(const Model &M, const double *u, long long m, double *theta, cudaStream_t s);
+cudaError_t launch_point_coef(const Model &M, const Tables &T, const double *theta, Coef *out,
+                              cudaStream_t s);
+cudaError_t launch_waveform(const Model &M, const Tables &T, const double *theta, Coef *scratch,
+                            double *h_re, double *h_im, cudaStream_t s);
+
+}  // namespace gwns

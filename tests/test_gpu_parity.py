@@ -1,0 +1,271 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the
+same seeded inputs.
+
+Tolerances: FP64 log L within 1e-9 relative (of max(|log L|, 1)); mixed
+precision within 1e-3 absolute; waveforms within 1e-10 of the peak strain.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import stats
+
+import gwinputs as gi
+import oracle
+from oracle import ns as ons
+
+pytestmark = pytest.mark.gpu
+
+FP64_RTOL = 1e-9
+MIXED_ATOL = 1e-3
+
+
+def sampler_from(g, pb, precision=0, **kw):
+    args = dict(kind=pb.kind, lo=pb.lo, hi=pb.hi, data=pb.data(), psd=pb.psd, f0=pb.f0, df=pb.df,
+                pos=pb.pos, xarm=pb.xarm, yarm=pb.yarm, ideal=pb.ideal, no_cutoff=not pb.cutoff,
+                precision=precision)
+    args.update(kw)
+    return g.Sampler(**args)
+
+
+_PROBLEMS = {}
+
+
+def problem(name, **over):
+    key = (name, tuple(sorted(over.items())))
+    if key not in _PROBLEMS:
+        w = gi.workload(name, **over)
+        _PROBLEMS[key] = (w,) + oracle.make_problem(w)
+    return _PROBLEMS[key]
+
+
+def pts_for(pb, th_inj, count=160, seed=17):
+    u = gi.unit_cube(seed, count, pb.dim)
+    # prior corners and faces
+    u[0] = 1e-12
+    u[1] = 1.0 - 1e-12
+    u[2, ::2] = 1e-12
+    u[3, 1::2] = 1.0 - 1e-12
+    return u
+
+
+@pytest.mark.parametrize("name,over", [
+    ("c0", {}),
+    ("c1", {}),
+    ("c1", {"N": 1013}),            # ragged tail
+    ("c1", {"N": 33, "df": 4.0}),    # tiny grid
+    ("c1", {"n_det": 1}),
+    ("c1", {"n_det": 2}),
+])
+@pytest.mark.parametrize("warps", [1, 4])
+def test_lnl_fp64_parity(gw, name, over, warps):
+    w, pb, th = problem(name, **over)
+    u = pts_for(pb, th)
+    want = pb.loglike(u)
+    with sampler_from(gw, pb, 0, n_live=8, warps_per_point=warps) as sp:
+        got = sp.eval_lnl(u)
+    err = np.abs(got - want) / np.maximum(1.0, np.abs(want))
+    assert np.max(err) < FP64_RTOL, (np.max(err), np.argmax(err))
+
+
+@pytest.mark.parametrize("name,over", [("c0", {}), ("c1", {}), ("c1", {"N": 1013}),
+                                       ("c1", {"N": 33, "df": 4.0})])
+@pytest.mark.parametrize("warps", [1, 2, 8])
+def test_lnl_mixed_parity(gw, name, over, warps):
+    w, pb, th = problem(name, **over)
+    u = pts_for(pb, th)
+    want = pb.loglike(u)
+    with sampler_from(gw, pb, 1, n_live=8, warps_per_point=warps) as sp:
+        got = sp.eval_lnl(u)
+    assert np.max(np.abs(got - want)) < MIXED_ATOL, np.max(np.abs(got - want))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("name", ["c2", "c4"])
+def test_lnl_full_size_sampled(gw, name, precision):
+    """Full-size grids (64,897 and 519,169 bins): sampled points, including the
+    injection, against the oracle evaluated one by one."""
+    w, pb, th = problem(name)
+    u = gi.unit_cube(23, 6, pb.dim)
+    want = pb.loglike(u)
+    with sampler_from(gw, pb, precision, n_live=8) as sp:
+        got = sp.eval_lnl(u)
+        import torch
+        tt = torch.tensor(th[None, :], dtype=torch.float64, device="cuda")
+        got_inj = sp.eval_lnl_theta(tt).cpu().numpy()[0]
+    want_inj = pb.loglike_theta(th)[0]
+    if precision == 0:
+        assert np.max(np.abs(got - want) / np.maximum(1, np.abs(want))) < FP64_RTOL
+        assert abs(got_inj - want_inj) / max(1, abs(want_inj)) < FP64_RTOL
+    else:
+        assert np.max(np.abs(got - want)) < MIXED_ATOL
+        assert abs(got_inj - want_inj) < MIXED_ATOL
+
+
+def test_lnl_device_pointer_path(gw):
+    import torch
+    w, pb, th = problem("c1")
+    u = gi.unit_cube(3, 64, pb.dim)
+    with sampler_from(gw, pb, 0, n_live=8) as sp:
+        dev = torch.tensor(u, dtype=torch.float64, device="cuda")
+        got = sp.eval_lnl(dev).cpu().numpy()
+        empty = sp.eval_lnl(torch.zeros((0, pb.dim), dtype=torch.float64, device="cuda"))
+    assert empty.numel() == 0
+    want = pb.loglike(u)
+    assert np.max(np.abs(got - want) / np.maximum(1, np.abs(want))) < FP64_RTOL
+
+
+def test_waveform_and_snr_parity(gw):
+    w, pb, th = problem("c1")
+    with sampler_from(gw, pb, 0, n_live=8) as sp:
+        h = sp.waveform(th)
+        rho2 = sp.snr2(th)
+        theta = sp.theta(gi.unit_cube(4, 50, pb.dim))
+    for d in range(pb.n_det):
+        ho = pb.strain(th, d)
+        assert np.max(np.abs(h[d] - ho)) < 1e-10 * np.max(np.abs(ho))
+    assert rho2 == pytest.approx(pb.snr2(th), rel=1e-10, abs=0)
+    assert np.max(np.abs(theta - pb.theta(gi.unit_cube(4, 50, pb.dim)))) < 1e-10
+
+
+def test_injection_identity_gpu(gw):
+    """Noise-free data: log L(theta_inj) = rho^2/2 on the GPU too."""
+    import torch
+    w, pb, th = problem("c1", noise=False)
+    for prec, tol in ((0, 1e-9 * 200), (1, MIXED_ATOL)):
+        with sampler_from(gw, pb, prec, n_live=8) as sp:
+            v = sp.eval_lnl_theta(torch.tensor(th[None], dtype=torch.float64, device="cuda")).item()
+        assert abs(v - w.snr ** 2 / 2) < tol
+
+
+def test_no_cutoff_and_empty_band(gw):
+    """The no-cutoff option, and points whose f_ISCO lies below the first bin
+    (jcut = -1, log L = 0)."""
+    w, pb, th = problem("c1", N=500)
+    pb2 = oracle.Problem(f0=pb.f0, df=pb.df, psd=pb.psd, data=pb.data(), pos=pb.pos, xarm=pb.xarm,
+                         yarm=pb.yarm, cutoff=False, kind=pb.kind, lo=pb.lo, hi=pb.hi)
+    u = gi.unit_cube(8, 40, pb.dim)
+    with sampler_from(gw, pb2, 0, n_live=8) as sp:
+        got = sp.eval_lnl(u)
+    want = pb2.loglike(u)
+    assert np.max(np.abs(got - want) / np.maximum(1, np.abs(want))) < FP64_RTOL
+    # grid starting at 400 Hz: heavy systems have f_ISCO < 400 Hz
+    pb3 = oracle.Problem(f0=400.0, df=pb.df, psd=pb.psd, data=pb.data(), pos=pb.pos, xarm=pb.xarm,
+                         yarm=pb.yarm, cutoff=True, kind=pb.kind, lo=pb.lo, hi=pb.hi)
+    with sampler_from(gw, pb3, 0, n_live=8) as sp:
+        got = sp.eval_lnl(u)
+    want = pb3.loglike(u)
+    assert np.sum(want == 0.0) > 5
+    assert np.max(np.abs(got - want) / np.maximum(1, np.abs(want))) < FP64_RTOL
+
+
+# ------------------------------------------------------------ sampler parity
+def _ns_pair(gw, name, n_live, k, precision=0, **over):
+    w, pb, th = problem(name, **over)
+    sp = sampler_from(gw, pb, precision, n_live=n_live, k=k, steps_per_dim=w.steps_per_dim,
+                      seed=w.seed_sampler)
+    st = ons.initial_state(pb, n_live, w.seed_sampler)
+    return w, pb, sp, st
+
+
+@pytest.mark.parametrize("name,n_live,k,iters", [("c0", 200, 100, 4), ("c1", 120, 60, 2)])
+def test_ns_iterations_match_oracle(gw, name, n_live, k, iters):
+    """Same Philox draws on both sides: the live set after each iteration and
+    the evidence bookkeeping match the oracle's."""
+    w, pb, sp, st = _ns_pair(gw, name, n_live, k)
+    u0, l0 = sp.live()
+    assert np.max(np.abs(u0 - st.live_u)) == 0.0
+    assert np.max(np.abs(l0 - st.live_logl) / np.maximum(1, np.abs(st.live_logl))) < FP64_RTOL
+    for it in range(iters):
+        info = ons.iterate(pb, st, k, w.steps_per_dim * pb.dim, w.seed_sampler)
+        sp.step(k)
+        gu, gl = sp.live()
+        s = sp.stats()
+        assert s["lstar"] == pytest.approx(info["lstar"], rel=1e-9, abs=1e-9)
+        assert np.max(np.abs(gu - st.live_u)) < 1e-9, (it, np.max(np.abs(gu - st.live_u)))
+        assert np.max(np.abs(gl - st.live_logl) / np.maximum(1, np.abs(st.live_logl))) < 1e-8
+        assert s["logX"] == pytest.approx(st.logX, rel=1e-12)
+        assert s["logZ"] == pytest.approx(st.logZ, rel=1e-9, abs=1e-9)
+        assert s["evals"] == st.evals
+    sp.close()
+
+
+def test_ns_step_host_dead_points(gw):
+    w, pb, sp, st = _ns_pair(gw, "c0", 100, 50)
+    k, d = 50, pb.dim
+    du, dl, dw = np.zeros((k, d)), np.zeros(k), np.zeros(k)
+    order = np.argsort(st.live_logl, kind="stable")
+    sp.step_host(k, du, dl, dw)
+    ons.iterate(pb, st, k, w.steps_per_dim * d, w.seed_sampler)
+    assert np.max(np.abs(du - st.dead_u[0])) == 0.0
+    assert np.max(np.abs(dw - st.dead_logw[0])) < 1e-12
+    sp.close()
+
+
+def test_toy_evidence_gpu(gw):
+    """Correlated-Gaussian toy, analytic log Z = -d ln 20."""
+    d = 4
+    truth = -d * math.log(20.0)
+    hits = 0
+    for s in range(6):
+        with gw.Sampler(model=gw.NS_MODEL_TOY, toy_dim=d, n_live=200, k=100, steps_per_dim=5,
+                        seed=300 + s) as sp:
+            sp.run()
+            r = sp.result(samples=False)
+        hits += abs(r["logZ"] - truth) < 3 * r["dlogZ"]
+    assert hits >= 5
+
+
+def test_toy_run_matches_oracle_run(gw):
+    """Whole toy run: same seed, same draws, same evidence and replicates."""
+    d = 4
+    pb = oracle.toy_problem(d)
+    ref = ons.run(pb, n_live=100, k=50, steps=5 * d, seed=42, replicates=200)
+    with gw.Sampler(model=gw.NS_MODEL_TOY, toy_dim=d, n_live=100, k=50, steps_per_dim=5, seed=42) as sp:
+        it = sp.run()
+        r = sp.result()
+    assert it == ref["iterations"]
+    assert r["logZ"] == pytest.approx(ref["logZ"], rel=1e-10, abs=1e-10)
+    assert r["dlogZ"] == pytest.approx(ref["dlogZ"], rel=1e-8)
+    assert np.max(np.abs(r["logl"] - ref["logl"])) < 1e-9
+    assert np.max(np.abs(r["logw"] - ref["logw"])) < 1e-9
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_c0_run_against_oracle(gw, precision):
+    """Single-detector workload end to end: log Z within 3 combined sigma of
+    the oracle's and per-parameter posterior KS p > 0.01."""
+    w, pb, th = problem("c0")
+    ref = ons.run(pb, n_live=w.n_live, k=w.k, steps=w.steps_per_dim * pb.dim, seed=w.seed_sampler)
+    with sampler_from(gw, pb, precision, n_live=w.n_live, k=w.k, steps_per_dim=w.steps_per_dim,
+                      seed=w.seed_sampler) as sp:
+        sp.run()
+        r = sp.result()
+    sig = math.hypot(r["dlogZ"], ref["dlogZ"])
+    assert abs(r["logZ"] - ref["logZ"]) < 3 * sig
+    lw_g = r["logw"] + r["logl"] - r["logZ"]
+    lw_o = ref["logw"] + ref["logl"] - ref["logZ"]
+    sg = ons.equal_weight_resample(r["u"], lw_g, 1)
+    so = ons.equal_weight_resample(ref["samples_u"], lw_o, 2)
+    for i in range(pb.dim):
+        assert stats.ks_2samp(sg[:, i], so[:, i]).pvalue > 0.01
+
+
+def test_errors(gw):
+    w, pb, th = problem("c0")
+    with pytest.raises(gw.GWNSError) as e:
+        sampler_from(gw, pb, 0, n_live=1)
+    assert e.value.code == -1
+    bad = pb.psd.copy()
+    bad[0, 7] = 0.0
+    with pytest.raises(gw.GWNSError) as e:
+        gw.Sampler(kind=pb.kind, lo=pb.lo, hi=pb.hi, data=pb.data(), psd=bad, f0=pb.f0, df=pb.df,
+                   ideal=True, n_live=10)
+    assert e.value.code == -2
+    with sampler_from(gw, pb, 0, n_live=10) as sp:
+        with pytest.raises(gw.GWNSError) as e:
+            sp.step(10)
+        assert e.value.code == -3
+        with pytest.raises(gw.GWNSError) as e:
+            sp.step(-1)
+        assert e.value.code == -3
