@@ -200,6 +200,27 @@ int ns_eval_lnl(ns_ctx *ctx, const double *u, int m, double *logl);
 /* Same with host pointers (copies in, evaluates, copies out, synchronises). */
 int ns_eval_lnl_host(ns_ctx *ctx, const double *u, int m, double *logl);
 
+/* Allocation-free variant of ns_eval_lnl_host, for callers that cannot call
+ * cudaMalloc at this point: code running inside stream capture, real-time or
+ * callback contexts, and hosts whose device memory is reserved by another
+ * allocator. (The paper has no counterpart; this is an integration feature.)
+ * ns_eval_lnl_host stages u and log L in device scratch that it allocates on
+ * first use or when m grows; this entry point stages them instead in one
+ * file-scope device array of NS_NOALLOC_MAX_POINTS x (NS_MAX_DIM + 1) doubles
+ * (557,056 bytes) that every GPU loading the library holds until exit, and it
+ * calls no cudaMalloc/cudaFree. Host pointers: u [m][d] in, logl [m] out;
+ * synchronises the context's stream before returning.
+ *   - m > NS_NOALLOC_MAX_POINTS returns NS_ERR_CAPACITY (split the batch);
+ *   - the first call on a device looks up the array's device address once
+ *     (cudaGetSymbolAddress), so make that first call before any stream
+ *     capture;
+ *   - all calls share the array and it keeps the last call's contents (each
+ *     call overwrites the m entries it uses; nothing needs to start at zero);
+ *     calls that overlap on the GPU (other threads, other contexts on other
+ *     streams) race on it and must be serialised by the caller. */
+#define NS_NOALLOC_MAX_POINTS 4096
+int ns_eval_lnl_host_noalloc(ns_ctx *ctx, const double *u, int m, double *logl);
+
 /* Batched likelihood of m physical parameter vectors theta [m][11] (device). */
 int ns_eval_lnl_theta(ns_ctx *ctx, const double *theta, int m, double *logl);
 

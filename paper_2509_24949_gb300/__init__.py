@@ -23,6 +23,7 @@ NS_FP64, NS_MIXED = 0, 1
 NS_MODEL_GW, NS_MODEL_TOY = 0, 1
 NPARAM = 11
 NS_MAX_DET = 4
+NOALLOC_MAX_POINTS = 4096
 
 
 class GWNSError(RuntimeError):
@@ -98,6 +99,7 @@ def lib():
         L.ns_eval_lnl.argtypes = [vp, vp, ip, vp]
         L.ns_eval_lnl_host.argtypes = [vp, vp, ip, vp]
         L.ns_eval_lnl_theta.argtypes = [vp, vp, ip, vp]
+        L.ns_eval_lnl_host_noalloc.argtypes = [vp, vp, ip, vp]
         L.ns_waveform.argtypes = [vp, vp, vp, vp]
         L.ns_prior_transform.argtypes = [vp, vp, ip, vp]
         L.ns_optimal_snr2.argtypes = [vp, vp, P(dp)]
@@ -107,6 +109,7 @@ def lib():
         L.ns_free.argtypes = [vp]; L.ns_free.restype = None
         for name in ("ns_init", "ns_set_data", "ns_step", "ns_step_host", "ns_run", "ns_result",
                      "ns_get_stats", "ns_eval_lnl", "ns_eval_lnl_host", "ns_eval_lnl_theta",
+                     "ns_eval_lnl_host_noalloc",
                      "ns_waveform", "ns_prior_transform", "ns_optimal_snr2", "ns_get_live", "ns_set_live", "ns_sync"):
             getattr(L, name).restype = ctypes.c_int
         _LIB = L
@@ -264,6 +267,15 @@ class Sampler:
         _check(lib().ns_eval_lnl(self._ctx, u.data_ptr(), m, out.data_ptr()), "ns_eval_lnl")
         self.sync()
         return out
+
+    def eval_lnl_host_noalloc(self, u) -> np.ndarray:
+        """Host-buffer batched log L that allocates no device memory (at most
+        NOALLOC_MAX_POINTS points per call; see include/gwns.h)."""
+        u = _f64(u).reshape(-1, self.dim)
+        res = np.zeros(u.shape[0])
+        _check(lib().ns_eval_lnl_host_noalloc(self._ctx, _ptr(u), u.shape[0], _ptr(res)),
+               "ns_eval_lnl_host_noalloc")
+        return res
 
     def eval_lnl_theta(self, theta, out=None):
         import torch

@@ -549,6 +549,31 @@ int ns_eval_lnl_host(ns_ctx *c, const double *u, int m, double *logl) {
     return NS_OK;
 }
 
+int ns_eval_lnl_host_noalloc(ns_ctx *c, const double *u, int m, double *logl) {
+    if (!c || m < 0 || (m > 0 && (!u || !logl))) return NS_ERR_INVALID_ARG;
+    if (m > NS_NOALLOC_MAX_POINTS) return NS_ERR_CAPACITY;
+    if (m == 0) return NS_OK;
+    int prev = 0;
+    CK(cudaGetDevice(&prev));
+    if (prev != c->device) CK(cudaSetDevice(c->device));
+    double *base = nullptr;
+    cudaError_t e = noalloc_scratch_address(&base);
+    int rc = NS_OK;
+    if (e != cudaSuccess) {
+        rc = cuda_fail(e);
+    } else {
+        double *du = base, *dl = base + (size_t)m * c->d;
+        e = cudaMemcpyAsync(du, u, sizeof(double) * m * c->d, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) rc = eval_points(c, du, 0, m, dl);
+        if (e == cudaSuccess && rc == NS_OK)
+            e = cudaMemcpyAsync(logl, dl, sizeof(double) * m, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess && rc == NS_OK) e = cudaStreamSynchronize(c->stream);
+        if (rc == NS_OK && e != cudaSuccess) rc = cuda_fail(e);
+    }
+    if (prev != c->device) cudaSetDevice(prev);
+    return rc;
+}
+
 int ns_waveform(ns_ctx *c, const double *theta, double *h_re, double *h_im) {
     if (!c || !theta || !h_re || !h_im || c->M.model != M_GW) return NS_ERR_INVALID_ARG;
     const size_t nn = (size_t)c->M.n_det * c->M.N;

@@ -11,9 +11,37 @@
 #include <float.h>
 #include <math.h>
 
+#include <mutex>
+
 #include "gwns_kernels.cuh"
 
 namespace gwns {
+
+// File-scope staging array of the allocation-free host-buffer likelihood
+// entry point (ns_eval_lnl_host_noalloc). Every GPU that loads the library
+// holds these NOALLOC_DOUBLES doubles (557,056 bytes) until the process exits.
+// Host code must not pass the symbol itself to a kernel (on the host it is a
+// stand-in, not a device address): noalloc_scratch_address() returns the
+// device address obtained with cudaGetSymbolAddress.
+static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_DOUBLES];
+
+cudaError_t noalloc_scratch_address(double **ptr) {
+    static std::mutex mu;
+    static double *addr[64] = {nullptr};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        addr[dev] = (double *)p;
+    }
+    *ptr = addr[dev];
+    return cudaSuccess;
+}
 
 // ------------------------------------------------------------- warp helpers
 __device__ __forceinline__ double warp_sum(double v) {

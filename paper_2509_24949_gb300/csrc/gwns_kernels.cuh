@@ -52,6 +52,14 @@ struct ResultArgs {
     int R;
 };
 
+// Staging for the allocation-free host-buffer likelihood entry: up to
+// NOALLOC_MAX_POINTS points of up to MAXD coordinates plus their log L.
+constexpr int NOALLOC_MAX_POINTS = 4096;
+constexpr size_t NOALLOC_DOUBLES = (size_t)NOALLOC_MAX_POINTS * (MAXD + 1);
+// Device address of that staging array on the current device (looked up once
+// per device and cached; never allocates).
+cudaError_t noalloc_scratch_address(double **ptr);
+
 // Launchers (return cudaGetLastError()).
 cudaError_t launch_build_tables(const Model &M, const double *data_re, const double *data_im,
                                 const double *psd, double *basis64, double *f64, double2 *w64,
