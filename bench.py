@@ -48,6 +48,9 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # detectors, in FMA-equivalents: 8 basis FMAs + one sincos (32 FMA-equivalents
 # on this GPU) + per detector 4 (phasor product) + 4 (complex MAC) + 4
 # (phasor rotation). 1 FMA = 2 flops.
+K_SLICE_FP64_C1_DRAM_BYTES = 647680
+
+
 def fp64_flops_per_point_bin(n_det: int) -> float:
     return 2.0 * (8 + 32 + 12 * n_det)
 
@@ -225,7 +228,10 @@ def slice_kernel_roofline(st0, st1, steps, n_det):
     share = ms / (sum(st1["kernel_ms"]) - sum(st0["kernel_ms"])) * steps if ms > 0 else None
     return {"bound": "alu", "kernel": "k_slice<FP64,3 det> (fused slice update + likelihood)",
             "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS if achieved else None, "traffic": None,
+            "frac": achieved / FP64_PEAK_TFLOPS if achieved else None,
+            # dram__bytes_read.sum + dram__bytes_write.sum of one k_slice<FP64> launch on this
+            # workload (profiles/k_slice_fp64_c1_ncu_full.md); null once the kernel changes
+            "traffic": K_SLICE_FP64_C1_DRAM_BYTES,
             "peak_source": "derived (not measured): 2 FP64 FMA/clk/SM x 152 SMs x 2070 MHz",
             "per_launch": {"ms": ms, "evals": ev, "point_bins": pb,
                            "flops_per_point_bin": fp64_flops_per_point_bin(n_det),
