@@ -95,11 +95,23 @@ typedef struct {
     const double *S;
 } ns_psd;
 
-/* Uniform frequency grid f_j = f0 + j df, j = 0 .. N-1 (both ends included). */
+/* Uniform frequency grid f_j = f0 + j df, j = 0 .. N-1 (both ends included).
+ * coarse_bins > 0 switches the likelihood to relative binning (the paper's
+ * heterodyned likelihood on a coarser frequency grid, Sec. 2-3; Zackay, Dai &
+ * Venumadhav 2018) about the fiducial parameters theta_fid[11] (host, copied):
+ * coarse_bins geometric bins between f0 and the last grid frequency, edges
+ * moved to the nearest grid index (repeated edges dropped); per bin and
+ * detector the summary data A0 = sum d h0^* w, A1 = sum d h0^* w (f - fm),
+ * B0 = sum |h0|^2 w, B1 = sum |h0|^2 w (f - fm) (w = 4 df / S, h0 the fiducial
+ * strain without cutoff, fm the bin centre), and for each point r = h/h0
+ * interpolated linearly between the edges. Bins whose centre lies above
+ * f_ISCO are dropped when the cutoff is on. */
 typedef struct {
     int N;
     double f0;
     double df;
+    int coarse_bins;
+    const double *theta_fid;
 } ns_grid;
 
 /* Run options. Zero-initialise and set what you need; zero fields take the
@@ -114,7 +126,9 @@ typedef struct {
     int max_shrink;      /* shrink draws per slice step [64] */
     int model;           /* NS_MODEL_GW, or NS_MODEL_TOY (correlated Gaussian) */
     int toy_dim;         /* toy dimension d (model = NS_MODEL_TOY) */
-    int warps_per_point; /* warps cooperating on one likelihood [0: tuned] */
+    int warps_per_point; /* warps cooperating on one batched likelihood (1,2,4,8) [0: rule] */
+    int slots;           /* candidates one chain evaluates concurrently in the slice
+                            update, one warp each (1,2,4,8) [0: rule] */
     double dlogz_stop;   /* stop when log(Z + X Lmax) - log Z < this [0.1] */
     uint64_t seed;       /* Philox key */
     void *stream;        /* cudaStream_t to run on [NULL: library-owned stream] */
@@ -186,6 +200,7 @@ typedef struct {
     int n_live;
     int n_dead;
     long long point_bins;   /* sum over slice-update evaluations of the bins each one read */
+    int status;             /* 0, or bit 0: a chain ended early (internal inconsistency) */
     double kernel_ms[5];    /* cumulative device time of the iteration's kernels, from CUDA
                                events recorded on the context's stream inside the iteration's
                                graph: select, evidence, covariance, slice update, finish */

@@ -57,6 +57,8 @@ class _Problem(ctypes.Structure):
         ("kind", ctypes.c_void_p), ("lo", ctypes.c_void_p), ("hi", ctypes.c_void_p),
         ("toy_d", ctypes.c_int), ("toy_prec", ctypes.c_void_p),
         ("toy_lognorm", ctypes.c_double), ("toy_lo", ctypes.c_double), ("toy_hi", ctypes.c_double),
+        ("rb_nedge", ctypes.c_int), ("rb_J", ctypes.c_void_p), ("rb_sum", ctypes.c_void_p * 6),
+        ("rb_theta_fid", ctypes.c_void_p),
     ]
 
 
@@ -99,6 +101,11 @@ def lib():
                                     ctypes.c_int, ctypes.c_int, dp, dp, dp]
             L.or_evolve.restype = ctypes.c_longlong
             L.or_max_threads.argtypes = []; L.or_max_threads.restype = ctypes.c_int
+            L.or_rb_edges.argtypes = [P, ctypes.c_int, dp]; L.or_rb_edges.restype = ctypes.c_int
+            L.or_rb_summary.argtypes = [P, dp, dp, ctypes.c_int] + [dp] * 6
+            L.or_rb_summary.restype = None
+            L.or_loglike_rb.argtypes = [P, dp, dp, ctypes.c_int] + [dp] * 6 + [dp]
+            L.or_loglike_rb.restype = ctypes.c_double
             _lib = L
     return _lib
 
@@ -319,6 +326,49 @@ def make_problem(w: gi.Workload, *, cutoff: bool = True, max_draws: int = 1000):
     pb = Problem(f0=w.f0, df=w.df, psd=psd, data=data, pos=pos, xarm=xarm, yarm=yarm,
                  ideal=w.ideal, cutoff=cutoff, kind=kind, lo=lo, hi=hi)
     return pb, th
+
+
+class RelativeBinning:
+    """Relative-binning (heterodyned) likelihood of a problem about a fiducial
+    parameter vector, on B geometric coarse bins."""
+
+    def __init__(self, problem: Problem, theta_fid, B: int = 1024):
+        self.pb = problem
+        self.theta_fid = _f64(theta_fid)
+        J = np.zeros(B + 1, dtype=np.int32)
+        ne = lib().or_rb_edges(problem.c, B, _ptr(J))
+        self.J = np.ascontiguousarray(J[:ne])
+        nb = ne - 1
+        nd = problem.n_det
+        self.sums = [np.zeros(nd * nb) for _ in range(6)]
+        lib().or_rb_summary(problem.c, _ptr(self.theta_fid), _ptr(self.J), ne,
+                            *[_ptr(a) for a in self.sums])
+
+    @property
+    def n_bins(self) -> int:
+        return len(self.J) - 1
+
+    def loglike_theta(self, theta) -> np.ndarray:
+        th = _f64(np.atleast_2d(theta))
+        return np.array([lib().or_loglike_rb(self.pb.c, _ptr(self.theta_fid), _ptr(self.J), len(self.J),
+                                             *[_ptr(a) for a in self.sums], _ptr(_f64(t))) for t in th])
+
+    def loglike(self, u) -> np.ndarray:
+        return self.loglike_theta(self.pb.theta(u))
+
+    def problem(self) -> "Problem":
+        """A copy of the problem whose likelihood (batched, and inside the
+        sampler's chains) is this relative-binning one."""
+        pb = self.pb
+        q = Problem(f0=pb.f0, df=pb.df, psd=pb.psd, data=pb.data(), pos=pb.pos, xarm=pb.xarm,
+                    yarm=pb.yarm, ideal=pb.ideal, cutoff=pb.cutoff, kind=pb.kind, lo=pb.lo, hi=pb.hi)
+        q._rb = self
+        q._c.rb_nedge = len(self.J)
+        q._c.rb_J = _ptr(self.J)
+        for i in range(6):
+            q._c.rb_sum[i] = _ptr(self.sums[i])
+        q._c.rb_theta_fid = _ptr(self.theta_fid)
+        return q
 
 
 def toy_problem(d: int) -> Problem:

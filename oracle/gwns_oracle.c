@@ -24,6 +24,11 @@
  *     k deleted points), with stepping out and shrinkage as in Neal (2003),
  *     Sec. 4, applied along a hit-and-run direction.
  *
+ *   - relative binning (Zackay, Dai & Venumadhav 2018; the paper's heterodyned,
+ *     coarse-grid likelihood, Sec. 2-3): summary data of a fiducial waveform
+ *     over geometric coarse bins, and the ratio r = h/h0 interpolated linearly
+ *     inside each bin from its values at the bin edges.
+ *
  * Parity status: the aligned-spin gamma term (2.5PN spin-orbit) is parity
  * unpinned; the other spin terms are pinned through an independent published
  * form; the non-spinning phasing is pinned by re-deriving it from the PN energy
@@ -69,6 +74,11 @@ typedef struct {
     int toy_d;
     const double *toy_prec;  /* [d][d] precision matrix */
     double toy_lognorm, toy_lo, toy_hi;
+    /* relative binning (rb_nedge > 0): edges, summary data, fiducial point */
+    int rb_nedge;
+    const int *rb_J;
+    const double *rb_sum[6];  /* A0re, A0im, A1re, A1im, B0, B1: [n_det][nedge-1] */
+    const double *rb_theta_fid;
 } or_problem;
 
 /* ------------------------------------------------------------------ prior */
@@ -301,11 +311,18 @@ double or_toy_loglike(const or_problem *pb, const double *u)
     return -0.5 * q + pb->toy_lognorm;
 }
 
+double or_loglike_rb(const or_problem *pb, const double *theta_fid, const int *J, int nedge,
+                     const double *A0re, const double *A0im, const double *A1re, const double *A1im,
+                     const double *B0, const double *B1, const double *theta);
+
 double or_loglike_u(const or_problem *pb, const double *u)
 {
     if (pb->model == MODEL_TOY) return or_toy_loglike(pb, u);
     double th[OR_NPARAM];
     or_theta_from_u(pb, u, th);
+    if (pb->rb_nedge > 0)
+        return or_loglike_rb(pb, pb->rb_theta_fid, pb->rb_J, pb->rb_nedge, pb->rb_sum[0], pb->rb_sum[1],
+                             pb->rb_sum[2], pb->rb_sum[3], pb->rb_sum[4], pb->rb_sum[5], th);
     return or_loglike_theta(pb, th);
 }
 
@@ -499,6 +516,117 @@ long long or_evolve(const or_problem *pb, int nthreads, uint64_t seed, uint32_t 
         capsum += cp;
     }
     *caps = capsum;
+    return total;
+}
+
+/* ------------------------------------------------------ relative binning */
+
+/* Coarse-bin edges: B+1 geometric frequencies f0 (f_last/f0)^(b/B), each moved
+ * to the nearest grid index; repeated indices are dropped. Writes the edge
+ * indices to J and returns their count (= number of bins + 1). */
+int or_rb_edges(const or_problem *pb, int B, int *J)
+{
+    double flo = pb->f0, fhi = pb->f0 + (pb->N - 1) * pb->df;
+    int n = 0;
+    for (int b = 0; b <= B; b++) {
+        double target = flo * pow(fhi / flo, (double)b / B);
+        int j = (int)floor((target - pb->f0) / pb->df + 0.5);
+        if (j < 0) j = 0;
+        if (j > pb->N - 1) j = pb->N - 1;
+        if (b == B) j = pb->N - 1;
+        if (n == 0 || j > J[n - 1]) J[n++] = j;
+    }
+    return n;
+}
+
+/* Fine bins of coarse bin b: J[b] <= j < J[b+1], the last bin also holding
+ * J[nb]. Centre frequency: midpoint of the edge frequencies. */
+static int rb_hi(const int *J, int nb, int b) { return (b == nb - 1) ? J[b + 1] + 1 : J[b + 1]; }
+
+/* Summary data of detector det against the fiducial strain h0 (no cutoff):
+ * A0 = 4 df sum d h0^* / S, A1 = 4 df sum d h0^* / S (f - fm),
+ * B0 = 4 df sum |h0|^2 / S,  B1 = 4 df sum |h0|^2 / S (f - fm), per coarse bin. */
+void or_rb_summary(const or_problem *pb, const double *theta_fid, const int *J, int nedge,
+                   double *A0re, double *A0im, double *A1re, double *A1im, double *B0, double *B1)
+{
+    int nb = nedge - 1;
+    or_problem nc = *pb;
+    nc.cutoff = 0;
+    double *hr = (double *)malloc(sizeof(double) * pb->N), *hi = (double *)malloc(sizeof(double) * pb->N);
+    for (int det = 0; det < pb->n_det; det++) {
+        or_strain(&nc, theta_fid, det, hr, hi);
+        const double *S = pb->psd + (size_t)det * pb->N;
+        const double *dre = pb->d_re + (size_t)det * pb->N, *dim = pb->d_im + (size_t)det * pb->N;
+        for (int b = 0; b < nb; b++) {
+            double fm = 0.5 * ((pb->f0 + J[b] * pb->df) + (pb->f0 + J[b + 1] * pb->df));
+            double a0r = 0, a0i = 0, a1r = 0, a1i = 0, b0 = 0, b1 = 0;
+            for (int j = J[b]; j < rb_hi(J, nb, b); j++) {
+                double f = pb->f0 + j * pb->df;
+                double w = 4.0 * pb->df / S[j];
+                /* d h0^* */
+                double xr = dre[j] * hr[j] + dim[j] * hi[j];
+                double xi = dim[j] * hr[j] - dre[j] * hi[j];
+                double hh = hr[j] * hr[j] + hi[j] * hi[j];
+                a0r += w * xr; a0i += w * xi;
+                a1r += w * xr * (f - fm); a1i += w * xi * (f - fm);
+                b0 += w * hh; b1 += w * hh * (f - fm);
+            }
+            size_t o = (size_t)det * nb + b;
+            A0re[o] = a0r; A0im[o] = a0i; A1re[o] = a1r; A1im[o] = a1i; B0[o] = b0; B1[o] = b1;
+        }
+    }
+    free(hr);
+    free(hi);
+}
+
+/* Relative-binning log-likelihood: r = h/h0 at the bin edges (both without
+ * cutoff), r0 = (r(e_b) + r(e_b+1))/2, r1 = (r(e_b+1) - r(e_b))/(e_b+1 - e_b),
+ * <d|h> = Re sum_b [A0 r0^* + A1 r1^*], <h|h> = sum_b [B0 |r0|^2 + 2 B1 Re(r0 r1^*)],
+ * with bins whose centre lies above f_ISCO(theta) dropped when the cutoff is on. */
+double or_loglike_rb(const or_problem *pb, const double *theta_fid, const int *J, int nedge,
+                     const double *A0re, const double *A0im, const double *A1re, const double *A1im,
+                     const double *B0, const double *B1, const double *theta)
+{
+    int nb = nedge - 1;
+    double fisco = or_fisco(theta);
+    double total = 0.0;
+    for (int det = 0; det < pb->n_det; det++) {
+        double fp, fc, dt, fp0, fc0, dt0;
+        det_response(pb, theta, det, &fp, &fc, &dt);
+        det_response(pb, theta_fid, det, &fp0, &fc0, &dt0);
+        double prev_r = 0, prev_i = 0;
+        double dh = 0.0, hh = 0.0;
+        for (int e = 0; e < nedge; e++) {
+            double f = pb->f0 + J[e] * pb->df;
+            double hp[2], hc[2], gp[2], gc[2];
+            or_polarizations(theta, f, hp, hc);
+            or_polarizations(theta_fid, f, gp, gc);
+            double ph = -2.0 * OR_PI * f * dt, ph0 = -2.0 * OR_PI * f * dt0;
+            double hr = fp * hp[0] + fc * hc[0], hi = fp * hp[1] + fc * hc[1];
+            double h0r = fp0 * gp[0] + fc0 * gc[0], h0i = fp0 * gp[1] + fc0 * gc[1];
+            double c = cos(ph), s_ = sin(ph), c0 = cos(ph0), s0 = sin(ph0);
+            double Hr = hr * c - hi * s_, Hi = hr * s_ + hi * c;
+            double H0r = h0r * c0 - h0i * s0, H0i = h0r * s0 + h0i * c0;
+            double den = H0r * H0r + H0i * H0i;
+            double rr = (Hr * H0r + Hi * H0i) / den, ri = (Hi * H0r - Hr * H0i) / den;
+            if (e > 0) {
+                int b = e - 1;
+                double fm = 0.5 * ((pb->f0 + J[b] * pb->df) + f);
+                if (!(pb->cutoff && fm > fisco)) {
+                    double r0r = 0.5 * (prev_r + rr), r0i = 0.5 * (prev_i + ri);
+                    double de = f - (pb->f0 + J[b] * pb->df);
+                    double r1r = (rr - prev_r) / de, r1i = (ri - prev_i) / de;
+                    size_t o = (size_t)det * nb + b;
+                    /* Re(A0 r0^* + A1 r1^*) */
+                    dh += A0re[o] * r0r + A0im[o] * r0i + A1re[o] * r1r + A1im[o] * r1i;
+                    hh += B0[o] * (r0r * r0r + r0i * r0i) + 2.0 * B1[o] * (r0r * r1r + r0i * r1i);
+                }
+            }
+            prev_r = rr;
+            prev_i = ri;
+        }
+        total += dh - 0.5 * hh;
+    }
     return total;
 }
 

@@ -48,7 +48,8 @@ class _Psd(ctypes.Structure):
 
 
 class _Grid(ctypes.Structure):
-    _fields_ = [("N", ctypes.c_int), ("f0", ctypes.c_double), ("df", ctypes.c_double)]
+    _fields_ = [("N", ctypes.c_int), ("f0", ctypes.c_double), ("df", ctypes.c_double),
+                ("coarse_bins", ctypes.c_int), ("theta_fid", ctypes.c_void_p)]
 
 
 class _Options(ctypes.Structure):
@@ -56,7 +57,8 @@ class _Options(ctypes.Structure):
                 ("precision", ctypes.c_int), ("no_cutoff", ctypes.c_int),
                 ("max_stepout", ctypes.c_int), ("max_shrink", ctypes.c_int),
                 ("model", ctypes.c_int), ("toy_dim", ctypes.c_int),
-                ("warps_per_point", ctypes.c_int), ("dlogz_stop", ctypes.c_double),
+                ("warps_per_point", ctypes.c_int), ("slots", ctypes.c_int),
+                ("dlogz_stop", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p)]
 
 
@@ -71,7 +73,7 @@ class _Stats(ctypes.Structure):
                 ("logX", ctypes.c_double), ("lstar", ctypes.c_double),
                 ("logl_max", ctypes.c_double), ("done", ctypes.c_int), ("d", ctypes.c_int),
                 ("n_live", ctypes.c_int), ("n_dead", ctypes.c_int), ("point_bins", ctypes.c_longlong),
-                ("kernel_ms", ctypes.c_double * 5)]
+                ("status", ctypes.c_int), ("kernel_ms", ctypes.c_double * 5)]
 
 
 def library_path() -> str:
@@ -135,8 +137,8 @@ class Sampler:
     def __init__(self, *, kind=None, lo=None, hi=None, data=None, psd=None, f0=20.0, df=1.0,
                  pos=None, xarm=None, yarm=None, ideal=False, n_live=100, k=0, steps_per_dim=5,
                  precision=NS_FP64, no_cutoff=False, max_stepout=0, max_shrink=0,
-                 model=NS_MODEL_GW, toy_dim=0, warps_per_point=0, dlogz_stop=0.1, seed=0,
-                 stream=None):
+                 model=NS_MODEL_GW, toy_dim=0, warps_per_point=0, slots=0, dlogz_stop=0.1, seed=0,
+                 stream=None, coarse_bins=0, theta_fid=None):
         L = lib()
         self._keep = []
         pr = _Prior()
@@ -165,11 +167,15 @@ class Sampler:
                 self._keep += arrs
                 dt.pos, dt.xarm, dt.yarm = (_ptr(a) for a in arrs)
             gr.N, gr.f0, gr.df = N, float(f0), float(df)
+            if coarse_bins:
+                tf = _f64(theta_fid)
+                self._keep.append(tf)
+                gr.coarse_bins, gr.theta_fid = int(coarse_bins), _ptr(tf)
             self.n_det, self.N = n_det, N
         else:
             self.n_det, self.N = 0, 0
         opt = _Options(n_live, k, steps_per_dim, precision, int(bool(no_cutoff)), max_stepout,
-                       max_shrink, model, toy_dim, warps_per_point, dlogz_stop, seed,
+                       max_shrink, model, toy_dim, warps_per_point, slots, dlogz_stop, seed,
                        None if stream is None else int(stream))
         ctx = ctypes.c_void_p()
         _check(L.ns_init(ctypes.byref(ctx), ctypes.byref(pr), ctypes.byref(dt), ctypes.byref(ps),

@@ -20,6 +20,7 @@ struct ns_ctx {
     Model M;
     Tables T;
     int n = 0, d = 0, k_default = 0, steps = 0, precision = 0, max_so = 64, max_sh = 64, warps = 0;
+    int slots = 0;
     double dlogz = 0.1;
     uint64_t seed = 0;
     cudaStream_t stream = nullptr;
@@ -39,6 +40,16 @@ struct ns_ctx {
     RunState *h_state = nullptr;     // pinned
     double *scratch = nullptr;       // eval / waveform scratch
     size_t scratch_bytes = 0;
+    // relative-binning tables
+    int rb_B = 0;
+    double rb_theta[NS_NPARAM];
+    int *rb_J = nullptr, *rb_nedge = nullptr;
+    Coef *rb_fid = nullptr;
+    double *rb_fe = nullptr, *rb_basis64 = nullptr, *rb_fm = nullptr, *rb_inv_de = nullptr;
+    double *rb_B0 = nullptr, *rb_B1 = nullptr;
+    double2 *rb_A0 = nullptr, *rb_A1 = nullptr;
+    float2 *rb_basis32 = nullptr, *rb_fe32 = nullptr, *rb_A0f = nullptr, *rb_A1f = nullptr;
+    float *rb_B0f = nullptr, *rb_B1f = nullptr, *rb_inv_de_f = nullptr;
     // result buffers
     double *fin_u = nullptr, *fin_logl = nullptr, *fin_logw = nullptr, *fin_nlive = nullptr;
     double *res = nullptr;           // [R + 8]
@@ -89,6 +100,19 @@ int choose_warps(const ns_ctx *c) {
     const int bins = c->M.N;
     if (c->precision == NS_FP64) return bins > 32768 ? 2 : 1;
     return bins > 16384 ? 8 : (bins > 2048 ? 4 : 2);
+}
+
+// Speculative candidate slots per chain in the slice update: several slots
+// shorten a chain's critical path when the GPU is not saturated by the k
+// chains' work (small grids), one slot avoids speculative work when it is.
+int choose_slots(const ns_ctx *c) {
+    if (c->slots > 0) return c->slots;
+    if (c->M.model == M_TOY) return 1;
+    const int bins = c->M.rb ? c->T.rb.nb : c->M.N;
+    // measured on GB300 (512 / 4017 / 64,897-bin workloads): FP64 binds on its
+    // pipe beyond small grids, the mixed form on latency up to large grids
+    if (c->precision == NS_FP64) return bins <= 1024 ? 4 : (bins <= 131072 ? 2 : 1);
+    return bins <= 1024 ? 8 : (bins <= 131072 ? 4 : 2);
 }
 
 StepArgs step_args(ns_ctx *c, int k) {
@@ -166,7 +190,7 @@ int enqueue_iteration(ns_ctx *c, int k) {
     if ((rc = mark(c, 2))) return rc;
     CK(launch_cov_chol(c->M, A, c->stream));
     if ((rc = mark(c, 3))) return rc;
-    CK(launch_slice(c->M, c->T, c->precision, choose_warps(c), A, c->stream));
+    CK(launch_slice(c->M, c->T, c->precision, choose_slots(c), A, c->stream));
     if ((rc = mark(c, 4))) return rc;
     CK(launch_finish(A, c->stream));
     if ((rc = mark(c, 5))) return rc;
@@ -186,6 +210,55 @@ int capture_iteration(ns_ctx *c, int k) {
     cudaGraphDestroy(g);
     if (e != cudaSuccess) { c->graph = nullptr; return cuda_fail(e); }
     c->graph_k = k;
+    return NS_OK;
+}
+
+// Relative-binning tables for the current data (edges, fiducial coefficients,
+// summary data); allocates on first use.
+int build_rb(ns_ctx *c) {
+    const int B = c->rb_B, nd = c->M.n_det;
+    const size_t ne = (size_t)B + 1, nb = B;
+    int rc;
+    if (!c->rb_J) {
+        if ((rc = dalloc(&c->rb_J, ne)) || (rc = dalloc(&c->rb_nedge, 1)) || (rc = dalloc(&c->rb_fid, 1)) ||
+            (rc = dalloc(&c->rb_fe, ne)) || (rc = dalloc(&c->rb_basis64, NB * ne)) ||
+            (rc = dalloc(&c->rb_basis32, NB * ne)) || (rc = dalloc(&c->rb_fe32, ne)) ||
+            (rc = dalloc(&c->rb_fm, nb)) || (rc = dalloc(&c->rb_inv_de, nb)) ||
+            (rc = dalloc(&c->rb_A0, nd * nb)) || (rc = dalloc(&c->rb_A1, nd * nb)) ||
+            (rc = dalloc(&c->rb_B0, nd * nb)) || (rc = dalloc(&c->rb_B1, nd * nb)) ||
+            (rc = dalloc(&c->rb_A0f, nd * nb)) || (rc = dalloc(&c->rb_A1f, nd * nb)) ||
+            (rc = dalloc(&c->rb_B0f, nd * nb)) || (rc = dalloc(&c->rb_B1f, nd * nb)) ||
+            (rc = dalloc(&c->rb_inv_de_f, nb)))
+            return rc;
+    }
+    double2 *h0 = nullptr;
+    double *th = nullptr;
+    if ((rc = dalloc(&h0, (size_t)nd * c->M.N)) || (rc = dalloc(&th, NS_NPARAM))) { dfree(h0); return rc; }
+    Model M0 = c->M;
+    M0.rb = 0;
+    RBTables R;
+    std::memset(&R, 0, sizeof(R));
+    cudaError_t e = cudaMemcpyAsync(th, c->rb_theta, sizeof(double) * NS_NPARAM, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = launch_rb_setup(M0, c->T, B, th, c->rb_J, c->rb_nedge, c->rb_fid, h0, c->d_re, c->d_im, c->d_psd, R,
+                            c->rb_fe, c->rb_basis64, c->rb_basis32, c->rb_fe32, c->rb_fm, c->rb_inv_de, c->rb_A0,
+                            c->rb_A1, c->rb_B0, c->rb_B1, c->rb_A0f, c->rb_A1f, c->rb_B0f, c->rb_B1f,
+                            c->rb_inv_de_f, c->stream);
+    int nedge = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&nedge, c->rb_nedge, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    dfree(h0);
+    dfree(th);
+    if (e != cudaSuccess) return cuda_fail(e);
+    RBTables &T = c->T.rb;
+    T.nedge = nedge;
+    T.nb = nedge - 1;
+    T.fe = c->rb_fe; T.basis64 = c->rb_basis64; T.basis32 = c->rb_basis32; T.fe32 = c->rb_fe32;
+    T.fm = c->rb_fm; T.inv_de = c->rb_inv_de; T.A0 = c->rb_A0; T.A1 = c->rb_A1; T.B0 = c->rb_B0;
+    T.B1 = c->rb_B1; T.A0f = c->rb_A0f; T.A1f = c->rb_A1f; T.B0f = c->rb_B0f; T.B1f = c->rb_B1f;
+    T.inv_de_f = c->rb_inv_de_f; T.fid = c->rb_fid;
+    c->M.rb = 1;
+    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; c->graph_k = -1; }
     return NS_OK;
 }
 
@@ -223,7 +296,10 @@ void ns_free(ns_ctx *c) {
     void *bufs[] = {c->d_re, c->d_im, c->d_psd, c->basis64, c->f64, c->prefix, c->w64, c->basis32,
                     c->f32, c->w32, c->live_u, c->live_logl, c->order, c->chol, c->dead_u,
                     c->dead_logl, c->dead_logw, c->dead_nlive, c->state, c->scratch, c->fin_u,
-                    c->fin_logl, c->fin_logw, c->fin_nlive, c->res};
+                    c->fin_logl, c->fin_logw, c->fin_nlive, c->res, c->rb_J, c->rb_nedge, c->rb_fid,
+                    c->rb_fe, c->rb_basis64, c->rb_basis32, c->rb_fe32, c->rb_fm, c->rb_inv_de, c->rb_A0,
+                    c->rb_A1, c->rb_B0, c->rb_B1, c->rb_A0f, c->rb_A1f, c->rb_B0f, c->rb_B1f,
+                    c->rb_inv_de_f};
     for (void *p : bufs) dfree(p);
     if (c->h_state) cudaFreeHost(c->h_state);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -240,6 +316,8 @@ static int validate(const ns_prior *prior, const ns_data *data, const ns_psd *ps
     if (o->warps_per_point != 0 && o->warps_per_point != 1 && o->warps_per_point != 2 &&
         o->warps_per_point != 4 && o->warps_per_point != 8)
         return NS_ERR_INVALID_ARG;
+    if (o->slots != 0 && o->slots != 1 && o->slots != 2 && o->slots != 4 && o->slots != 8)
+        return NS_ERR_INVALID_ARG;
     if (o->model == NS_MODEL_TOY) {
         if (o->toy_dim < 1 || o->toy_dim > NS_MAX_DIM) return NS_ERR_INVALID_ARG;
         return NS_OK;
@@ -249,6 +327,9 @@ static int validate(const ns_prior *prior, const ns_data *data, const ns_psd *ps
     if (grid->N < 1 || !is_fin(grid->f0) || !is_fin(grid->df) || grid->df <= 0.0 || grid->f0 <= 0.0)
         return NS_ERR_INVALID_ARG;
     if (data->n_det < 1 || data->n_det > NS_MAX_DET) return NS_ERR_INVALID_ARG;
+    if (grid->coarse_bins < 0 || grid->coarse_bins > 65536 || (grid->coarse_bins > 0 && !grid->theta_fid))
+        return NS_ERR_INVALID_ARG;
+    if (grid->coarse_bins > 0 && grid->N < 2) return NS_ERR_INVALID_ARG;
     if ((data->re == nullptr) != (data->im == nullptr)) return NS_ERR_INVALID_ARG;
     if (!data->ideal && (!data->pos || !data->xarm || !data->yarm)) return NS_ERR_INVALID_ARG;
     int dim = 0;
@@ -290,6 +371,7 @@ int ns_init(ns_ctx **out, const ns_prior *prior, const ns_data *data, const ns_p
     c->max_so = o->max_stepout ? o->max_stepout : 64;
     c->max_sh = o->max_shrink ? o->max_shrink : 64;
     c->warps = o->warps_per_point;
+    c->slots = o->slots;
     c->dlogz = o->dlogz_stop > 0.0 ? o->dlogz_stop : 0.1;
     c->seed = o->seed;
     if (o->stream) {
@@ -371,6 +453,10 @@ int ns_init(ns_ctx **out, const ns_prior *prior, const ns_data *data, const ns_p
                                     c->basis32, c->f32, c->w32, c->stream);
     }
     if (e != cudaSuccess) { ns_free(c); return cuda_fail(e); }
+    if (M.model == M_GW && grid->coarse_bins > 0) {
+        c->rb_B = grid->coarse_bins;
+        for (int p = 0; p < NS_NPARAM; p++) c->rb_theta[p] = grid->theta_fid[p];
+    }
     c->T.basis64 = c->basis64;
     c->T.f64 = c->f64;
     c->T.w64 = c->w64;
@@ -378,6 +464,7 @@ int ns_init(ns_ctx **out, const ns_prior *prior, const ns_data *data, const ns_p
     c->T.basis32 = c->basis32;
     c->T.f32 = c->f32;
     c->T.w32 = c->w32;
+    if (c->rb_B > 0 && (rc = build_rb(c))) { ns_free(c); return rc; }
     RunState s0;
     std::memset(&s0, 0, sizeof(s0));
     s0.logZ = -INFINITY;
@@ -401,7 +488,9 @@ int ns_set_data(ns_ctx *c, const double *re, const double *im) {
     CK(cudaMemcpyAsync(c->d_im, im, nn * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     CK(launch_build_tables(c->M, c->d_re, c->d_im, c->d_psd, c->basis64, c->f64, c->w64, c->prefix,
                            c->basis32, c->f32, c->w32, c->stream));
-    int rc = eval_points(c, c->live_u, 0, c->n, c->live_logl);
+    int rc;
+    if (c->rb_B > 0 && (rc = build_rb(c))) return rc;
+    rc = eval_points(c, c->live_u, 0, c->n, c->live_logl);
     if (rc) return rc;
     CK(cudaStreamSynchronize(c->stream));
     return NS_OK;
@@ -470,6 +559,7 @@ int ns_get_stats(ns_ctx *c, ns_stats *st) {
     st->n_live = c->n;
     st->n_dead = (int)c->n_dead;
     st->point_bins = (long long)s.point_bins;
+    st->status = s.status;
     for (int i = 0; i < 5; i++) st->kernel_ms[i] = c->timing ? c->kernel_ms[i] : -1.0;
     return NS_OK;
 }

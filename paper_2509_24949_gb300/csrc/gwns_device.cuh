@@ -40,12 +40,32 @@ constexpr double INV_TWO_PI_D = 0.15915494309189535;
 struct Model {
     int model;        // M_GW or M_TOY
     int n_det, N, ideal, cutoff, dim;
+    int rb;           // 1: relative-binning likelihood on the coarse bins
     double f0, df;
     int kind[NPARAM];
     double lo[NPARAM], hi[NPARAM];
     double pos[MAXDET][3], xarm[MAXDET][3], yarm[MAXDET][3];
     // toy: x = toy_lo + (toy_hi - toy_lo) u, Sigma_ij = rho^|i-j|
     double toy_lo, toy_hi, toy_rho, toy_lognorm;
+};
+
+// Relative-binning (heterodyned) tables: coarse bins between grid indices
+// J[b] .. J[b+1], summary data of the fiducial waveform h0 per detector and
+// bin, and the phase basis at the edge frequencies.
+struct Coef;
+struct RBTables {
+    int nedge, nb;
+    const double *fe;          // [nedge] edge frequencies
+    const double *basis64;     // [NB][nedge]
+    const float2 *basis32;     // [NB][nedge] (hi, lo)
+    const float2 *fe32;        // [nedge] (hi, lo)
+    const double *fm;          // [nb] bin centres (cutoff test)
+    const double *inv_de;      // [nb] 1/(e_{b+1} - e_b)
+    const double2 *A0, *A1;    // [n_det][nb] sum d h0^* w, sum d h0^* w (f - fm)
+    const double *B0, *B1;     // [n_det][nb] sum |h0|^2 w, sum |h0|^2 w (f - fm)
+    const float2 *A0f, *A1f;   // FP32 copies for the mixed form
+    const float *B0f, *B1f, *inv_de_f;
+    const Coef *fid;           // fiducial point's coefficients
 };
 
 // Device tables of one grid.
@@ -57,6 +77,7 @@ struct Tables {
     const float2 *basis32;   // [NB][N]   B_m(f_j) as (hi, lo) floats
     const float2 *f32;       // [N]       f_j as (hi, lo)
     const float2 *w32;       // [n_det][N]
+    RBTables rb;             // used when Model::rb is set
 };
 
 // Per-point likelihood coefficients.
@@ -67,6 +88,8 @@ struct Coef {
     double gre[MAXDET], gim[MAXDET];   // G_d = A conj(Q_d)
     double hh;             // sum_d <h_d|h_d>
     double toy;            // toy model log L
+    double rot_re[MAXDET], rot_im[MAXDET];   // exp(2 pi i rot_stride df tau_d) (FP64 loop)
+    double fisco;          // f_ISCO [Hz]
     int jcut;              // last bin with f_j <= f_ISCO (-1: none)
     int pad;
 };
@@ -143,13 +166,163 @@ __device__ __forceinline__ int cutoff_index(const Model &M, double fisco) {
     return j;
 }
 
-// Per-point coefficients computed by one warp: parameter-only quantities are
-// computed redundantly by every lane (uniform control flow, so they cost one
-// warp instruction each), transcendentals of independent arguments are packed
-// into different lanes of one call, and the detector terms run on lanes
-// 0 .. n_det-1. Writes *out (shared memory) from lane 0 and the detector lanes.
-// u: the point's unit-cube coordinates (shared or global, read by all lanes).
-__device__ inline void point_coef_warp(const Model &M, const Tables &T, const double *u, Coef *out) {
+// Per-point coefficients, computed by lane groups of 8: group g of the calling
+// warp handles point g (g < count), so one warp computes up to four points at
+// the cost of one (FP64 costs one warp instruction whatever the number of
+// active lanes). Inside a group, parameter-only quantities are computed
+// redundantly by all 8 lanes (uniform control flow), transcendentals of
+// independent arguments are packed into different lanes of a single call (one
+// log, one exp, one sincos), and the detector terms run on sub-lanes
+// 0 .. n_det-1. The distance enters only through ln D_L, so a uniform-in-volume
+// distance needs no cube root. u0 + g*ustride: point g's unit-cube coordinates;
+// out0[g]: its coefficients. rot_stride > 0 also stores, per detector,
+// exp(2 pi i rot_stride df tau_d), the rotation between bins rot_stride apart
+// used by the FP64 bin loop. GW model only; all 32 lanes must call.
+__device__ inline void point_coef_group(const Model &M, const Tables &T, const double *u0, int ustride,
+                                        Coef *out0, int count, int rot_stride) {
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, g = lane >> 3, sl = lane & 7;
+    const bool writer = g < count;
+    const double *u = u0 + (writer ? g : 0) * ustride;
+    Coef *out = out0 + (writer ? g : 0);
+    // prior transform; a uniform-in-volume distance keeps its volume argument
+    double th[NPARAM];
+    double dl_arg = 0.0;
+    bool dl_vol = false;
+    {
+        int i = 0;
+#pragma unroll
+        for (int p = 0; p < NPARAM; p++) {
+            if (M.kind[p] == K_FIXED) {
+                th[p] = M.lo[p];
+            } else if (M.kind[p] == K_UNIFORM) {
+                th[p] = __dadd_rn(M.lo[p], __dmul_rn(__dsub_rn(M.hi[p], M.lo[p]), u[i++]));
+            } else {
+                const double lo3 = M.lo[p] * M.lo[p] * M.lo[p], hi3 = M.hi[p] * M.hi[p] * M.hi[p];
+                const double v = __dadd_rn(lo3, __dmul_rn(u[i++], __dsub_rn(hi3, lo3)));
+                if (p == P_DL) { dl_vol = true; dl_arg = v; th[p] = 0.0; }
+                else th[p] = cbrt(v);
+            }
+        }
+        if (!dl_vol) dl_arg = th[P_DL];
+    }
+    const double q = th[P_Q];
+    const double r1q = 1.0 / (1.0 + q);
+    const double eta = q * r1q * r1q;               // m1 m2 / M^2
+    const double delta = (1.0 - q) * r1q;           // (m1 - m2)/M, m1 >= m2
+    const double chis = 0.5 * (th[P_CHI1] + th[P_CHI2]);
+    const double chia = 0.5 * (th[P_CHI1] - th[P_CHI2]);
+    const double tmc = th[P_MC] * TSUN;
+    // packed log: sub-lane 0 ln(eta), 1 ln(T_Mc), others ln(D_L) (or of D_L^3)
+    const double lg = log(sl == 0 ? eta : (sl == 1 ? tmc : dl_arg));
+    const double ln_eta = __shfl_sync(FULL, lg, 0, 8);
+    const double ln_tmc = __shfl_sync(FULL, lg, 1, 8);
+    const double ln_dlx = __shfl_sync(FULL, lg, 2, 8);
+    const double ln_dl = dl_vol ? ln_dlx * (1.0 / 3.0) : ln_dlx;
+    // ln(pi T_M) with T_M = T_Mc eta^(-3/5); a = (pi T_M)^(1/3), v = a f^(1/3)
+    const double ln_x = 1.1447298858494002 + ln_tmc - 0.6 * ln_eta;
+    const double ln_a = ln_x * (1.0 / 3.0);
+    // packed exp: 0 a, 1 1/a, 2 1/(pi T_M), 3 K = 3/(128 eta),
+    // others A = sqrt(5/24) pi^(-2/3) c T_Mc^(5/6) / D_L (D_L in Mpc)
+    const double ex_arg = sl == 0 ? ln_a
+                        : sl == 1 ? -ln_a
+                        : sl == 2 ? -ln_x
+                        : sl == 3 ? -3.7534179752515073 - ln_eta
+                        : -33.81250354619071 + (5.0 / 6.0) * ln_tmc - ln_dl;
+    const double ex = exp(ex_arg);
+    const double a = __shfl_sync(FULL, ex, 0, 8);
+    const double ia = __shfl_sync(FULL, ex, 1, 8);
+    const double inv_pitm = __shfl_sync(FULL, ex, 2, 8);
+    const double K = __shfl_sync(FULL, ex, 3, 8);
+    const double amp = __shfl_sync(FULL, ex, 4, 8);
+    // f_ISCO = 1/(6^(3/2) pi T_M)
+    const int jcut = cutoff_index(M, inv_pitm * 0.06804138174397717);
+
+    // TaylorF2 phasing (3.5PN non-spinning + aligned-spin beta, sigma, gamma)
+    const double pi = PI_D;
+    if (sl == 0 && writer) {
+        const double beta = (113.0 / 12.0) * (chis + delta * chia - (76.0 / 113.0) * eta * chis);
+        const double sigma = (79.0 / 8.0) * eta * th[P_CHI1] * th[P_CHI2];
+        const double gamma = (732985.0 / 2268.0 - 24260.0 / 81.0 * eta - 340.0 / 9.0 * eta * eta) * chis
+                           + (732985.0 / 2268.0 + 140.0 / 9.0 * eta) * delta * chia;
+        const double phi2 = 3715.0 / 756.0 + 55.0 / 9.0 * eta;
+        const double phi3 = -16.0 * pi + 4.0 * beta;
+        const double phi4 = 15293365.0 / 508032.0 + 27145.0 / 504.0 * eta + 3085.0 / 72.0 * eta * eta
+                          - 10.0 * sigma;
+        const double phi5 = pi * (38645.0 / 756.0 - 65.0 / 9.0 * eta) - gamma;   // x (1 + 3 ln(v sqrt 6))
+        const double phi6 = 11583231236531.0 / 4694215680.0 - 640.0 / 3.0 * pi * pi
+                          - 6848.0 / 21.0 * GAMMA_E
+                          + eta * (-15737765635.0 / 3048192.0 + 2255.0 / 12.0 * pi * pi)
+                          + 76055.0 / 1728.0 * eta * eta - 127825.0 / 1296.0 * eta * eta * eta;
+        const double phi7 = pi * (77096675.0 / 254016.0 + 378515.0 / 1512.0 * eta - 74045.0 / 756.0 * eta * eta);
+        // K v^(k-5) = K a^(k-5) f^((k-5)/3)
+        const double ia2 = ia * ia, ia3 = ia2 * ia, ia5 = ia3 * ia2;
+        out->a[0] = K * ia5;                       // f^(-5/3)
+        out->a[1] = K * phi2 * ia3;                // f^(-1)
+        out->a[2] = K * phi3 * ia2;                // f^(-2/3)
+        out->a[3] = K * phi4 * ia;                 // f^(-1/3)
+        out->a[4] = K * phi5;                      // ln f   (3 ln v = 3 ln a + ln f)
+        out->a[5] = K * a * (phi6 - 6848.0 / 21.0 * (1.3862943611198906 + ln_a));   // f^(1/3)
+        out->a[6] = -K * a * (6848.0 / 63.0);      // f^(1/3) ln f
+        out->a[7] = K * phi7 * a * a;              // f^(2/3)
+        // constant: -phi_c - pi/4 + K phi5 (1 + 3 ln sqrt 6 + 3 ln a), reduced mod 2 pi
+        const double c0 = -th[P_PHIC] - 0.25 * pi + K * phi5 * (1.0 + 3.0 * 0.8958797346140275 + 3.0 * ln_a);
+        out->c0 = c0 - TWO_PI_D * rint(c0 * INV_TWO_PI_D);
+        out->jcut = jcut;
+        out->fisco = inv_pitm * 0.06804138174397717;
+    }
+    const double ci = th[P_COSI];
+    // packed sincos: sub-lane 0 ra, others psi
+    double sn, cs;
+    sincos(sl == 0 ? th[P_RA] : th[P_PSI], &sn, &cs);
+    const double sa = __shfl_sync(FULL, sn, 0, 8), ca = __shfl_sync(FULL, cs, 0, 8);
+    const double sp = __shfl_sync(FULL, sn, 1, 8), cp = __shfl_sync(FULL, cs, 1, 8);
+    double hh_part = 0.0, tau = 0.0;
+    if (sl < M.n_det) {
+        const int dd = sl;
+        double fp, fc, dt;
+        if (M.ideal) {
+            fp = 1.0; fc = 0.0; dt = 0.0;
+        } else {
+            const double sd = th[P_SINDEC];
+            const double cd = sqrt(1.0 - sd * sd);
+            // wave-frame basis X, Y (Anderson et al. 2001) and source direction n
+            const double X0 = sa * cp - sp * ca * sd, X1 = -ca * cp - sp * sa * sd, X2 = sp * cd;
+            const double Y0 = -sa * sp - cp * ca * sd, Y1 = ca * sp - cp * sa * sd, Y2 = cp * cd;
+            const double *x = M.xarm[dd], *y = M.yarm[dd];
+            // D = (x x^T - y y^T)/2: X^T D Y = ((x.X)(x.Y) - (y.X)(y.Y))/2
+            const double xX = x[0] * X0 + x[1] * X1 + x[2] * X2;
+            const double xY = x[0] * Y0 + x[1] * Y1 + x[2] * Y2;
+            const double yX = y[0] * X0 + y[1] * X1 + y[2] * X2;
+            const double yY = y[0] * Y0 + y[1] * Y1 + y[2] * Y2;
+            fp = 0.5 * ((xX * xX - yX * yX) - (xY * xY - yY * yY));
+            fc = (xX * xY - yX * yY);
+            const double *r = M.pos[dd];
+            dt = -(r[0] * cd * ca + r[1] * cd * sa + r[2] * sd) * (1.0 / C_SI);
+        }
+        const double qre = fp * 0.5 * (1.0 + ci * ci);
+        const double qim = -fc * ci;
+        tau = th[P_TC] + dt;
+        if (writer) {
+            out->tau[dd] = tau;
+            out->gre[dd] = amp * qre;
+            out->gim[dd] = -amp * qim;
+        }
+        if (jcut >= 0) hh_part = amp * amp * (qre * qre + qim * qim) * T.prefix[(size_t)dd * M.N + jcut];
+    }
+    if (rot_stride > 0) {
+        double rs, rc;
+        sincos(TWO_PI_D * ((double)rot_stride * M.df) * tau, &rs, &rc);
+        if (sl < M.n_det && writer) { out->rot_re[sl] = rc; out->rot_im[sl] = rs; }
+    }
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) hh_part += __shfl_xor_sync(FULL, hh_part, o, 8);
+    if (sl == 0 && writer) out->hh = hh_part;
+}
+
+// Coefficients of one point by one warp (toy model, or GW via lane group 0).
+__device__ inline void point_coef_warp(const Model &M, const Tables &T, const double *u, Coef *out,
+                                       int rot_stride = 0) {
     const int lane = threadIdx.x & 31;
     if (M.model == M_TOY) {
         // log N(x; 0, Sigma) with Sigma_ij = rho^|i-j|: the inverse is tridiagonal,
@@ -171,110 +344,7 @@ __device__ inline void point_coef_warp(const Model &M, const Tables &T, const do
         }
         return;
     }
-    double th[NPARAM];
-    prior_transform(M, u, th);
-    const double q = th[P_Q];
-    const double opq = 1.0 + q;
-    const double eta = q / (opq * opq);
-    const double delta = (1.0 - q) / opq;          // (m1 - m2)/M, m1 >= m2
-    const double chis = 0.5 * (th[P_CHI1] + th[P_CHI2]);
-    const double chia = 0.5 * (th[P_CHI1] - th[P_CHI2]);
-    const double tmc = th[P_MC] * TSUN;
-    // packed logs: lane 0 ln(eta), lane 1 ln(T_Mc)
-    double lg = log(lane == 0 ? eta : tmc);
-    const double ln_eta = __shfl_sync(0xffffffffu, lg, 0);
-    const double ln_tmc = __shfl_sync(0xffffffffu, lg, 1);
-    // ln(pi T_M) with T_M = T_Mc eta^(-3/5); a = (pi T_M)^(1/3)
-    const double ln_x = 1.1447298858494002 + ln_tmc - 0.6 * ln_eta;   // ln(pi) + ...
-    const double ln_a = ln_x * (1.0 / 3.0);
-    // packed exps: lane 0 a = exp(ln_a), lane 1 T_Mc^(5/6), lane 2 1/(pi T_M)
-    double ex_arg = (lane == 0) ? ln_a : (lane == 1 ? (5.0 / 6.0) * ln_tmc : -ln_x);
-    double ex = exp(ex_arg);
-    const double a = __shfl_sync(0xffffffffu, ex, 0);
-    const double tmc56 = __shfl_sync(0xffffffffu, ex, 1);
-    const double inv_pitm = __shfl_sync(0xffffffffu, ex, 2);
-    // f_ISCO = 1/(6^(3/2) pi T_M)
-    const double fisco = inv_pitm * 0.06804138174397717;   // 6^(-3/2)
-    const int jcut = cutoff_index(M, fisco);
-
-    // TaylorF2 phasing coefficients (3.5PN non-spinning + aligned-spin terms)
-    const double pi = PI_D;
-    const double beta = (113.0 / 12.0) * (chis + delta * chia - (76.0 / 113.0) * eta * chis);
-    const double sigma = (79.0 / 8.0) * eta * th[P_CHI1] * th[P_CHI2];
-    const double gamma = (732985.0 / 2268.0 - 24260.0 / 81.0 * eta - 340.0 / 9.0 * eta * eta) * chis
-                       + (732985.0 / 2268.0 + 140.0 / 9.0 * eta) * delta * chia;
-    const double phi2 = 3715.0 / 756.0 + 55.0 / 9.0 * eta;
-    const double phi3 = -16.0 * pi + 4.0 * beta;
-    const double phi4 = 15293365.0 / 508032.0 + 27145.0 / 504.0 * eta + 3085.0 / 72.0 * eta * eta
-                      - 10.0 * sigma;
-    const double phi5 = pi * (38645.0 / 756.0 - 65.0 / 9.0 * eta) - gamma;   // times (1 + 3 ln(v sqrt 6))
-    const double phi6 = 11583231236531.0 / 4694215680.0 - 640.0 / 3.0 * pi * pi
-                      - 6848.0 / 21.0 * GAMMA_E
-                      + eta * (-15737765635.0 / 3048192.0 + 2255.0 / 12.0 * pi * pi)
-                      + 76055.0 / 1728.0 * eta * eta - 127825.0 / 1296.0 * eta * eta * eta;
-    const double phi7 = pi * (77096675.0 / 254016.0 + 378515.0 / 1512.0 * eta - 74045.0 / 756.0 * eta * eta);
-    // v = a f^(1/3): K v^(k-5) = K a^(k-5) f^((k-5)/3), K = 3/(128 eta)
-    const double K = 3.0 / (128.0 * eta);
-    const double ia = 1.0 / a;
-    const double ia2 = ia * ia;
-    const double ia3 = ia2 * ia;
-    const double ia5 = ia3 * ia2;
-    const double ln_sqrt6 = 0.8958797346140275;
-    const double ln4 = 1.3862943611198906;
-    if (lane == 0) {
-        out->a[0] = K * ia5;                       // f^(-5/3)
-        out->a[1] = K * phi2 * ia3;                // f^(-1)
-        out->a[2] = K * phi3 * ia2;                // f^(-2/3)
-        out->a[3] = K * phi4 * ia;                 // f^(-1/3)
-        out->a[4] = K * phi5;                      // ln f   (3 ln v = 3 ln a + ln f)
-        out->a[5] = K * a * (phi6 - 6848.0 / 21.0 * (ln4 + ln_a));   // f^(1/3)
-        out->a[6] = -K * a * (6848.0 / 63.0);      // f^(1/3) ln f
-        out->a[7] = K * phi7 * a * a;              // f^(2/3)
-        double c0 = -th[P_PHIC] - 0.25 * pi + K * phi5 * (1.0 + 3.0 * ln_sqrt6 + 3.0 * ln_a);
-        out->c0 = c0 - TWO_PI_D * rint(c0 * INV_TWO_PI_D);
-        out->jcut = jcut;
-    }
-    // amplitude A = sqrt(5/24) pi^(-2/3) c T_Mc^(5/6) / D_L
-    const double amp = 0.21278751013966343 * C_SI * tmc56 / (th[P_DL] * MPC_SI);
-    const double ci = th[P_COSI];
-    // antenna patterns and delays on detector lanes; packed sincos of ra (lane 0) and psi (lane 1)
-    double sn, cs;
-    sincos(lane == 0 ? th[P_RA] : th[P_PSI], &sn, &cs);
-    const double sa = __shfl_sync(0xffffffffu, sn, 0), ca = __shfl_sync(0xffffffffu, cs, 0);
-    const double sp = __shfl_sync(0xffffffffu, sn, 1), cp = __shfl_sync(0xffffffffu, cs, 1);
-    double hh_part = 0.0;
-    if (lane < M.n_det) {
-        const int dd = lane;
-        double fp, fc, dt;
-        if (M.ideal) {
-            fp = 1.0; fc = 0.0; dt = 0.0;
-        } else {
-            const double sd = th[P_SINDEC];
-            const double cd = sqrt(1.0 - sd * sd);
-            // wave-frame basis X, Y (Anderson et al. 2001) and source direction n
-            const double X0 = sa * cp - sp * ca * sd, X1 = -ca * cp - sp * sa * sd, X2 = sp * cd;
-            const double Y0 = -sa * sp - cp * ca * sd, Y1 = ca * sp - cp * sa * sd, Y2 = cp * cd;
-            const double *x = M.xarm[dd], *y = M.yarm[dd];
-            // D = (x x^T - y y^T)/2: X^T D Y = ((x.X)(x.Y) - (y.X)(y.Y))/2
-            const double xX = x[0] * X0 + x[1] * X1 + x[2] * X2;
-            const double xY = x[0] * Y0 + x[1] * Y1 + x[2] * Y2;
-            const double yX = y[0] * X0 + y[1] * X1 + y[2] * X2;
-            const double yY = y[0] * Y0 + y[1] * Y1 + y[2] * Y2;
-            fp = 0.5 * ((xX * xX - yX * yX) - (xY * xY - yY * yY));
-            fc = (xX * xY - yX * yY);
-            const double *r = M.pos[dd];
-            dt = -(r[0] * cd * ca + r[1] * cd * sa + r[2] * sd) / C_SI;
-        }
-        const double qre = fp * 0.5 * (1.0 + ci * ci);
-        const double qim = -fc * ci;
-        out->tau[dd] = th[P_TC] + dt;
-        out->gre[dd] = amp * qre;
-        out->gim[dd] = -amp * qim;
-        if (jcut >= 0) hh_part = amp * amp * (qre * qre + qim * qim) * T.prefix[(size_t)dd * M.N + jcut];
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) hh_part += __shfl_xor_sync(0xffffffffu, hh_part, o);
-    if (lane == 0) out->hh = hh_part;
+    point_coef_group(M, T, u, 0, out, 1, rot_stride);
 }
 
 // Split a double into (hi, lo) floats.
@@ -283,19 +353,22 @@ __device__ __forceinline__ void split_df(double x, float &h, float &l) {
     l = __double2float_rn(x - (double)h);
 }
 
-// Mixed-precision coefficients (phase in turns), from lane-parallel conversions.
-__device__ __forceinline__ void coef_to_mixed_warp(const Coef &c, int n_det, CoefMixed *m) {
+// Mixed-precision coefficients (phase in turns), from lane-parallel
+// conversions; with fid, the differences from the fiducial point's.
+__device__ __forceinline__ void coef_to_mixed_warp(const Coef &c, int n_det, CoefMixed *m,
+                                                   const Coef *fid = nullptr) {
     const int lane = threadIdx.x & 31;
-    if (lane < NB) split_df(c.a[lane] * INV_TWO_PI_D, m->ah[lane], m->al[lane]);
-    else if (lane == NB) split_df(c.c0 * INV_TWO_PI_D, m->c0h, m->c0l);
-    else if (lane >= 16 && lane < 16 + n_det) split_df(c.tau[lane - 16], m->tauh[lane - 16], m->taul[lane - 16]);
+    if (lane < NB) split_df((c.a[lane] - (fid ? fid->a[lane] : 0.0)) * INV_TWO_PI_D, m->ah[lane], m->al[lane]);
+    else if (lane == NB) split_df((c.c0 - (fid ? fid->c0 : 0.0)) * INV_TWO_PI_D, m->c0h, m->c0l);
+    else if (lane >= 16 && lane < 16 + n_det)
+        split_df(c.tau[lane - 16] - (fid ? fid->tau[lane - 16] : 0.0), m->tauh[lane - 16], m->taul[lane - 16]);
 }
 
 // ------------------------------------------------------------ bin loops
 // FP64: Psi_j from the basis (FP64 FMAs), exp(i Psi_j) by sincos, the detector
 // factor exp(2 pi i f_j tau_d) by a rotation recurrence along the thread's bins
 // (f advances by stride*df per step).
-template <int NDET>
+template <int NDET, bool PRE_ROT = false>
 __device__ __forceinline__ void bins_fp64(const Tables &T, int N, double f0, double df, const Coef &c,
                                           int tid, int stride, double zr[NDET], double zi[NDET]) {
     double a[NB];
@@ -308,7 +381,8 @@ __device__ __forceinline__ void bins_fp64(const Tables &T, int N, double f0, dou
         zr[d] = 0.0; zi[d] = 0.0;
         if (tid <= c.jcut) {
             sincos(TWO_PI_D * (f0 + tid * df) * c.tau[d], &ri[d], &rr[d]);
-            sincos(TWO_PI_D * (stride * df) * c.tau[d], &pi_[d], &pr[d]);
+            if (PRE_ROT) { pr[d] = c.rot_re[d]; pi_[d] = c.rot_im[d]; }
+            else sincos(TWO_PI_D * (stride * df) * c.tau[d], &pi_[d], &pr[d]);
         }
     }
     for (int j = tid; j <= c.jcut; j += stride) {
@@ -406,6 +480,146 @@ __device__ __forceinline__ void bins_mixed(const Tables &T, int N, const CoefMix
         zr[d] = (double)zrh[d] + (double)zrl[d];
         zi[d] = (double)zih[d] + (double)zil[d];
     }
+}
+
+// ------------------------------------------------------- relative binning
+// One warp, edges striped over lanes in chunks of 31 bins (32 edges): each lane
+// computes E_d(e) = exp(-i dPsi_d(e)) at its edge, with dPsi the phase
+// difference from the fiducial point, takes E_d(e+1) from the next lane and
+// accumulates its bin:
+//   Y_d += A0 conj(S)/2 + A1 conj(D),  H_d += B0 |S|^2/4 + B1 Re(S conj(D)),
+//   S = E_b + E_b+1,  D = (E_b+1 - E_b)/(e_b+1 - e_b),
+// so that with rho_d = conj(G_d)/conj(G0_d) (r = h/h0 = rho_d E_d):
+//   <d|h_d> = Re(conj(rho_d) Y_d),  <h_d|h_d> = |rho_d|^2 H_d.
+// Bins whose centre lies above f_ISCO are dropped when the cutoff is on.
+template <int NDET>
+__device__ __forceinline__ void rb_fp64(const Model &M, const RBTables &R, const Coef &c, int lane,
+                                        double Yr[NDET], double Yi[NDET], double H[NDET]) {
+    const Coef &f = *R.fid;
+    double da[NB];
+#pragma unroll
+    for (int m = 0; m < NB; m++) da[m] = c.a[m] - f.a[m];
+    const double dc = c.c0 - f.c0;
+    double dtau[NDET];
+#pragma unroll
+    for (int d = 0; d < NDET; d++) { dtau[d] = c.tau[d] - f.tau[d]; Yr[d] = Yi[d] = H[d] = 0.0; }
+    for (int base = 0; base < R.nb; base += 31) {
+        const int e = base + lane;
+        const bool ok = e < R.nedge;
+        double psi = dc;
+        if (ok) {
+#pragma unroll
+            for (int m = 0; m < NB; m++) psi = fma(da[m], __ldg(R.basis64 + (size_t)m * R.nedge + e), psi);
+        }
+        const double fe = ok ? __ldg(R.fe + e) : 0.0;
+        const int b = base + lane;
+        const bool use = lane < 31 && b < R.nb && (!M.cutoff || __ldg(R.fm + b) <= c.fisco);
+#pragma unroll
+        for (int d = 0; d < NDET; d++) {
+            double sn, cs;
+            sincos(psi + TWO_PI_D * fe * dtau[d], &sn, &cs);
+            const double er = cs, ei = -sn;                    // exp(-i dPsi)
+            const double nr = __shfl_down_sync(0xffffffffu, er, 1);
+            const double ni = __shfl_down_sync(0xffffffffu, ei, 1);
+            if (use) {
+                const double idl = __ldg(R.inv_de + b);
+                const double Sr = er + nr, Si = ei + ni;
+                const double Dr = (nr - er) * idl, Di = (ni - ei) * idl;
+                const size_t o = (size_t)d * R.nb + b;
+                const double2 a0 = __ldg(R.A0 + o), a1 = __ldg(R.A1 + o);
+                // A0 conj(S)/2 + A1 conj(D)
+                Yr[d] += 0.5 * (a0.x * Sr + a0.y * Si) + (a1.x * Dr + a1.y * Di);
+                Yi[d] += 0.5 * (a0.y * Sr - a0.x * Si) + (a1.y * Dr - a1.x * Di);
+                H[d] += 0.25 * __ldg(R.B0 + o) * (Sr * Sr + Si * Si) + __ldg(R.B1 + o) * (Sr * Dr + Si * Di);
+            }
+        }
+    }
+}
+
+template <int NDET>
+__device__ __forceinline__ void rb_mixed(const Model &M, const RBTables &R, const CoefMixed &c, double fisco,
+                                         int lane, double Yr[NDET], double Yi[NDET], double H[NDET]) {
+    float yr[NDET], yi[NDET], hh[NDET];
+#pragma unroll
+    for (int d = 0; d < NDET; d++) yr[d] = yi[d] = hh[d] = 0.f;
+    for (int base = 0; base < R.nb; base += 31) {
+        const int e = base + lane;
+        const bool ok = e < R.nedge;
+        float sh = c.c0h, sl = c.c0l;
+        float2 fe = make_float2(0.f, 0.f);
+        if (ok) {
+#pragma unroll
+            for (int m = 0; m < NB; m++) {
+                const float2 bb = __ldg(R.basis32 + (size_t)m * R.nedge + e);
+                const float p = c.ah[m] * bb.x;
+                float er = fmaf(c.ah[m], bb.x, -p);
+                er = fmaf(c.ah[m], bb.y, er);
+                er = fmaf(c.al[m], bb.x, er);
+                float s2, e2;
+                two_sum(sh, p, s2, e2);
+                sh = s2;
+                sl += e2 + er;
+            }
+            fe = __ldg(R.fe32 + e);
+        }
+        const int b = base + lane;
+        const bool use = lane < 31 && b < R.nb && (!M.cutoff || __ldg(R.fm + b) <= fisco);
+#pragma unroll
+        for (int d = 0; d < NDET; d++) {
+            const float p = c.tauh[d] * fe.x;
+            float er = fmaf(c.tauh[d], fe.x, -p);
+            er = fmaf(c.tauh[d], fe.y, er);
+            er = fmaf(c.taul[d], fe.x, er);
+            float s2, e2;
+            two_sum(sh, p, s2, e2);
+            const float n = rintf(s2);
+            const float r = (s2 - n) + (sl + (e2 + er));
+            float sv, cv;
+            __sincosf(r * 6.283185307179586f, &sv, &cv);
+            const float Er = cv, Ei = -sv;
+            const float Nr = __shfl_down_sync(0xffffffffu, Er, 1);
+            const float Ni = __shfl_down_sync(0xffffffffu, Ei, 1);
+            if (use) {
+                const float idl = __ldg(R.inv_de_f + b);
+                const float Sr = Er + Nr, Si = Ei + Ni;
+                const float Dr = (Nr - Er) * idl, Di = (Ni - Ei) * idl;
+                const size_t o = (size_t)d * R.nb + b;
+                const float2 a0 = __ldg(R.A0f + o), a1 = __ldg(R.A1f + o);
+                yr[d] += 0.5f * (a0.x * Sr + a0.y * Si) + (a1.x * Dr + a1.y * Di);
+                yi[d] += 0.5f * (a0.y * Sr - a0.x * Si) + (a1.y * Dr - a1.x * Di);
+                hh[d] += 0.25f * __ldg(R.B0f + o) * (Sr * Sr + Si * Si) + __ldg(R.B1f + o) * (Sr * Dr + Si * Di);
+            }
+        }
+    }
+#pragma unroll
+    for (int d = 0; d < NDET; d++) { Yr[d] = yr[d]; Yi[d] = yi[d]; H[d] = hh[d]; }
+}
+
+// log L of one point from the relative-binning sums (lane 0 holds the result).
+template <int NDET, int PREC>
+__device__ __forceinline__ double rb_loglike_warp(const Model &M, const RBTables &R, const Coef &c,
+                                                  const CoefMixed &cm, int lane) {
+    double Yr[NDET], Yi[NDET], H[NDET];
+    if (PREC == 0) rb_fp64<NDET>(M, R, c, lane, Yr, Yi, H);
+    else rb_mixed<NDET>(M, R, cm, c.fisco, lane, Yr, Yi, H);
+    double v = 0.0;
+#pragma unroll
+    for (int d = 0; d < NDET; d++) {
+        double yr = Yr[d], yi = Yi[d], h = H[d];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            yr += __shfl_xor_sync(0xffffffffu, yr, o);
+            yi += __shfl_xor_sync(0xffffffffu, yi, o);
+            h += __shfl_xor_sync(0xffffffffu, h, o);
+        }
+        // rho = conj(G)/conj(G0)
+        const double g0r = R.fid->gre[d], g0i = R.fid->gim[d];
+        const double den = g0r * g0r + g0i * g0i;
+        const double rr = (c.gre[d] * g0r + c.gim[d] * g0i) / den;
+        const double ri = -(c.gim[d] * g0r - c.gre[d] * g0i) / den;
+        v += (rr * yr + ri * yi) - 0.5 * (rr * rr + ri * ri) * h;
+    }
+    return v;
 }
 
 }  // namespace gwns

@@ -228,7 +228,7 @@ __device__ __forceinline__ void warp_point_coef(const Model &M, const Tables &T,
         point_coef_warp(M, T, in, coef);
     }
     __syncwarp();
-    if (precision == 1) coef_to_mixed_warp(*coef, M.n_det, cm);
+    if (precision == 1) coef_to_mixed_warp(*coef, M.n_det, cm, M.rb ? T.rb.fid : nullptr);
     (void)lane;
 }
 
@@ -247,6 +247,15 @@ __global__ void __launch_bounds__(W * 32) k_eval(Model M, Tables T, const double
     __syncthreads();
     if ((threadIdx.x >> 5) == 0) warp_point_coef(M, T, pt, in_is_theta, PREC, &coef, &cm);
     __syncthreads();
+    if (M.rb) {
+        // relative-binning sums: one warp
+        if ((threadIdx.x >> 5) == 0) {
+            const int lane = threadIdx.x & 31;
+            const double v = rb_loglike_warp<NDET, PREC>(M, T.rb, coef, cm, lane);
+            if (lane == 0) logl[i] = v;
+        }
+        return;
+    }
     cta_loglike_bins<PREC, NDET, W>(M, T, coef, cm, red, &lval);
     if (threadIdx.x == 0) logl[i] = lval;
 }
@@ -458,26 +467,85 @@ cudaError_t launch_cov_chol(const Model &M, const StepArgs &A, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------ slice update
-enum { PH_NEWSTEP = 0, PH_LEFT = 1, PH_RIGHT = 2, PH_SHRINK = 3, PH_DONE = 4 };
+// One CTA per chain, S warps ("slots"). Warp 0 owns the chain: the point x,
+// the direction e and the bracket (lane i < d holds coordinate i). Every slice
+// step draws a direction and a bracket offset, steps out to the left and to the
+// right, then shrinks (Neal 2003, Sec. 4, along a hit-and-run direction).
+//
+// The candidates of each stage form sequences fixed by the draws alone:
+// stepping out to the left visits x + (a - q) e, to the right x + (b + q) e,
+// and the q-th shrink draw is determined once the earlier draws are known to be
+// rejected. Each round, warp 0 plans the next S candidates of these sequences
+// that lie inside the prior box and are not yet evaluated; every slot warp
+// computes one candidate's coefficients and bins; warp 0 then consumes the
+// results strictly in the sequential order (left stepping out, right stepping
+// out, shrinkage) and keeps results it could not consume yet in a small cache.
+// Evaluations the sequential order never reaches are discarded. The trajectory,
+// the evaluation count and every draw are those of the sequential algorithm;
+// the slots only shorten the chain's critical path.
+enum { PH_NEWSTEP = 0, PH_OUT = 1, PH_SHRINK = 2, PH_DONE = 3 };
+enum { KIND_L = 0, KIND_R = 1, KIND_SH = 2 };
+constexpr int CACHE_MAX = 16;
 
-// Warp-0 chain state; lane i < d holds coordinate i of x, e and y.
 struct Chain {
-    double x, e, y, lrow[MAXD];
-    double lx, a, b, t;
-    int s, phase, nout, nsh, caps;
+    double x, e, lrow[MAXD];
+    double lx, a, b;
+    int s, phase, nl, nr, nsh, caps, left_done, right_done;
     long long evals;
     unsigned long long bins;
+    // cache of evaluated, not yet consumed candidates
+    int ncache;
+    int ckind[CACHE_MAX], cidx[CACHE_MAX], cbins[CACHE_MAX];
+    double cval[CACHE_MAX];
 };
 
-// Advance the chain until a candidate needs a likelihood evaluation (returns
-// true, candidate in c.y and ysh) or the chain has finished (false). The
-// sequence of draws and decisions follows the oracle's loops exactly.
-__device__ bool chain_advance(const Model &M, const StepArgs &A, Chain &c, int chain, uint32_t iter,
-                              double *ysh) {
+__device__ __forceinline__ bool warp_inbox(double y, int lane, int d) {
+    return __all_sync(0xffffffffu, lane >= d || (y >= 0.0 && y <= 1.0));
+}
+
+__device__ __forceinline__ int cache_find(const Chain &c, int kind, int idx) {
+    for (int i = 0; i < c.ncache; i++)
+        if (c.ckind[i] == kind && c.cidx[i] == idx) return i;
+    return -1;
+}
+
+__device__ __forceinline__ void cache_drop(Chain &c, int i) {
+    c.ncache--;
+    c.ckind[i] = c.ckind[c.ncache];
+    c.cidx[i] = c.cidx[c.ncache];
+    c.cval[i] = c.cval[c.ncache];
+    c.cbins[i] = c.cbins[c.ncache];
+}
+
+// Drop every cached result of one stepping-out side (once that side has ended,
+// its later candidates are never consumed).
+__device__ __forceinline__ void cache_purge(Chain &c, int kind) {
+    for (int i = c.ncache - 1; i >= 0; i--)
+        if (c.ckind[i] == kind) cache_drop(c, i);
+}
+
+__device__ __forceinline__ void end_side(Chain &c, bool left) {
+    if (left) { c.left_done = 1; cache_purge(c, KIND_L); }
+    else { c.right_done = 1; cache_purge(c, KIND_R); }
+}
+
+__device__ __forceinline__ double shrink_t(const StepArgs &A, double a, double b, int nsh, int step,
+                                           int chain, uint32_t iter) {
+    const uint4 w = draw(A.seed, SLOT_SHRINK0 + (uint32_t)nsh, (uint32_t)step, (uint32_t)chain, iter);
+    return __dadd_rn(a, __dmul_rn(__dsub_rn(b, a), u01(w.x, w.y)));
+}
+
+// Apply every transition that needs no new evaluation: new steps (direction and
+// bracket draws), cap and prior-box outcomes, and results already in the cache.
+// Returns when the next transition needs an evaluation not in the cache, or the
+// chain is done.
+__device__ void chain_run(const Model &M, const StepArgs &A, Chain &c, int chain, uint32_t iter,
+                          double lstar) {
     const int lane = threadIdx.x & 31, d = M.dim;
-    for (int guard = 0; guard < 1 << 20; guard++) {
+    for (int guard = 0; guard < (1 << 22); guard++) {
+        if (c.phase == PH_DONE) return;
         if (c.phase == PH_NEWSTEP) {
-            if (c.s >= A.steps) { c.phase = PH_DONE; return false; }
+            if (c.s >= A.steps) { c.phase = PH_DONE; return; }
             // direction e = L z / |z|, z ~ N(0, I) by Box-Muller, two normals per draw
             double z = 0.0;
             if (lane < d) {
@@ -499,82 +567,129 @@ __device__ bool chain_advance(const Model &M, const StepArgs &A, Chain &c, int c
             const double r = u01(w.x, w.y);
             c.a = -r;
             c.b = 1.0 - r;
-            c.nout = 0;
-            c.phase = PH_LEFT;
+            c.nl = c.nr = c.nsh = 0;
+            c.left_done = c.right_done = 0;
+            c.ncache = 0;
+            c.phase = PH_OUT;
             continue;
         }
-        double t;
-        if (c.phase == PH_LEFT || c.phase == PH_RIGHT) {
-            if (c.nout >= A.max_stepout) {
-                if (c.phase == PH_LEFT) { c.phase = PH_RIGHT; c.nout = 0; }
-                else { c.phase = PH_SHRINK; c.nsh = 0; }
+        if (c.phase == PH_OUT) {
+            const bool left = !c.left_done;
+            if (!left && c.right_done) { c.phase = PH_SHRINK; continue; }
+            const int n = left ? c.nl : c.nr;
+            if (n >= A.max_stepout) {
+                end_side(c, left);
                 continue;
             }
-            t = (c.phase == PH_LEFT) ? c.a : c.b;
-        } else {  // PH_SHRINK
-            if (c.nsh >= A.max_shrink) {
-                c.caps++;
+            const double t = left ? c.a : c.b;
+            const double y = (lane < d) ? __dadd_rn(c.x, __dmul_rn(t, c.e)) : 0.5;
+            if (!warp_inbox(y, lane, d)) {
+                end_side(c, left);
+                continue;
+            }
+            const int ci = cache_find(c, left ? KIND_L : KIND_R, n);
+            if (ci < 0) return;
+            const bool in = c.cval[ci] > lstar;
+            c.evals++;
+            c.bins += (unsigned long long)c.cbins[ci];
+            cache_drop(c, ci);
+            if (left) { if (in) { c.a -= 1.0; c.nl++; } else end_side(c, true); }
+            else { if (in) { c.b += 1.0; c.nr++; } else end_side(c, false); }
+            continue;
+        }
+        // PH_SHRINK
+        if (c.nsh >= A.max_shrink) {
+            c.caps++;
+            c.s++;
+            c.phase = PH_NEWSTEP;
+            continue;
+        }
+        const double t = shrink_t(A, c.a, c.b, c.nsh, c.s, chain, iter);
+        const double y = (lane < d) ? __dadd_rn(c.x, __dmul_rn(t, c.e)) : 0.5;
+        if (warp_inbox(y, lane, d)) {
+            const int ci = cache_find(c, KIND_SH, c.nsh);
+            if (ci < 0) return;
+            const double val = c.cval[ci];
+            c.evals++;
+            c.bins += (unsigned long long)c.cbins[ci];
+            cache_drop(c, ci);
+            if (val > lstar) {
+                c.x = y;
+                c.lx = val;
                 c.s++;
                 c.phase = PH_NEWSTEP;
                 continue;
             }
-            const uint4 w = draw(A.seed, SLOT_SHRINK0 + (uint32_t)c.nsh, (uint32_t)c.s, (uint32_t)chain, iter);
-            t = __dadd_rn(c.a, __dmul_rn(__dsub_rn(c.b, c.a), u01(w.x, w.y)));
         }
-        c.t = t;
-        c.y = (lane < d) ? __dadd_rn(c.x, __dmul_rn(t, c.e)) : 0.5;
-        const bool inbox = __all_sync(0xffffffffu, c.y >= 0.0 && c.y <= 1.0);
-        if (inbox) {
-            if (lane < d) ysh[lane] = c.y;
-            return true;
-        }
-        // outside the prior box: not in the slice, no evaluation
-        if (c.phase == PH_LEFT) { c.phase = PH_RIGHT; c.nout = 0; }
-        else if (c.phase == PH_RIGHT) { c.phase = PH_SHRINK; c.nsh = 0; }
-        else {
-            if (t < 0.0) c.a = t; else c.b = t;
-            c.nsh++;
-        }
+        if (t < 0.0) c.a = t; else c.b = t;
+        c.nsh++;
     }
-    c.phase = PH_DONE;   // unreachable for valid caps; keeps the loop bounded
-    return false;
+    c.phase = PH_DONE;   // unreachable with finite caps; keeps the loop bounded
 }
 
-// Consume the likelihood of the pending candidate.
-__device__ __forceinline__ void chain_consume(Chain &c, double ly, double lstar) {
-    c.evals++;
-    const bool in = ly > lstar;
-    if (c.phase == PH_LEFT) {
-        if (in) { c.a -= 1.0; c.nout++; } else { c.phase = PH_RIGHT; c.nout = 0; }
-    } else if (c.phase == PH_RIGHT) {
-        if (in) { c.b += 1.0; c.nout++; } else { c.phase = PH_SHRINK; c.nsh = 0; }
-    } else {
-        if (in) {
-            c.x = c.y;
-            c.lx = ly;
-            c.s++;
-            c.phase = PH_NEWSTEP;
-        } else {
-            if (c.t < 0.0) c.a = c.t; else c.b = c.t;
-            c.nsh++;
+// Plan up to S candidates to evaluate in the next round (in-box, not cached),
+// continuing the current stage's sequences. Writes their coordinates to
+// ysh[slot][*] and their keys to pk/pi; returns the number of slots used.
+template <int S>
+__device__ int chain_plan(const Model &M, const StepArgs &A, const Chain &c, int chain, uint32_t iter,
+                          double (*ysh)[MAXD], int *pk, int *pidx) {
+    const int lane = threadIdx.x & 31, d = M.dim;
+    int ns = 0;
+    const int room = CACHE_MAX - c.ncache;
+    const int cap = S < room ? S : room;
+    if (c.phase == PH_OUT) {
+        // the side in progress first (half the slots if the other side is
+        // still open), then the other side; each looks at most S candidates
+        // ahead of its consumed position, so the cache holds at most 2S entries
+        for (int side = 0; side < 2 && ns < cap; side++) {
+            const bool left = (side == 0);
+            if (left ? c.left_done : c.right_done) continue;
+            const int limit = (left && !c.right_done) ? (cap + 1) / 2 : cap;
+            double t = left ? c.a : c.b;
+            const int n0 = left ? c.nl : c.nr;
+            for (int n = n0; n < n0 + S && n < A.max_stepout && ns < limit; n++) {
+                const double y = (lane < d) ? __dadd_rn(c.x, __dmul_rn(t, c.e)) : 0.5;
+                if (!warp_inbox(y, lane, d)) break;
+                if (cache_find(c, left ? KIND_L : KIND_R, n) < 0) {
+                    if (lane < d) ysh[ns][lane] = y;
+                    pk[ns] = left ? KIND_L : KIND_R;
+                    pidx[ns] = n;
+                    ns++;
+                }
+                if (left) t -= 1.0; else t += 1.0;
+            }
+        }
+    } else if (c.phase == PH_SHRINK) {
+        double a = c.a, b = c.b;
+        for (int n = c.nsh; n < c.nsh + S && n < A.max_shrink && ns < cap; n++) {
+            const double t = shrink_t(A, a, b, n, c.s, chain, iter);
+            const double y = (lane < d) ? __dadd_rn(c.x, __dmul_rn(t, c.e)) : 0.5;
+            if (warp_inbox(y, lane, d) && cache_find(c, KIND_SH, n) < 0) {
+                if (lane < d) ysh[ns][lane] = y;
+                pk[ns] = KIND_SH;
+                pidx[ns] = n;
+                ns++;
+            }
+            if (t < 0.0) a = t; else b = t;     // as if rejected
         }
     }
+    return ns;
 }
 
-template <int PREC, int NDET, int W>
-__global__ void __launch_bounds__(W * 32) k_slice(Model M, Tables T, StepArgs A) {
-    __shared__ Coef coef;
-    __shared__ CoefMixed cm;
-    __shared__ double red[W][2 * MAXDET];
-    __shared__ double lval;
-    __shared__ double ysh[MAXD];
-    __shared__ int finished;
+template <int PREC, int NDET, int S>
+__global__ void __launch_bounds__(S * 32) k_slice(Model M, Tables T, StepArgs A) {
+    __shared__ Coef coef[S];
+    __shared__ CoefMixed cm[S];
+    __shared__ double ysh[S][MAXD];
+    __shared__ double lval[S];
+    __shared__ int nslot;
     const int chain = blockIdx.x;
     if (chain >= A.k) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, d = M.dim;
     const uint32_t iter = (uint32_t)A.state->iter;
     const double lstar = A.state->lstar;
     Chain c;
+    int pk[S], pidx[S];
     if (warp == 0) {
         const int m = A.n - A.k;
         const uint4 w = draw(A.seed, 0u, STEP_START, (uint32_t)chain, iter);
@@ -584,24 +699,72 @@ __global__ void __launch_bounds__(W * 32) k_slice(Model M, Tables T, StepArgs A)
         c.x = (lane < d) ? A.live_u[(size_t)src * d + lane] : 0.0;
         c.lx = A.live_logl[src];
         for (int j = 0; j < MAXD; j++) c.lrow[j] = (lane < d && j < d) ? A.chol[lane * d + j] : 0.0;
-        c.e = 0.0; c.y = 0.0; c.a = 0.0; c.b = 0.0; c.t = 0.0;
-        c.s = 0; c.phase = PH_NEWSTEP; c.nout = 0; c.nsh = 0; c.caps = 0; c.evals = 0; c.bins = 0;
+        c.e = 0.0; c.a = 0.0; c.b = 0.0;
+        c.s = 0; c.phase = PH_NEWSTEP; c.nl = c.nr = c.nsh = 0; c.caps = 0; c.evals = 0; c.bins = 0;
+        c.left_done = c.right_done = 0; c.ncache = 0;
     }
     for (;;) {
         if (warp == 0) {
-            const bool need = chain_advance(M, A, c, chain, iter, ysh);
-            if (lane == 0) finished = need ? 0 : 1;
-            __syncwarp();
-            if (need) warp_point_coef(M, T, ysh, 0, PREC, &coef, &cm);
+            chain_run(M, A, c, chain, iter, lstar);
+            int ns = (c.phase == PH_DONE) ? 0 : chain_plan<S>(M, A, c, chain, iter, ysh, pk, pidx);
+            if (ns == 0 && c.phase != PH_DONE) {
+                // cannot happen with the bounds above; end the chain at its
+                // current (in-slice) point and flag the run state
+                c.phase = PH_DONE;
+                if (lane == 0) atomicOr(&A.state->status, 1);
+            }
+            if (lane == 0) nslot = ns;
         }
         __syncthreads();
-        if (finished) break;
-        cta_loglike_bins<PREC, NDET, W>(M, T, coef, cm, red, &lval);
-        if (warp == 0) {
-            __syncwarp();
-            if (coef.jcut >= 0) c.bins += (unsigned long long)(coef.jcut + 1);
-            chain_consume(c, lval, lstar);
+        const int ns = nslot;
+        if (ns == 0) break;
+        // coefficients: warp w computes candidates 4w .. 4w+3 (8 lanes each)
+        if (M.model == M_TOY) {
+            if (warp < ns) point_coef_warp(M, T, ysh[warp], &coef[warp]);
+        } else if (4 * warp < ns) {
+            const int cnt = ns - 4 * warp < 4 ? ns - 4 * warp : 4;
+            point_coef_group(M, T, ysh[4 * warp], MAXD, &coef[4 * warp], cnt, PREC == 0 ? 32 : 0);
         }
+        __syncthreads();
+        if (warp < ns && M.rb) {
+            // relative-binning likelihood of the slot's candidate
+            if (PREC == 1) {
+                coef_to_mixed_warp(coef[warp], M.n_det, &cm[warp], T.rb.fid);
+                __syncwarp();
+            }
+            const double v = rb_loglike_warp<NDET, PREC>(M, T.rb, coef[warp], cm[warp], lane);
+            if (lane == 0) {
+                lval[warp] = v;
+                coef[warp].jcut = T.rb.nb - 1;     // bins counted for the work statistics
+            }
+        } else if (warp < ns) {
+            // one candidate per slot warp: bins and warp reduction
+            if (PREC == 1) {
+                coef_to_mixed_warp(coef[warp], M.n_det, &cm[warp]);
+                __syncwarp();
+            }
+            double zr[NDET], zi[NDET];
+            if (PREC == 0) bins_fp64<NDET, true>(T, M.N, M.f0, M.df, coef[warp], lane, 32, zr, zi);
+            else bins_mixed<NDET>(T, M.N, cm[warp], coef[warp].jcut, lane, 32, zr, zi);
+            double v = 0.0;
+#pragma unroll
+            for (int dd = 0; dd < NDET; dd++) {
+                const double ZR = warp_sum(zr[dd]), ZI = warp_sum(zi[dd]);
+                v += coef[warp].gre[dd] * ZR - coef[warp].gim[dd] * ZI;
+            }
+            if (lane == 0) lval[warp] = (M.model == M_TOY) ? coef[warp].toy : v - 0.5 * coef[warp].hh;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            for (int sl = 0; sl < ns; sl++) {
+                c.ckind[c.ncache] = pk[sl];
+                c.cidx[c.ncache] = pidx[sl];
+                c.cval[c.ncache] = lval[sl];
+                c.cbins[c.ncache] = coef[sl].jcut + 1;
+                c.ncache++;
+            }
+        }
+        // coef/lval are rewritten only after the next barrier's plan
     }
     if (warp == 0) {
         const int dst = A.order[chain];
@@ -616,8 +779,8 @@ __global__ void __launch_bounds__(W * 32) k_slice(Model M, Tables T, StepArgs A)
 }
 
 template <int PREC, int NDET>
-static cudaError_t slice_w(const Model &M, const Tables &T, int warps, const StepArgs &A, cudaStream_t s) {
-    switch (warps) {
+static cudaError_t slice_w(const Model &M, const Tables &T, int slots, const StepArgs &A, cudaStream_t s) {
+    switch (slots) {
         case 1: k_slice<PREC, NDET, 1><<<A.k, 32, 0, s>>>(M, T, A); break;
         case 2: k_slice<PREC, NDET, 2><<<A.k, 64, 0, s>>>(M, T, A); break;
         case 4: k_slice<PREC, NDET, 4><<<A.k, 128, 0, s>>>(M, T, A); break;
@@ -627,18 +790,18 @@ static cudaError_t slice_w(const Model &M, const Tables &T, int warps, const Ste
 }
 
 template <int PREC>
-static cudaError_t slice_d(const Model &M, const Tables &T, int warps, const StepArgs &A, cudaStream_t s) {
+static cudaError_t slice_d(const Model &M, const Tables &T, int slots, const StepArgs &A, cudaStream_t s) {
     switch (M.n_det) {
-        case 1: return slice_w<PREC, 1>(M, T, warps, A, s);
-        case 2: return slice_w<PREC, 2>(M, T, warps, A, s);
-        case 3: return slice_w<PREC, 3>(M, T, warps, A, s);
-        default: return slice_w<PREC, 4>(M, T, warps, A, s);
+        case 1: return slice_w<PREC, 1>(M, T, slots, A, s);
+        case 2: return slice_w<PREC, 2>(M, T, slots, A, s);
+        case 3: return slice_w<PREC, 3>(M, T, slots, A, s);
+        default: return slice_w<PREC, 4>(M, T, slots, A, s);
     }
 }
 
-cudaError_t launch_slice(const Model &M, const Tables &T, int precision, int warps, const StepArgs &A,
+cudaError_t launch_slice(const Model &M, const Tables &T, int precision, int slots, const StepArgs &A,
                          cudaStream_t s) {
-    return precision == 1 ? slice_d<1>(M, T, warps, A, s) : slice_d<0>(M, T, warps, A, s);
+    return precision == 1 ? slice_d<1>(M, T, slots, A, s) : slice_d<0>(M, T, slots, A, s);
 }
 
 // ------------------------------------------------------------------ finish
@@ -858,6 +1021,121 @@ __global__ void k_waveform_bins(Model M, Tables T, const Coef *cp, double *h_re,
             h_im[(size_t)d * M.N + j] = im;
         }
     }
+}
+
+// ------------------------------------------------------- relative binning setup
+// Coarse-bin edges: B+1 geometric frequencies f0 (f_last/f0)^(b/B), moved to the
+// nearest grid index, repeated indices dropped (one thread: B is ~1e3).
+__global__ void k_rb_edges(Model M, int B, int *J, int *nedge) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double flo = M.f0, fhi = __dadd_rn(M.f0, __dmul_rn((double)(M.N - 1), M.df));
+    int n = 0;
+    for (int b = 0; b <= B; b++) {
+        const double target = flo * pow(fhi / flo, (double)b / B);
+        int j = (int)floor((target - M.f0) / M.df + 0.5);
+        j = j < 0 ? 0 : (j > M.N - 1 ? M.N - 1 : j);
+        if (b == B) j = M.N - 1;
+        if (n == 0 || j > J[n - 1]) J[n++] = j;
+    }
+    *nedge = n;
+}
+
+// Fiducial strain without cutoff on the fine grid: h0 = conj(G0) f^(-7/6) exp(-i Psi0).
+__global__ void k_rb_h0(Model M, Tables T, const Coef *fid, double2 *h0) {
+    const Coef &c = *fid;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < M.N; j += gridDim.x * blockDim.x) {
+        const double f = T.f64[j];
+        double psi0 = c.c0;
+        for (int m = 0; m < NB; m++) psi0 += c.a[m] * T.basis64[(size_t)m * M.N + j];
+        const double amp = pow(f, -7.0 / 6.0);
+        for (int d = 0; d < M.n_det; d++) {
+            double s, co;
+            sincos(psi0 + TWO_PI_D * f * c.tau[d], &s, &co);
+            h0[(size_t)d * M.N + j] = make_double2(amp * (c.gre[d] * co - c.gim[d] * s),
+                                                   amp * (-c.gre[d] * s - c.gim[d] * co));
+        }
+    }
+}
+
+// Summary data of bin b (blockIdx.x) and detector d (blockIdx.y), plus the edge
+// tables (from block (b, 0)).
+__global__ void __launch_bounds__(256) k_rb_summary(Model M, const int *J, const int *nedge_p,
+                                                    const double *dre, const double *dim, const double *psd,
+                                                    const double2 *h0, RBTables R, double *fe, double *basis64,
+                                                    float2 *basis32, float2 *fe32, double *fm, double *inv_de,
+                                                    double2 *A0, double2 *A1, double *B0, double *B1, float2 *A0f,
+                                                    float2 *A1f, float *B0f, float *B1f, float *inv_de_f) {
+    __shared__ double scratch[32];
+    const int nedge = *nedge_p, nb = nedge - 1;
+    const int b = blockIdx.x, d = blockIdx.y;
+    if (b >= nb) return;
+    const int lo = J[b], hi = (b == nb - 1) ? J[b + 1] + 1 : J[b + 1];
+    const double elo = __dadd_rn(M.f0, __dmul_rn((double)J[b], M.df));
+    const double ehi = __dadd_rn(M.f0, __dmul_rn((double)J[b + 1], M.df));
+    const double fmid = 0.5 * (elo + ehi);
+    double a0r = 0, a0i = 0, a1r = 0, a1i = 0, b0 = 0, b1 = 0;
+    for (int j = lo + threadIdx.x; j < hi; j += blockDim.x) {
+        const size_t o = (size_t)d * M.N + j;
+        const double f = __dadd_rn(M.f0, __dmul_rn((double)j, M.df));
+        const double w = 4.0 * M.df / psd[o];
+        const double2 h = h0[o];
+        const double xr = dre[o] * h.x + dim[o] * h.y;      // d h0^*
+        const double xi = dim[o] * h.x - dre[o] * h.y;
+        const double hh = h.x * h.x + h.y * h.y;
+        a0r += w * xr; a0i += w * xi;
+        a1r += w * xr * (f - fmid); a1i += w * xi * (f - fmid);
+        b0 += w * hh; b1 += w * hh * (f - fmid);
+    }
+    a0r = block_sum(a0r, scratch); a0i = block_sum(a0i, scratch);
+    a1r = block_sum(a1r, scratch); a1i = block_sum(a1i, scratch);
+    b0 = block_sum(b0, scratch); b1 = block_sum(b1, scratch);
+    if (threadIdx.x == 0) {
+        const size_t o = (size_t)d * nb + b;
+        A0[o] = make_double2(a0r, a0i);
+        A1[o] = make_double2(a1r, a1i);
+        B0[o] = b0;
+        B1[o] = b1;
+        A0f[o] = make_float2((float)a0r, (float)a0i);
+        A1f[o] = make_float2((float)a1r, (float)a1i);
+        B0f[o] = (float)b0;
+        B1f[o] = (float)b1;
+        if (d == 0) {
+            fm[b] = fmid;
+            inv_de[b] = 1.0 / (ehi - elo);
+            inv_de_f[b] = (float)(1.0 / (ehi - elo));
+        }
+    }
+    // edge tables: edge b (and the last edge from the last bin)
+    if (d == 0 && threadIdx.x < 2) {
+        const int e = b + threadIdx.x;
+        if (threadIdx.x == 1 && b != nb - 1) return;
+        const double f = __dadd_rn(M.f0, __dmul_rn((double)J[e], M.df));
+        const double lf = log(f), cb = cbrt(f), ic = 1.0 / cb;
+        double Bv[NB] = {ic * ic * ic * ic * ic, 1.0 / f, ic * ic, ic, lf, cb, cb * lf, cb * cb};
+        for (int m = 0; m < NB; m++) {
+            basis64[(size_t)m * nedge + e] = Bv[m];
+            const float h = __double2float_rn(Bv[m]);
+            basis32[(size_t)m * nedge + e] = make_float2(h, __double2float_rn(Bv[m] - (double)h));
+        }
+        fe[e] = f;
+        const float h = __double2float_rn(f);
+        fe32[e] = make_float2(h, __double2float_rn(f - (double)h));
+    }
+}
+
+cudaError_t launch_rb_setup(const Model &M, const Tables &T, int B, const double *theta_fid, int *J,
+                            int *nedge_dev, Coef *fid, double2 *h0_tmp, const double *dre, const double *dim,
+                            const double *psd, RBTables &R, double *fe, double *basis64, float2 *basis32,
+                            float2 *fe32, double *fm, double *inv_de, double2 *A0, double2 *A1, double *B0,
+                            double *B1, float2 *A0f, float2 *A1f, float *B0f, float *B1f, float *inv_de_f,
+                            cudaStream_t s) {
+    k_rb_edges<<<1, 1, 0, s>>>(M, B, J, nedge_dev);
+    k_waveform_coef<<<1, 32, 0, s>>>(M, T, theta_fid, fid);
+    k_rb_h0<<<min((M.N + 255) / 256, 1216), 256, 0, s>>>(M, T, fid, h0_tmp);
+    dim3 grid(B, M.n_det);
+    k_rb_summary<<<grid, 256, 0, s>>>(M, J, nedge_dev, dre, dim, psd, h0_tmp, R, fe, basis64, basis32, fe32,
+                                      fm, inv_de, A0, A1, B0, B1, A0f, A1f, B0f, B1f, inv_de_f);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_point_coef(const Model &M, const Tables &T, const double *theta, Coef *out,

@@ -78,6 +78,12 @@ cudaError_t launch_final_live(const Model &M, const StepArgs &A, double *fin_u, 
                               double *fin_logw, double *fin_nlive, double *logz_total, cudaStream_t s);
 cudaError_t launch_result_stats(const ResultArgs &R, cudaStream_t s);
 cudaError_t launch_theta(const Model &M, const double *u, long long m, double *theta, cudaStream_t s);
+cudaError_t launch_rb_setup(const Model &M, const Tables &T, int B, const double *theta_fid, int *J,
+                            int *nedge_dev, Coef *fid, double2 *h0_tmp, const double *dre, const double *dim,
+                            const double *psd, RBTables &R, double *fe, double *basis64, float2 *basis32,
+                            float2 *fe32, double *fm, double *inv_de, double2 *A0, double2 *A1, double *B0,
+                            double *B1, float2 *A0f, float2 *A1f, float *B0f, float *B1f, float *inv_de_f,
+                            cudaStream_t s);
 cudaError_t launch_point_coef(const Model &M, const Tables &T, const double *theta, Coef *out,
                               cudaStream_t s);
 cudaError_t launch_waveform(const Model &M, const Tables &T, const double *theta, Coef *scratch,

@@ -160,19 +160,21 @@ def test_no_cutoff_and_empty_band(gw):
 
 
 # ------------------------------------------------------------ sampler parity
-def _ns_pair(gw, name, n_live, k, precision=0, **over):
+def _ns_pair(gw, name, n_live, k, precision=0, slots=0, **over):
     w, pb, th = problem(name, **over)
     sp = sampler_from(gw, pb, precision, n_live=n_live, k=k, steps_per_dim=w.steps_per_dim,
-                      seed=w.seed_sampler)
+                      seed=w.seed_sampler, slots=slots)
     st = ons.initial_state(pb, n_live, w.seed_sampler)
     return w, pb, sp, st
 
 
+@pytest.mark.parametrize("slots", [1, 2, 4, 8])
 @pytest.mark.parametrize("name,n_live,k,iters", [("c0", 200, 100, 4), ("c1", 120, 60, 2)])
-def test_ns_iterations_match_oracle(gw, name, n_live, k, iters):
+def test_ns_iterations_match_oracle(gw, name, n_live, k, iters, slots):
     """Same Philox draws on both sides: the live set after each iteration and
-    the evidence bookkeeping match the oracle's."""
-    w, pb, sp, st = _ns_pair(gw, name, n_live, k)
+    the evidence bookkeeping match the oracle's, whatever the number of
+    speculative candidate slots per chain."""
+    w, pb, sp, st = _ns_pair(gw, name, n_live, k, slots=slots)
     u0, l0 = sp.live()
     assert np.max(np.abs(u0 - st.live_u)) == 0.0
     assert np.max(np.abs(l0 - st.live_logl) / np.maximum(1, np.abs(st.live_logl))) < FP64_RTOL
@@ -187,6 +189,7 @@ def test_ns_iterations_match_oracle(gw, name, n_live, k, iters):
         assert s["logX"] == pytest.approx(st.logX, rel=1e-12)
         assert s["logZ"] == pytest.approx(st.logZ, rel=1e-9, abs=1e-9)
         assert s["evals"] == st.evals
+        assert s["status"] == 0
     sp.close()
 
 
@@ -269,3 +272,59 @@ def test_errors(gw):
         with pytest.raises(gw.GWNSError) as e:
             sp.step(-1)
         assert e.value.code == -3
+
+
+# ---------------------------------------------------------- relative binning
+@pytest.mark.parametrize("precision", [0, 1])
+def test_relative_binning_parity(gw, precision):
+    w, pb, th = problem("c1")
+    rb = oracle.RelativeBinning(pb, th, B=256)
+    u = pts_for(pb, th, count=80)
+    want = rb.loglike(u)
+    with sampler_from(gw, pb, precision, n_live=8, coarse_bins=256, theta_fid=th) as sp:
+        got = sp.eval_lnl(u)
+    if precision == 0:
+        assert np.max(np.abs(got - want) / np.maximum(1, np.abs(want))) < FP64_RTOL
+    else:
+        assert np.max(np.abs(got - want)) < MIXED_ATOL
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_relative_binning_full_size(gw, precision):
+    """519,169-bin grid on 1024 geometric coarse bins about the injection:
+    sampled points and the injection itself against the oracle, and the
+    coarse result at the fiducial point against the full-grid one."""
+    import torch
+    w, pb, th = problem("c4")
+    rb = oracle.RelativeBinning(pb, th, B=1024)
+    u = gi.unit_cube(29, 6, pb.dim)
+    want = rb.loglike(u)
+    with sampler_from(gw, pb, precision, n_live=8, coarse_bins=1024, theta_fid=th) as sp:
+        got = sp.eval_lnl(u)
+        g_inj = sp.eval_lnl_theta(torch.tensor(th[None], dtype=torch.float64, device="cuda")).item()
+    w_inj = rb.loglike_theta(th)[0]
+    full_inj = pb.loglike_theta(th)[0]
+    if precision == 0:
+        assert np.max(np.abs(got - want) / np.maximum(1, np.abs(want))) < FP64_RTOL
+        assert abs(g_inj - w_inj) / abs(w_inj) < FP64_RTOL
+    else:
+        assert np.max(np.abs(got - want)) < MIXED_ATOL
+        assert abs(g_inj - w_inj) < MIXED_ATOL
+    # bin-granular cutoff: a fraction of a coarse bin of signal at most
+    assert abs(w_inj - full_inj) < 0.02 * abs(full_inj)
+
+
+def test_relative_binning_iterations_match_oracle(gw):
+    w, pb, th = problem("c1")
+    rb = oracle.RelativeBinning(pb, th, B=256)
+    pbr = rb.problem()
+    n_live, k = 120, 60
+    st = ons.initial_state(pbr, n_live, w.seed_sampler)
+    with sampler_from(gw, pb, 0, n_live=n_live, k=k, steps_per_dim=w.steps_per_dim, seed=w.seed_sampler,
+                      coarse_bins=256, theta_fid=th) as sp:
+        for it in range(2):
+            ons.iterate(pbr, st, k, w.steps_per_dim * pb.dim, w.seed_sampler)
+            sp.step(k)
+            gu, gl = sp.live()
+            assert np.max(np.abs(gu - st.live_u)) < 1e-9
+            assert np.max(np.abs(gl - st.live_logl) / np.maximum(1, np.abs(st.live_logl))) < 1e-8

@@ -418,3 +418,42 @@ def test_detector_strain_is_delayed_geocentre_waveform():
                 continue
             hp, hc = oracle.polarizations(th2, f[j])
             assert h[j] == pytest.approx(fp * hp + fc * hc, rel=1e-9, abs=0)
+
+
+# --------------------------------------------------------- relative binning
+def _rb_problem():
+    w = gi.workload("c1")
+    w.N = 4017
+    pb, th = oracle.make_problem(w)
+    nocut = oracle.Problem(f0=pb.f0, df=pb.df, psd=pb.psd, data=pb.data(), pos=pb.pos, xarm=pb.xarm,
+                           yarm=pb.yarm, cutoff=False, kind=pb.kind, lo=pb.lo, hi=pb.hi)
+    return pb, nocut, th
+
+
+def test_relative_binning_exact_at_fiducial():
+    """At theta = theta_fid, r = 1 and the coarse sums reproduce the full-grid
+    inner products exactly (no cutoff: every fine bin is in some coarse bin)."""
+    pb, nocut, th = _rb_problem()
+    rb = oracle.RelativeBinning(nocut, th, B=256)
+    assert rb.J[0] == 0 and rb.J[-1] == pb.N - 1 and np.all(np.diff(rb.J) > 0)
+    assert rb.loglike_theta(th)[0] == pytest.approx(nocut.loglike_theta(th)[0], rel=1e-11)
+
+
+def test_relative_binning_close_near_fiducial():
+    """Near the fiducial point the linear interpolation of h/h0 inside each
+    coarse bin is accurate; the error grows away from it."""
+    pb, nocut, th = _rb_problem()
+    rb = oracle.RelativeBinning(nocut, th, B=256)
+    near, far = [], []
+    rng = np.random.default_rng(4)
+    for _ in range(8):
+        t = th.copy()
+        t[gi.P_MC] *= 1 + 1e-4 * rng.standard_normal()
+        t[gi.P_TC] += 1e-4 * rng.standard_normal()
+        t[gi.P_PHIC] += 0.1 * rng.standard_normal()
+        near.append(abs(rb.loglike_theta(t)[0] - nocut.loglike_theta(t)[0]))
+        t2 = th.copy()
+        t2[gi.P_MC] *= 1 + 3e-2
+        far.append(abs(rb.loglike_theta(t2)[0] - nocut.loglike_theta(t2)[0]))
+    assert max(near) < 1e-3
+    assert max(far) > 10 * max(near)
