@@ -48,7 +48,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # detectors, in FMA-equivalents: 8 basis FMAs + one sincos (32 FMA-equivalents
 # on this GPU) + per detector 4 (phasor product) + 4 (complex MAC) + 4
 # (phasor rotation). 1 FMA = 2 flops.
-K_SLICE_FP64_C1_DRAM_BYTES = 647680
+K_SLICE_FP64_C1_DRAM_BYTES = None   # re-captured after the kernel changes
 
 
 def fp64_flops_per_point_bin(n_det: int) -> float:
@@ -190,6 +190,9 @@ def run_gpu(args):
     # then K ns_step_host calls that copy each iteration's dead points to host
     e2e = e2e_run(g, w, args.steps, stream)
 
+    # the serving workload (64 analyses arriving at 2/s): p50/p99 time-to-logZ
+    serving = serving_stream(g) if rank == 0 else None
+
     if rank == 0:
         cpu = cpu_baseline() if ws == 1 else None
         out = {
@@ -202,6 +205,7 @@ def run_gpu(args):
                        "parallelism": f"replicas{ws}", "l2": "flushed before every timed step (256 MB write)"},
             "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
             "time_to_logZ": ttl,
+            "serving": serving,
             "e2e": e2e,
             "gpu_launches": 5 * args.steps + 1,   # 5 kernels per ns_step + the L2 flush fill
             "kernel_ms_per_step": [(b - a) / args.steps for a, b in zip(st0["kernel_ms"], st1["kernel_ms"])],
@@ -279,6 +283,63 @@ def e2e_run(g, w, steps, stream):
     return {"value": ev / (t1 - t0), "unit": UNIT, "h2d_bytes_per_step": h2d / steps,
             "d2h_bytes_per_step": k * (d + 2) * 8,
             "note": "ns_init from host arrays (data, PSD upload amortised over the steps) + ns_step_host"}
+
+
+def serving_stream(g, count=64, time_limit_s=240.0):
+    """The serving workload: `count` analyses arriving as a Poisson stream at
+    2/s (durations 4-64 s at 20-2048 Hz, n_live U{500..2000}, k = n/2, SNR
+    U[10, 40], 3 detectors, mixed precision), served by one ns_server that
+    interleaves the running analyses' iterations. Arrival -> result latency
+    per analysis (p50/p99) and the aggregate likelihood throughput."""
+    stream = gi.serving_stream(count=count)
+    reqs = []
+    for i, r in enumerate(stream):
+        w = gi.workload("c3", duration=r["duration"], n_live_c3=r["n_live"], snr_c3=r["snr"])
+        w.seed_noise += 10 * i
+        w.seed_injection += 10 * i
+        w.seed_sampler += 10 * i
+        sp, th = g.make_analysis(w, precision=g.NS_MIXED, n_live=2, k=1)
+        f = w.freqs()
+        psd = np.tile(gi.psd_analytic(f), (w.n_det, 1))
+        data = sp.waveform(th) + gi.noise(w.seed_noise, psd, w.df)
+        sp.close()
+        pos, xarm, yarm = gi.detectors(w.seed_geometry, w.n_det)
+        reqs.append((r["arrival_s"], dict(kind=w.kind, lo=w.lo, hi=w.hi, data=data, psd=psd, f0=w.f0, df=w.df,
+                                          pos=pos, xarm=xarm, yarm=yarm, n_live=w.n_live, k=w.k,
+                                          steps_per_dim=w.steps_per_dim, seed=w.seed_sampler)))
+    srv = g.Server(precision=g.NS_MIXED, max_active=16)
+    ids, arrival = [], []
+    t0 = srv.time()
+    nxt = 0
+    while True:
+        t = srv.time() - t0
+        while nxt < len(reqs) and reqs[nxt][0] <= t:
+            ids.append(srv.submit(**reqs[nxt][1]))
+            arrival.append(reqs[nxt][0])
+            nxt += 1
+        r, p = srv.tick()
+        if r == 0 and p == 0:
+            if nxt == len(reqs):
+                break
+            time.sleep(max(0.0, min(0.05, reqs[nxt][0] - (srv.time() - t0))))
+        if srv.time() - t0 > time_limit_s:
+            break
+    t_end = srv.time() - t0
+    lat, evals, logz = [], 0, []
+    for rid, ta in zip(ids, arrival):
+        st = srv.poll(rid)
+        if st["state"] == g.NS_REQ_DONE:
+            lat.append(st["t_done"] - t0 - ta)
+            evals += st["evals"]
+            logz.append(st["logZ"])
+    srv.close()
+    return {"requests": count, "completed": len(lat), "makespan_s": t_end,
+            "p50_time_to_logZ_s": float(np.percentile(lat, 50)) if lat else None,
+            "p99_time_to_logZ_s": float(np.percentile(lat, 99)) if lat else None,
+            "evals_per_s": evals / t_end if t_end > 0 else None,
+            "workload": "Poisson arrivals at 2/s; durations {4,8,16,32,64} s at 20-2048 Hz "
+                        "(8,113-129,793 bins); n_live U{500..2000}, k = n/2; SNR U[10,40]; 3 detectors; "
+                        "mixed precision; up to 16 analyses interleaved"}
 
 
 def oracle_sample(chains: int, iteration: int = 0):

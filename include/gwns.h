@@ -257,11 +257,78 @@ int ns_get_live(ns_ctx *ctx, double *u, double *logl);
 /* Overwrite the live set (host u [n][d], logl [n]); used to resume. */
 int ns_set_live(ns_ctx *ctx, const double *u, const double *logl);
 
+/* Autotune the slice update: time `trials` iterations (>= 1) with each slot
+ * count 1, 2, 4, 8 from the same saved state (live set, run state and dead
+ * list are restored afterwards, so the run continues as if untouched), keep
+ * the fastest for this context, and remember it for contexts of the same grid
+ * size, detector count, precision, n_live and k created later in the process
+ * (used when their options leave slots at 0). The slot count never changes
+ * results. *slots (may be NULL) receives the choice. */
+int ns_autotune(ns_ctx *ctx, int trials, int *slots);
+
 /* Synchronise the context's stream. */
 int ns_sync(ns_ctx *ctx);
 
 void ns_free(ns_ctx *ctx);
 const char *ns_strerror(int code);
+
+/* ------------------------------------------------------------- serving */
+/* A continuous-batching server of many analyses on one GPU. Requests (one
+ * analysis each: prior, data, PSD, grid, options) are queued by ns_submit; each
+ * ns_server_tick admits queued requests in arrival order while the number of
+ * running analyses is below max_active and their estimated device footprint
+ * fits the memory budget, then runs ONE nested-sampling iteration of every
+ * running analysis with one launch per iteration kernel (the slice updates of
+ * all their chains interleaved in the same launch), and retires the analyses
+ * that reached their stopping rule (their evidence, error and samples are kept
+ * on the host; their device memory is released). Every analysis keeps its own
+ * live set, Philox key and iteration counter on the device, so its result does
+ * not depend on which other analyses share the GPU. Not thread-safe. */
+typedef struct ns_server ns_server;
+
+typedef struct {
+    int max_active;        /* analyses interleaved at once [16] */
+    size_t mem_budget;     /* device bytes for running analyses [0: 80% of free memory] */
+    int precision;         /* NS_FP64 or NS_MIXED for every analysis */
+    int slots;             /* slice-update slots per chain for every analysis [0: 4] */
+    int max_iter;          /* iteration cap per analysis [100000] */
+    void *stream;          /* cudaStream_t [NULL: server-owned] */
+} ns_server_options;
+
+typedef struct {
+    ns_prior prior;
+    ns_data data;
+    ns_psd psd;
+    ns_grid grid;
+    ns_options opts;       /* precision, slots and stream are the server's */
+} ns_request;
+
+enum { NS_REQ_PENDING = 0, NS_REQ_RUNNING = 1, NS_REQ_DONE = 2, NS_REQ_CANCELLED = 3 };
+
+typedef struct {
+    int state;             /* NS_REQ_*, or a negative NS_ERR_* if its admission failed */
+    double logZ, dlogZ;    /* when done */
+    long long iterations, evals;
+    double t_submit, t_admit, t_done;   /* seconds on the server's clock */
+    size_t footprint;      /* estimated device bytes while running */
+    int n_samples;         /* weighted samples kept (dead + final live) */
+} ns_request_status;
+
+int ns_server_create(ns_server **out, const ns_server_options *opts);
+/* Copies the request's host inputs; *id identifies it. Validation errors are
+ * returned here (INVALID_ARG, PSD_NONPOS, K_RANGE). */
+int ns_submit(ns_server *srv, const ns_request *req, uint64_t *id);
+/* Admit, iterate every running analysis once, retire finished ones.
+ * n_running / n_pending (may be NULL) report the queue after the tick. */
+int ns_server_tick(ns_server *srv, int *n_running, int *n_pending);
+int ns_poll(ns_server *srv, uint64_t id, ns_request_status *st);
+/* Weighted samples of a finished request (as ns_result; CAPACITY if too small). */
+int ns_server_result(ns_server *srv, uint64_t id, ns_samples *samples);
+/* Cancel a pending or running request (its device memory is released). */
+int ns_cancel(ns_server *srv, uint64_t id);
+/* Seconds on the server's clock (steady clock, zero at creation). */
+double ns_server_time(ns_server *srv);
+void ns_server_free(ns_server *srv);
 
 #ifdef __cplusplus
 }

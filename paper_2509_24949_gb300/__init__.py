@@ -76,6 +76,25 @@ class _Stats(ctypes.Structure):
                 ("status", ctypes.c_int), ("kernel_ms", ctypes.c_double * 5)]
 
 
+class _ServerOptions(ctypes.Structure):
+    _fields_ = [("max_active", ctypes.c_int), ("mem_budget", ctypes.c_size_t), ("precision", ctypes.c_int),
+                ("slots", ctypes.c_int), ("max_iter", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class _Request(ctypes.Structure):
+    _fields_ = [("prior", _Prior), ("data", _Data), ("psd", _Psd), ("grid", _Grid), ("opts", _Options)]
+
+
+class _ReqStatus(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int), ("logZ", ctypes.c_double), ("dlogZ", ctypes.c_double),
+                ("iterations", ctypes.c_longlong), ("evals", ctypes.c_longlong),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("footprint", ctypes.c_size_t), ("n_samples", ctypes.c_int)]
+
+
+NS_REQ_PENDING, NS_REQ_RUNNING, NS_REQ_DONE, NS_REQ_CANCELLED = 0, 1, 2, 3
+
+
 def library_path() -> str:
     return _build.LIB
 
@@ -108,11 +127,24 @@ def lib():
         L.ns_get_live.argtypes = [vp, vp, vp]
         L.ns_set_live.argtypes = [vp, vp, vp]
         L.ns_sync.argtypes = [vp]
+        L.ns_autotune.argtypes = [vp, ip, P(ip)]
         L.ns_free.argtypes = [vp]; L.ns_free.restype = None
+        L.ns_server_create.argtypes = [P(vp), P(_ServerOptions)]
+        L.ns_submit.argtypes = [vp, P(_Request), P(ctypes.c_uint64)]
+        L.ns_server_tick.argtypes = [vp, P(ip), P(ip)]
+        L.ns_poll.argtypes = [vp, ctypes.c_uint64, P(_ReqStatus)]
+        L.ns_server_result.argtypes = [vp, ctypes.c_uint64, P(_Samples)]
+        L.ns_cancel.argtypes = [vp, ctypes.c_uint64]
+        L.ns_server_time.argtypes = [vp]; L.ns_server_time.restype = ctypes.c_double
+        L.ns_server_free.argtypes = [vp]; L.ns_server_free.restype = None
+        for name in ("ns_server_create", "ns_submit", "ns_server_tick", "ns_poll", "ns_server_result",
+                     "ns_cancel"):
+            getattr(L, name).restype = ctypes.c_int
         for name in ("ns_init", "ns_set_data", "ns_step", "ns_step_host", "ns_run", "ns_result",
                      "ns_get_stats", "ns_eval_lnl", "ns_eval_lnl_host", "ns_eval_lnl_theta",
                      "ns_eval_lnl_host_noalloc",
-                     "ns_waveform", "ns_prior_transform", "ns_optimal_snr2", "ns_get_live", "ns_set_live", "ns_sync"):
+                     "ns_waveform", "ns_prior_transform", "ns_optimal_snr2", "ns_get_live", "ns_set_live", "ns_sync",
+                     "ns_autotune"):
             getattr(L, name).restype = ctypes.c_int
         _LIB = L
     return _LIB
@@ -324,6 +356,111 @@ class Sampler:
 
     def sync(self):
         _check(lib().ns_sync(self._ctx), "ns_sync")
+
+    def autotune(self, trials: int = 2) -> int:
+        """Pick the fastest slice-update slot count on this workload (results unchanged)."""
+        s = ctypes.c_int()
+        _check(lib().ns_autotune(self._ctx, trials, ctypes.byref(s)), "ns_autotune")
+        return s.value
+
+
+def _fill_inputs(kind, lo, hi, data, psd, f0, df, pos, xarm, yarm, ideal, coarse_bins, theta_fid, keep):
+    pr, dt, ps, gr = _Prior(), _Data(), _Psd(), _Grid()
+    kind = np.asarray(kind, dtype=np.int32)
+    for p in range(NPARAM):
+        pr.kind[p], pr.lo[p], pr.hi[p] = int(kind[p]), float(lo[p]), float(hi[p])
+    psd = _f64(psd)
+    n_det, N = psd.shape
+    keep.append(psd)
+    ps.S = _ptr(psd)
+    dt.n_det, dt.ideal = n_det, int(bool(ideal))
+    if data is not None:
+        data = np.asarray(data, dtype=np.complex128).reshape(n_det, N)
+        re, im = _f64(data.real), _f64(data.imag)
+        keep += [re, im]
+        dt.re, dt.im = _ptr(re), _ptr(im)
+    if not ideal:
+        arrs = [_f64(pos).reshape(n_det, 3), _f64(xarm).reshape(n_det, 3), _f64(yarm).reshape(n_det, 3)]
+        keep += arrs
+        dt.pos, dt.xarm, dt.yarm = (_ptr(a) for a in arrs)
+    gr.N, gr.f0, gr.df = N, float(f0), float(df)
+    if coarse_bins:
+        tf = _f64(theta_fid)
+        keep.append(tf)
+        gr.coarse_bins, gr.theta_fid = int(coarse_bins), _ptr(tf)
+    return pr, dt, ps, gr
+
+
+class Server:
+    """Continuous-batching server of many analyses (ns_server_* in gwns.h)."""
+
+    def __init__(self, *, max_active=16, mem_budget=0, precision=NS_MIXED, slots=0, max_iter=0, stream=None):
+        o = _ServerOptions(max_active, mem_budget, precision, slots, max_iter,
+                           None if stream is None else int(stream))
+        h = ctypes.c_void_p()
+        _check(lib().ns_server_create(ctypes.byref(h), ctypes.byref(o)), "ns_server_create")
+        self._h = h
+
+    def submit(self, *, kind, lo, hi, data, psd, f0, df, pos=None, xarm=None, yarm=None, ideal=False,
+               n_live=100, k=0, steps_per_dim=5, no_cutoff=False, dlogz_stop=0.1, seed=0,
+               coarse_bins=0, theta_fid=None) -> int:
+        keep = []
+        pr, dt, ps, gr = _fill_inputs(kind, lo, hi, data, psd, f0, df, pos, xarm, yarm, ideal,
+                                      coarse_bins, theta_fid, keep)
+        opt = _Options(n_live, k, steps_per_dim, 0, int(bool(no_cutoff)), 0, 0, NS_MODEL_GW, 0, 0, 0,
+                       dlogz_stop, seed, None)
+        req = _Request(pr, dt, ps, gr, opt)
+        rid = ctypes.c_uint64()
+        _check(lib().ns_submit(self._h, ctypes.byref(req), ctypes.byref(rid)), "ns_submit")
+        return rid.value
+
+    def tick(self):
+        r, p = ctypes.c_int(), ctypes.c_int()
+        _check(lib().ns_server_tick(self._h, ctypes.byref(r), ctypes.byref(p)), "ns_server_tick")
+        return r.value, p.value
+
+    def poll(self, rid: int) -> dict:
+        st = _ReqStatus()
+        _check(lib().ns_poll(self._h, rid, ctypes.byref(st)), "ns_poll")
+        return {name: getattr(st, name) for name, _ in _ReqStatus._fields_}
+
+    def result(self, rid: int, dim: int) -> dict:
+        st = self.poll(rid)
+        n = st["n_samples"]
+        u, logl, logw, theta = np.zeros((n, dim)), np.zeros(n), np.zeros(n), np.zeros((n, NPARAM))
+        sm = _Samples(n, 0, _ptr(theta), _ptr(u), _ptr(logl), _ptr(logw))
+        _check(lib().ns_server_result(self._h, rid, ctypes.byref(sm)), "ns_server_result")
+        return dict(u=u, logl=logl, logw=logw, theta=theta, logZ=st["logZ"], dlogZ=st["dlogZ"])
+
+    def cancel(self, rid: int):
+        _check(lib().ns_cancel(self._h, rid), "ns_cancel")
+
+    def time(self) -> float:
+        return lib().ns_server_time(self._h)
+
+    def run_until_idle(self, max_ticks: int = 1000000):
+        for _ in range(max_ticks):
+            r, p = self.tick()
+            if r == 0 and p == 0:
+                return
+        raise RuntimeError("server did not drain")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ns_server_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def sampler_for_workload(w, data=None, precision=NS_FP64, **kw) -> Sampler:

@@ -8,68 +8,29 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 #include <vector>
 
-#include "../../include/gwns.h"
-#include "gwns_kernels.cuh"
+#include "gwns_ctx.h"
 
 using namespace gwns;
+using namespace gwns_host;
 
-struct ns_ctx {
-    Model M;
-    Tables T;
-    int n = 0, d = 0, k_default = 0, steps = 0, precision = 0, max_so = 64, max_sh = 64, warps = 0;
-    int slots = 0;
-    double dlogz = 0.1;
-    uint64_t seed = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    int device = 0;
-    // device buffers
-    double *d_re = nullptr, *d_im = nullptr, *d_psd = nullptr;
-    double *basis64 = nullptr, *f64 = nullptr, *prefix = nullptr;
-    double2 *w64 = nullptr;
-    float2 *basis32 = nullptr, *f32 = nullptr, *w32 = nullptr;
-    double *live_u = nullptr, *live_logl = nullptr;
-    int *order = nullptr;
-    double *chol = nullptr;
-    double *dead_u = nullptr, *dead_logl = nullptr, *dead_logw = nullptr, *dead_nlive = nullptr;
-    long long dead_cap = 0;
-    RunState *state = nullptr;
-    RunState *h_state = nullptr;     // pinned
-    double *scratch = nullptr;       // eval / waveform scratch
-    size_t scratch_bytes = 0;
-    // relative-binning tables
-    int rb_B = 0;
-    double rb_theta[NS_NPARAM];
-    int *rb_J = nullptr, *rb_nedge = nullptr;
-    Coef *rb_fid = nullptr;
-    double *rb_fe = nullptr, *rb_basis64 = nullptr, *rb_fm = nullptr, *rb_inv_de = nullptr;
-    double *rb_B0 = nullptr, *rb_B1 = nullptr;
-    double2 *rb_A0 = nullptr, *rb_A1 = nullptr;
-    float2 *rb_basis32 = nullptr, *rb_fe32 = nullptr, *rb_A0f = nullptr, *rb_A1f = nullptr;
-    float *rb_B0f = nullptr, *rb_B1f = nullptr, *rb_inv_de_f = nullptr;
-    // result buffers
-    double *fin_u = nullptr, *fin_logl = nullptr, *fin_logw = nullptr, *fin_nlive = nullptr;
-    double *res = nullptr;           // [R + 8]
-    // graph of one iteration, with timing events between its kernels
-    cudaGraphExec_t graph = nullptr;
-    int graph_k = -1;
-    cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-    bool timing = false;
-    double kernel_ms[5] = {0, 0, 0, 0, 0};
-    long long n_dead = 0;
-};
+
+namespace gwns_host {
+int cuda_fail(cudaError_t e) {
+    if (e == cudaErrorMemoryAllocation) return NS_ERR_OOM;
+    return NS_ERR_CUDA;
+}
+}  // namespace gwns_host
 
 namespace {
 
 constexpr int kReplicates = 200;
 
-int cuda_fail(cudaError_t e) {
-    if (e == cudaErrorMemoryAllocation) return NS_ERR_OOM;
-    return NS_ERR_CUDA;
-}
 
 #define CK(call)                                   \
     do {                                           \
@@ -105,60 +66,8 @@ int choose_warps(const ns_ctx *c) {
 // Speculative candidate slots per chain in the slice update: several slots
 // shorten a chain's critical path when the GPU is not saturated by the k
 // chains' work (small grids), one slot avoids speculative work when it is.
-int choose_slots(const ns_ctx *c) {
-    if (c->slots > 0) return c->slots;
-    if (c->M.model == M_TOY) return 1;
-    const int bins = c->M.rb ? c->T.rb.nb : c->M.N;
-    // measured on GB300 (512 / 4017 / 64,897-bin workloads): FP64 binds on its
-    // pipe beyond small grids, the mixed form on latency up to large grids
-    if (c->precision == NS_FP64) return bins <= 1024 ? 4 : (bins <= 131072 ? 2 : 1);
-    return bins <= 1024 ? 8 : (bins <= 131072 ? 4 : 2);
-}
 
-StepArgs step_args(ns_ctx *c, int k) {
-    StepArgs A;
-    A.live_u = c->live_u;
-    A.live_logl = c->live_logl;
-    A.order = c->order;
-    A.chol = c->chol;
-    A.dead_u = c->dead_u;
-    A.dead_logl = c->dead_logl;
-    A.dead_logw = c->dead_logw;
-    A.dead_nlive = c->dead_nlive;
-    A.state = c->state;
-    A.seed = c->seed;
-    A.n = c->n;
-    A.k = k;
-    A.steps = c->steps;
-    A.max_stepout = c->max_so;
-    A.max_shrink = c->max_sh;
-    A.dlogz_stop = c->dlogz;
-    return A;
-}
 
-int ensure_dead_capacity(ns_ctx *c, long long need) {
-    if (need <= c->dead_cap) return NS_OK;
-    long long cap = std::max<long long>(need, std::max<long long>(2 * c->dead_cap, 64LL * c->n));
-    double *u = nullptr, *l = nullptr, *w = nullptr, *nl = nullptr;
-    int rc;
-    if ((rc = dalloc(&u, (size_t)cap * c->d)) || (rc = dalloc(&l, cap)) || (rc = dalloc(&w, cap)) ||
-        (rc = dalloc(&nl, cap))) {
-        dfree(u); dfree(l); dfree(w); dfree(nl);
-        return rc;
-    }
-    if (c->n_dead > 0) {
-        CK(cudaMemcpyAsync(u, c->dead_u, sizeof(double) * c->n_dead * c->d, cudaMemcpyDeviceToDevice, c->stream));
-        CK(cudaMemcpyAsync(l, c->dead_logl, sizeof(double) * c->n_dead, cudaMemcpyDeviceToDevice, c->stream));
-        CK(cudaMemcpyAsync(w, c->dead_logw, sizeof(double) * c->n_dead, cudaMemcpyDeviceToDevice, c->stream));
-        CK(cudaMemcpyAsync(nl, c->dead_nlive, sizeof(double) * c->n_dead, cudaMemcpyDeviceToDevice, c->stream));
-    }
-    CK(cudaStreamSynchronize(c->stream));
-    dfree(c->dead_u); dfree(c->dead_logl); dfree(c->dead_logw); dfree(c->dead_nlive);
-    c->dead_u = u; c->dead_logl = l; c->dead_logw = w; c->dead_nlive = nl;
-    c->dead_cap = cap;
-    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; c->graph_k = -1; }
-    return NS_OK;
-}
 
 int ensure_scratch(ns_ctx *c, size_t bytes) {
     if (bytes <= c->scratch_bytes) return NS_OK;
@@ -268,6 +177,77 @@ int eval_points(ns_ctx *c, const double *in, int is_theta, int m, double *logl) 
 }
 
 }  // namespace
+
+namespace gwns_host {
+// slot counts chosen by ns_autotune, keyed by (bins, detectors, precision, n, k)
+using TuneKey = std::tuple<int, int, int, int, int>;
+static std::mutex g_tune_mu;
+static std::map<TuneKey, int> g_tuned;
+
+TuneKey tune_key(const ns_ctx *c) {
+    return TuneKey(c->M.rb ? -c->T.rb.nb : c->M.N, c->M.n_det, c->precision, c->n, c->k_default);
+}
+
+int choose_slots(const ns_ctx *c) {
+    if (c->slots > 0) return c->slots;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tuned.find(tune_key(c));
+        if (it != g_tuned.end()) return it->second;
+    }
+    if (c->M.model == M_TOY) return 1;
+    const int bins = c->M.rb ? c->T.rb.nb : c->M.N;
+    // measured on GB300 (512 / 4017 / 64,897-bin workloads): FP64 binds on its
+    // pipe beyond small grids, the mixed form on latency up to large grids
+    if (c->precision == NS_FP64) return bins <= 1024 ? 4 : (bins <= 131072 ? 2 : 1);
+    return bins <= 1024 ? 8 : (bins <= 131072 ? 4 : 2);
+}
+
+StepArgs step_args(ns_ctx *c, int k) {
+    StepArgs A;
+    A.live_u = c->live_u;
+    A.live_logl = c->live_logl;
+    A.order = c->order;
+    A.chol = c->chol;
+    A.dead_u = c->dead_u;
+    A.dead_logl = c->dead_logl;
+    A.dead_logw = c->dead_logw;
+    A.dead_nlive = c->dead_nlive;
+    A.state = c->state;
+    A.seed = c->seed;
+    A.n = c->n;
+    A.k = k;
+    A.steps = c->steps;
+    A.max_stepout = c->max_so;
+    A.max_shrink = c->max_sh;
+    A.dlogz_stop = c->dlogz;
+    return A;
+}
+
+int ensure_dead_capacity(ns_ctx *c, long long need) {
+    if (need <= c->dead_cap) return NS_OK;
+    long long cap = std::max<long long>(need, std::max<long long>(2 * c->dead_cap, 64LL * c->n));
+    double *u = nullptr, *l = nullptr, *w = nullptr, *nl = nullptr;
+    int rc;
+    if ((rc = dalloc(&u, (size_t)cap * c->d)) || (rc = dalloc(&l, cap)) || (rc = dalloc(&w, cap)) ||
+        (rc = dalloc(&nl, cap))) {
+        dfree(u); dfree(l); dfree(w); dfree(nl);
+        return rc;
+    }
+    if (c->n_dead > 0) {
+        CK(cudaMemcpyAsync(u, c->dead_u, sizeof(double) * c->n_dead * c->d, cudaMemcpyDeviceToDevice, c->stream));
+        CK(cudaMemcpyAsync(l, c->dead_logl, sizeof(double) * c->n_dead, cudaMemcpyDeviceToDevice, c->stream));
+        CK(cudaMemcpyAsync(w, c->dead_logw, sizeof(double) * c->n_dead, cudaMemcpyDeviceToDevice, c->stream));
+        CK(cudaMemcpyAsync(nl, c->dead_nlive, sizeof(double) * c->n_dead, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    dfree(c->dead_u); dfree(c->dead_logl); dfree(c->dead_logw); dfree(c->dead_nlive);
+    c->dead_u = u; c->dead_logl = l; c->dead_logw = w; c->dead_nlive = nl;
+    c->dead_cap = cap;
+    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; c->graph_k = -1; }
+    return NS_OK;
+}
+}  // namespace gwns_host
 
 extern "C" {
 
@@ -719,6 +699,62 @@ int ns_set_live(ns_ctx *c, const double *u, const double *logl) {
     CK(cudaMemcpyAsync(c->live_u, u, sizeof(double) * c->n * c->d, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->live_logl, logl, sizeof(double) * c->n, cudaMemcpyHostToDevice, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    return NS_OK;
+}
+
+int ns_autotune(ns_ctx *c, int trials, int *slots) {
+    if (!c || trials < 1) return NS_ERR_INVALID_ARG;
+    const int k = c->k_default;
+    int rc = ensure_dead_capacity(c, c->n_dead + (long long)trials * k);
+    if (rc) return rc;
+    // snapshot: live set and run state (the dead list is only appended)
+    const size_t nu = (size_t)c->n * c->d;
+    double *su = nullptr, *sl = nullptr;
+    RunState *ss = nullptr;
+    if ((rc = dalloc(&su, nu)) || (rc = dalloc(&sl, c->n)) || (rc = dalloc(&ss, 1))) {
+        dfree(su); dfree(sl); dfree(ss);
+        return rc;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    const int saved_slots = c->slots;
+    const bool saved_timing = c->timing;
+    const int cand[4] = {1, 2, 4, 8};
+    float best_ms = 3.4e38f;
+    int best = choose_slots(c);
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(su, c->live_u, sizeof(double) * nu, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sl, c->live_logl, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ss, c->state, sizeof(RunState), cudaMemcpyDeviceToDevice, c->stream);
+    c->timing = false;
+    for (int i = 0; i < 4 && e == cudaSuccess && rc == NS_OK; i++) {
+        c->slots = cand[i];
+        e = cudaEventRecord(e0, c->stream);
+        for (int t = 0; t < trials && e == cudaSuccess && rc == NS_OK; t++) rc = enqueue_iteration(c, k);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess && rc == NS_OK) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && rc == NS_OK && ms < best_ms) { best_ms = ms; best = cand[i]; }
+        // restore the snapshot
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c->live_u, su, sizeof(double) * nu, cudaMemcpyDeviceToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c->live_logl, sl, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c->state, ss, sizeof(RunState), cudaMemcpyDeviceToDevice, c->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    c->timing = saved_timing;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    dfree(su); dfree(sl); dfree(ss);
+    if (rc) { c->slots = saved_slots; return rc; }
+    if (e != cudaSuccess) { c->slots = saved_slots; return cuda_fail(e); }
+    c->slots = best;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tuned[tune_key(c)] = best;
+    }
+    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; c->graph_k = -1; }
+    if (slots) *slots = best;
     return NS_OK;
 }
 

@@ -300,7 +300,7 @@ __device__ __forceinline__ unsigned long long sortable_key(double x) {
     return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
 }
 
-__global__ void __launch_bounds__(1024) k_select(const double *logl, int n, int *order) {
+__device__ void select_body(const double *logl, int n, int *order) {
     __shared__ unsigned long long key[SELECT_MAX];
     __shared__ int idx[SELECT_MAX];
     int P = 1;
@@ -328,6 +328,10 @@ __global__ void __launch_bounds__(1024) k_select(const double *logl, int n, int 
     for (int i = threadIdx.x; i < n; i += blockDim.x) order[i] = idx[i];
 }
 
+__global__ void __launch_bounds__(1024) k_select(const double *logl, int n, int *order) {
+    select_body(logl, n, order);
+}
+
 cudaError_t launch_select(const double *logl, int n, int *order, cudaStream_t s) {
     if (n > SELECT_MAX) return cudaErrorInvalidValue;
     k_select<<<1, 1024, 0, s>>>(logl, n, order);
@@ -339,7 +343,7 @@ cudaError_t launch_select(const double *logl, int n, int *order, cudaStream_t s)
 // log w_j = log X_{j-1} + log(1 - exp(-Delta_j)), log X_j = log X_{j-1} - Delta_j,
 // log Z <- logaddexp(log Z, logsumexp_j(log L_j + log w_j)). The prefix sums of
 // Delta_j use a block scan; the dead records are appended at state->n_dead.
-__global__ void __launch_bounds__(1024) k_evidence(Model M, StepArgs A) {
+__device__ void evidence_body(const Model &M, const StepArgs &A) {
     __shared__ double scan[1024];
     __shared__ double scratch[32];
     RunState *st = A.state;
@@ -395,6 +399,8 @@ __global__ void __launch_bounds__(1024) k_evidence(Model M, StepArgs A) {
     }
 }
 
+__global__ void __launch_bounds__(1024) k_evidence(Model M, StepArgs A) { evidence_body(M, A); }
+
 cudaError_t launch_evidence(const Model &M, const StepArgs &A, cudaStream_t s) {
     k_evidence<<<1, 1024, 0, s>>>(M, A);
     return cudaGetLastError();
@@ -404,7 +410,7 @@ cudaError_t launch_evidence(const Model &M, const StepArgs &A, cudaStream_t s) {
 // Unbiased covariance (1/(m-1)) of the m = n-k survivors (sorted positions
 // k..n-1) in unit-cube coordinates, jittered by 1e-12 tr/d, Cholesky factor
 // by warp 0 (lane i owns row i); diag(sqrt(Sigma_ii)) if it fails.
-__global__ void __launch_bounds__(256) k_cov_chol(Model M, StepArgs A) {
+__device__ void cov_chol_body(const Model &M, const StepArgs &A) {
     __shared__ double mean[MAXD];
     __shared__ double cov[MAXD * MAXD];
     __shared__ double scratch[32];
@@ -460,6 +466,8 @@ __global__ void __launch_bounds__(256) k_cov_chol(Model M, StepArgs A) {
         }
     }
 }
+
+__global__ void __launch_bounds__(256) k_cov_chol(Model M, StepArgs A) { cov_chol_body(M, A); }
 
 cudaError_t launch_cov_chol(const Model &M, const StepArgs &A, cudaStream_t s) {
     k_cov_chol<<<1, 256, 0, s>>>(M, A);
@@ -677,13 +685,12 @@ __device__ int chain_plan(const Model &M, const StepArgs &A, const Chain &c, int
 }
 
 template <int PREC, int NDET, int S>
-__global__ void __launch_bounds__(S * 32) k_slice(Model M, Tables T, StepArgs A) {
+__device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, const int chain) {
     __shared__ Coef coef[S];
     __shared__ CoefMixed cm[S];
     __shared__ double ysh[S][MAXD];
     __shared__ double lval[S];
     __shared__ int nslot;
-    const int chain = blockIdx.x;
     if (chain >= A.k) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, d = M.dim;
     const uint32_t iter = (uint32_t)A.state->iter;
@@ -778,6 +785,11 @@ __global__ void __launch_bounds__(S * 32) k_slice(Model M, Tables T, StepArgs A)
     }
 }
 
+template <int PREC, int NDET, int S>
+__global__ void __launch_bounds__(S * 32) k_slice(Model M, Tables T, StepArgs A) {
+    slice_body<PREC, NDET, S>(M, T, A, blockIdx.x);
+}
+
 template <int PREC, int NDET>
 static cudaError_t slice_w(const Model &M, const Tables &T, int slots, const StepArgs &A, cudaStream_t s) {
     switch (slots) {
@@ -805,7 +817,7 @@ cudaError_t launch_slice(const Model &M, const Tables &T, int precision, int slo
 }
 
 // ------------------------------------------------------------------ finish
-__global__ void __launch_bounds__(1024) k_finish(StepArgs A) {
+__device__ void finish_body(const StepArgs &A) {
     __shared__ double scratch[32];
     double m = -DBL_MAX;
     for (int i = threadIdx.x; i < A.n; i += blockDim.x) m = fmax(m, A.live_logl[i]);
@@ -821,6 +833,8 @@ __global__ void __launch_bounds__(1024) k_finish(StepArgs A) {
         st->iter += 1;
     }
 }
+
+__global__ void __launch_bounds__(1024) k_finish(StepArgs A) { finish_body(A); }
 
 cudaError_t launch_finish(const StepArgs &A, cudaStream_t s) {
     k_finish<<<1, 1024, 0, s>>>(A);
@@ -1148,6 +1162,88 @@ cudaError_t launch_waveform(const Model &M, const Tables &T, const double *theta
                             double *h_re, double *h_im, cudaStream_t s) {
     k_waveform_coef<<<1, 32, 0, s>>>(M, T, theta, scratch);
     k_waveform_bins<<<min((M.N + 255) / 256, 1216), 256, 0, s>>>(M, T, scratch, h_re, h_im);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------ multi-analysis iteration
+// The serving loop runs one iteration of every admitted analysis with one
+// launch per kernel: block a of the per-analysis kernels works on analysis a,
+// and block b of the slice update on chain map[b].y of analysis map[b].x.
+// Each block first copies its analysis' descriptor to shared memory.
+__device__ __forceinline__ void load_desc(const Desc *g, Desc &s) {
+    const int *src = (const int *)g;
+    int *dst = (int *)&s;
+    for (int i = threadIdx.x; i < (int)(sizeof(Desc) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(1024) k_select_multi(const Desc *D) {
+    // the sort's 48 KB of shared memory leaves no room for a descriptor copy
+    const StepArgs &A = D[blockIdx.x].A;
+    select_body(A.live_logl, A.n, A.order);
+}
+__global__ void __launch_bounds__(1024) k_evidence_multi(const Desc *D) {
+    __shared__ Desc d;
+    load_desc(D + blockIdx.x, d);
+    evidence_body(d.M, d.A);
+}
+__global__ void __launch_bounds__(256) k_cov_chol_multi(const Desc *D) {
+    __shared__ Desc d;
+    load_desc(D + blockIdx.x, d);
+    cov_chol_body(d.M, d.A);
+}
+__global__ void __launch_bounds__(1024) k_finish_multi(const Desc *D) {
+    __shared__ Desc d;
+    load_desc(D + blockIdx.x, d);
+    finish_body(d.A);
+}
+template <int PREC, int NDET, int S>
+__global__ void __launch_bounds__(S * 32) k_slice_multi(const Desc *D, const int2 *map) {
+    __shared__ Desc d;
+    const int2 ac = map[blockIdx.x];
+    load_desc(D + ac.x, d);
+    slice_body<PREC, NDET, S>(d.M, d.T, d.A, ac.y);
+}
+
+template <int PREC, int NDET>
+static cudaError_t slice_multi_w(const Desc *D, const int2 *map, int nblocks, int slots, cudaStream_t s) {
+    switch (slots) {
+        case 1: k_slice_multi<PREC, NDET, 1><<<nblocks, 32, 0, s>>>(D, map); break;
+        case 2: k_slice_multi<PREC, NDET, 2><<<nblocks, 64, 0, s>>>(D, map); break;
+        case 4: k_slice_multi<PREC, NDET, 4><<<nblocks, 128, 0, s>>>(D, map); break;
+        default: k_slice_multi<PREC, NDET, 8><<<nblocks, 256, 0, s>>>(D, map); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_iteration_multi_head(const Desc *D, int n_an, cudaStream_t s) {
+    k_select_multi<<<n_an, 1024, 0, s>>>(D);
+    k_evidence_multi<<<n_an, 1024, 0, s>>>(D);
+    k_cov_chol_multi<<<n_an, 256, 0, s>>>(D);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_slice_multi(const Desc *D, const int2 *map, int nblocks, int precision, int ndet, int slots,
+                               cudaStream_t s) {
+    if (nblocks <= 0) return cudaSuccess;
+    if (precision == 1) {
+        switch (ndet) {
+            case 1: return slice_multi_w<1, 1>(D, map, nblocks, slots, s);
+            case 2: return slice_multi_w<1, 2>(D, map, nblocks, slots, s);
+            case 3: return slice_multi_w<1, 3>(D, map, nblocks, slots, s);
+            default: return slice_multi_w<1, 4>(D, map, nblocks, slots, s);
+        }
+    }
+    switch (ndet) {
+        case 1: return slice_multi_w<0, 1>(D, map, nblocks, slots, s);
+        case 2: return slice_multi_w<0, 2>(D, map, nblocks, slots, s);
+        case 3: return slice_multi_w<0, 3>(D, map, nblocks, slots, s);
+        default: return slice_multi_w<0, 4>(D, map, nblocks, slots, s);
+    }
+}
+
+cudaError_t launch_iteration_multi_tail(const Desc *D, int n_an, cudaStream_t s) {
+    k_finish_multi<<<n_an, 1024, 0, s>>>(D);
     return cudaGetLastError();
 }
 

@@ -40,6 +40,13 @@ struct StepArgs {
     double dlogz_stop;
 };
 
+// One analysis' iteration arguments, for the multi-analysis launches.
+struct Desc {
+    Model M;
+    Tables T;
+    StepArgs A;
+};
+
 struct ResultArgs {
     const double *dead_logl, *dead_logw, *dead_nlive;
     const double *fin_logl, *fin_logw, *fin_nlive;   // [n] final live points, ascending
@@ -77,6 +84,10 @@ cudaError_t launch_finish(const StepArgs &A, cudaStream_t s);
 cudaError_t launch_final_live(const Model &M, const StepArgs &A, double *fin_u, double *fin_logl,
                               double *fin_logw, double *fin_nlive, double *logz_total, cudaStream_t s);
 cudaError_t launch_result_stats(const ResultArgs &R, cudaStream_t s);
+cudaError_t launch_iteration_multi_head(const Desc *D, int n_an, cudaStream_t s);
+cudaError_t launch_slice_multi(const Desc *D, const int2 *map, int nblocks, int precision, int ndet, int slots,
+                               cudaStream_t s);
+cudaError_t launch_iteration_multi_tail(const Desc *D, int n_an, cudaStream_t s);
 cudaError_t launch_theta(const Model &M, const double *u, long long m, double *theta, cudaStream_t s);
 cudaError_t launch_rb_setup(const Model &M, const Tables &T, int B, const double *theta_fid, int *J,
                             int *nedge_dev, Coef *fid, double2 *h0_tmp, const double *dre, const double *dim,

@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def declared_functions():
     src = open(os.path.join(ROOT, "include", "gwns.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = re.findall(r"^\s*(?:int|void|const char \*)\s*\*?\s*(ns_\w+)\s*\(", src, flags=re.M)
+    names = re.findall(r"^\s*(?:int|void|double|const char \*)\s*\*?\s*(ns_\w+)\s*\(", src, flags=re.M)
     return sorted(set(names))
 
 

@@ -328,3 +328,19 @@ def test_relative_binning_iterations_match_oracle(gw):
             gu, gl = sp.live()
             assert np.max(np.abs(gu - st.live_u)) < 1e-9
             assert np.max(np.abs(gl - st.live_logl) / np.maximum(1, np.abs(st.live_logl))) < 1e-8
+
+
+def test_autotune_keeps_the_trajectory(gw):
+    """Autotuning times each slot count from a saved state and restores it:
+    the run continues exactly as the oracle's."""
+    w, pb, sp, st = _ns_pair(gw, "c1", 120, 60)
+    chosen = sp.autotune(trials=1)
+    assert chosen in (1, 2, 4, 8)
+    for it in range(2):
+        ons.iterate(pb, st, 60, w.steps_per_dim * pb.dim, w.seed_sampler)
+        sp.step(60)
+    gu, gl = sp.live()
+    assert np.max(np.abs(gu - st.live_u)) < 1e-9
+    s = sp.stats()
+    assert s["iterations"] == 2 and s["evals"] == st.evals
+    sp.close()

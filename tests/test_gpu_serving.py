@@ -1,0 +1,109 @@
+"""Serving: many analyses interleaved on one GPU give each the same result as
+alone; admission respects the slot count and the memory budget; requests can
+be cancelled. All on the GPU through the C ABI."""
+import numpy as np
+import pytest
+
+import gwinputs as gi
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def _analysis(seed_offset, N=1200, n_live=80, n_det=3):
+    w = gi.workload("c1", n_live=n_live, k=n_live // 2)
+    w.N = N
+    w.n_det = n_det
+    w.seed_noise += seed_offset
+    w.seed_injection += seed_offset
+    w.seed_sampler += seed_offset
+    pb, th = oracle.make_problem(w)
+    return dict(kind=pb.kind, lo=pb.lo, hi=pb.hi, data=pb.data(), psd=pb.psd, f0=pb.f0, df=pb.df,
+                pos=pb.pos, xarm=pb.xarm, yarm=pb.yarm, n_live=w.n_live, k=w.k,
+                steps_per_dim=w.steps_per_dim, seed=w.seed_sampler), pb.dim
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_alone_equals_in_the_mix(gw, precision):
+    reqs = [_analysis(i, N=900 + 300 * i, n_live=60 + 20 * i, n_det=2 + (i % 2)) for i in range(3)]
+    with gw.Server(precision=precision, slots=2) as srv:
+        rid = srv.submit(**reqs[0][0])
+        srv.run_until_idle()
+        alone = srv.result(rid, reqs[0][1])
+        st_alone = srv.poll(rid)
+    with gw.Server(precision=precision, slots=2) as srv:
+        ids = [srv.submit(**r) for r, _ in reqs]
+        max_run = 0
+        while True:
+            r, p = srv.tick()
+            max_run = max(max_run, r)
+            if r == 0 and p == 0:
+                break
+        assert max_run >= 2          # they did share the GPU
+        mixed = srv.result(ids[0], reqs[0][1])
+        for i in ids:
+            assert srv.poll(i)["state"] == gw.NS_REQ_DONE
+    assert st_alone["state"] == gw.NS_REQ_DONE
+    assert mixed["logZ"] == alone["logZ"] and mixed["dlogZ"] == alone["dlogZ"]
+    assert np.array_equal(mixed["u"], alone["u"]) and np.array_equal(mixed["logl"], alone["logl"])
+
+
+def test_server_equals_single_context(gw):
+    args, dim = _analysis(7)
+    with gw.Server(precision=0, slots=2) as srv:
+        rid = srv.submit(**args)
+        srv.run_until_idle()
+        a = srv.result(rid, dim)
+    with gw.Sampler(precision=0, slots=2, **args) as sp:
+        sp.run()
+        b = sp.result()
+    assert a["logZ"] == b["logZ"]
+    assert np.array_equal(a["logl"], b["logl"])
+
+
+def test_admission_by_slots_and_memory(gw):
+    reqs = [_analysis(10 + i) for i in range(4)]
+    with gw.Server(precision=1, max_active=2) as srv:
+        ids = [srv.submit(**r) for r, _ in reqs]
+        while True:
+            r, p = srv.tick()
+            assert r <= 2
+            if r == 0 and p == 0:
+                break
+        assert all(srv.poll(i)["state"] == gw.NS_REQ_DONE for i in ids)
+    # a budget that holds one analysis at a time
+    fp = None
+    with gw.Server(precision=1) as srv:
+        fp = srv.poll(srv.submit(**reqs[0][0]))["footprint"]
+    with gw.Server(precision=1, mem_budget=int(fp * 1.5)) as srv:
+        ids = [srv.submit(**r) for r, _ in reqs[:3]]
+        while True:
+            r, p = srv.tick()
+            assert r <= 1
+            if r == 0 and p == 0:
+                break
+        sts = [srv.poll(i) for i in ids]
+        assert all(s["state"] == gw.NS_REQ_DONE for s in sts)
+        # served one after another, in arrival order
+        assert sts[0]["t_done"] <= sts[1]["t_admit"] <= sts[1]["t_done"] <= sts[2]["t_admit"]
+    # a request that can never fit is rejected, the rest still run
+    with gw.Server(precision=1, mem_budget=int(fp * 0.5)) as srv:
+        rid = srv.submit(**reqs[0][0])
+        srv.tick()
+        assert srv.poll(rid)["state"] == -4     # NS_ERR_OOM
+
+
+def test_cancel(gw):
+    reqs = [_analysis(20 + i) for i in range(3)]
+    with gw.Server(precision=1, max_active=1) as srv:
+        ids = [srv.submit(**r) for r, _ in reqs]
+        srv.tick()
+        assert srv.poll(ids[0])["state"] == gw.NS_REQ_RUNNING
+        srv.cancel(ids[0])            # running
+        srv.cancel(ids[1])            # pending
+        assert srv.poll(ids[0])["state"] == gw.NS_REQ_CANCELLED
+        assert srv.poll(ids[1])["state"] == gw.NS_REQ_CANCELLED
+        srv.run_until_idle()
+        assert srv.poll(ids[2])["state"] == gw.NS_REQ_DONE
+        with pytest.raises(gw.GWNSError):
+            srv.cancel(ids[2])
