@@ -61,6 +61,19 @@ def world():
     return ws, rank
 
 
+def reduce_ranks(dist, total_ms: float, evals: float):
+    """Whole-job figures of independent replicas: the slowest rank's timed
+    region and the evaluations of all ranks."""
+    if not dist:
+        return float(total_ms), float(evals)
+    import torch
+    t = torch.tensor([float(total_ms)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e = torch.tensor([float(evals)], dtype=torch.float64)
+    dist.all_reduce(e, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(e.item())
+
+
 def init_dist(ws):
     if ws > 1:
         import torch.distributed as dist
@@ -168,14 +181,7 @@ def run_gpu(args):
     total_ms = sum(step_ms)
     st1 = sp.stats()
     evals = st1["evals"] - evals0
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e = torch.tensor([float(evals)], dtype=torch.float64)
-        dist.all_reduce(e, op=dist.ReduceOp.SUM)
-        total_ms_max, evals_all = float(t.item()), float(e.item())
-    else:
-        total_ms_max, evals_all = total_ms, float(evals)
+    total_ms_max, evals_all = reduce_ranks(dist, total_ms, evals)
     value = evals_all / (total_ms_max / 1e3)
 
     roof = slice_kernel_roofline(st0, st1, args.steps, w.n_det)
@@ -192,6 +198,7 @@ def run_gpu(args):
 
     # the serving workload (64 analyses arriving at 2/s): p50/p99 time-to-logZ
     serving = serving_stream(g) if rank == 0 else None
+    agreement = precision_agreement(g, w, stream) if rank == 0 else None
 
     if rank == 0:
         cpu = cpu_baseline() if ws == 1 else None
@@ -206,6 +213,7 @@ def run_gpu(args):
             "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
             "time_to_logZ": ttl,
             "serving": serving,
+            "mixed_vs_fp64": agreement,
             "e2e": e2e,
             "gpu_launches": 5 * args.steps + 1,   # 5 kernels per ns_step + the L2 flush fill
             "kernel_ms_per_step": [(b - a) / args.steps for a, b in zip(st0["kernel_ms"], st1["kernel_ms"])],
@@ -256,6 +264,34 @@ def time_to_logz(g, w, precision, stream):
     sp.close()
     return {"seconds": t2 - t1, "setup_s": t_setup, "iterations": it, "evals": s["evals"],
             "evals_per_s": s["evals"] / (t2 - t1), "logZ": r["logZ"], "dlogZ": r["dlogZ"]}
+
+
+def precision_agreement(g, w, stream, seeds: int = 16, points: int = 4096):
+    """Mixed against FP64 on the GPU: per-point log L difference on prior
+    draws, and log Z over `seeds` sampler seeds (same data), reported as the
+    mean difference with its standard error."""
+    sp64, th = g.make_analysis(w, precision=g.NS_FP64, stream=stream.cuda_stream)
+    spmx, _ = g.make_analysis(w, precision=g.NS_MIXED, stream=stream.cuda_stream)
+    u = gi.unit_cube(777, points, w.dim)
+    d = np.abs(spmx.eval_lnl(u) - sp64.eval_lnl(u))
+    sp64.close()
+    spmx.close()
+    dz, z64 = [], []
+    for i in range(seeds):
+        zs = []
+        for prec in (g.NS_FP64, g.NS_MIXED):
+            w2 = build_workload(g, prec)
+            w2.seed_sampler += 1000 * (i + 1)
+            sp, _ = g.make_analysis(w2, precision=prec, stream=stream.cuda_stream)
+            sp.run()
+            zs.append(sp.result(samples=False)["logZ"])
+            sp.close()
+        dz.append(zs[1] - zs[0])
+        z64.append(zs[0])
+    dz = np.array(dz)
+    return {"points": points, "max_abs_dlogL": float(d.max()), "rms_dlogL": float(np.sqrt(np.mean(d * d))),
+            "seeds": seeds, "mean_dlogZ": float(dz.mean()), "stderr_dlogZ": float(dz.std(ddof=1) / np.sqrt(seeds)),
+            "max_abs_dlogZ_single_seed": float(np.abs(dz).max()), "sd_logZ_fp64_over_seeds": float(np.std(z64, ddof=1))}
 
 
 def e2e_run(g, w, steps, stream):

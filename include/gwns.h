@@ -251,6 +251,19 @@ int ns_prior_transform(ns_ctx *ctx, const double *u, int m, double *theta);
  * theta[11]), from the closed form A^2 |Q_d|^2 P_d(jcut). */
 int ns_optimal_snr2(ns_ctx *ctx, const double *theta, double *rho2);
 
+/* Checkpoint of the run: live set, run state (log Z, log X, iteration,
+ * counters) and the dead list, in a self-describing byte buffer (host,
+ * caller-owned). With buf NULL, *len receives the size needed; otherwise
+ * *len is the buffer's size on input and the bytes written on output
+ * (CAPACITY if too small). Inputs (data, PSD, grid, options) are not stored:
+ * restore into a context created with the same ones. */
+int ns_checkpoint(ns_ctx *ctx, void *buf, size_t *len);
+
+/* Resume from a checkpoint: the continuation is bit-identical to the run that
+ * wrote it (same draws, same order). INVALID_ARG if the buffer does not match
+ * the context's n_live and dimension. */
+int ns_restore(ns_ctx *ctx, const void *buf, size_t len);
+
 /* Live set (host, each may be NULL): u [n][d], logl [n]. */
 int ns_get_live(ns_ctx *ctx, double *u, double *logl);
 

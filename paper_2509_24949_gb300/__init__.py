@@ -128,6 +128,8 @@ def lib():
         L.ns_set_live.argtypes = [vp, vp, vp]
         L.ns_sync.argtypes = [vp]
         L.ns_autotune.argtypes = [vp, ip, P(ip)]
+        L.ns_checkpoint.argtypes = [vp, vp, P(ctypes.c_size_t)]
+        L.ns_restore.argtypes = [vp, vp, ctypes.c_size_t]
         L.ns_free.argtypes = [vp]; L.ns_free.restype = None
         L.ns_server_create.argtypes = [P(vp), P(_ServerOptions)]
         L.ns_submit.argtypes = [vp, P(_Request), P(ctypes.c_uint64)]
@@ -144,7 +146,7 @@ def lib():
                      "ns_get_stats", "ns_eval_lnl", "ns_eval_lnl_host", "ns_eval_lnl_theta",
                      "ns_eval_lnl_host_noalloc",
                      "ns_waveform", "ns_prior_transform", "ns_optimal_snr2", "ns_get_live", "ns_set_live", "ns_sync",
-                     "ns_autotune"):
+                     "ns_autotune", "ns_checkpoint", "ns_restore"):
             getattr(L, name).restype = ctypes.c_int
         _LIB = L
     return _LIB
@@ -356,6 +358,17 @@ class Sampler:
 
     def sync(self):
         _check(lib().ns_sync(self._ctx), "ns_sync")
+
+    def checkpoint(self) -> bytes:
+        n = ctypes.c_size_t(0)
+        _check(lib().ns_checkpoint(self._ctx, None, ctypes.byref(n)), "ns_checkpoint")
+        buf = ctypes.create_string_buffer(n.value)
+        _check(lib().ns_checkpoint(self._ctx, buf, ctypes.byref(n)), "ns_checkpoint")
+        return buf.raw[: n.value]
+
+    def restore(self, blob: bytes):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        _check(lib().ns_restore(self._ctx, buf, len(blob)), "ns_restore")
 
     def autotune(self, trials: int = 2) -> int:
         """Pick the fastest slice-update slot count on this workload (results unchanged)."""

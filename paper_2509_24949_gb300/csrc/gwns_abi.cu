@@ -99,7 +99,7 @@ int enqueue_iteration(ns_ctx *c, int k) {
     if ((rc = mark(c, 2))) return rc;
     CK(launch_cov_chol(c->M, A, c->stream));
     if ((rc = mark(c, 3))) return rc;
-    CK(launch_slice(c->M, c->T, c->precision, choose_slots(c), A, c->stream));
+    CK(launch_slice(c->M, c->T, c->precision, slots_alloc(c), A, c->stream));
     if ((rc = mark(c, 4))) return rc;
     CK(launch_finish(A, c->stream));
     if ((rc = mark(c, 5))) return rc;
@@ -200,7 +200,18 @@ int choose_slots(const ns_ctx *c) {
     // measured on GB300 (512 / 4017 / 64,897-bin workloads): FP64 binds on its
     // pipe beyond small grids, the mixed form on latency up to large grids
     if (c->precision == NS_FP64) return bins <= 1024 ? 4 : (bins <= 131072 ? 2 : 1);
-    return bins <= 1024 ? 8 : (bins <= 131072 ? 4 : 2);
+    return bins <= 1024 ? 8 : (c->M.coop ? 2 : 4);
+}
+
+// Warps per chain CTA: twice the base depth (at most 8; 4 for the cooperative
+// mixed loop), so that the last chains of an update can plan deeper.
+int slots_alloc(const ns_ctx *c) {
+    // tail speculation doubles the slots of a chain up to 4; wider slot
+    // templates cost more registers than the deeper lookahead saves (GB300:
+    // 4 -> 8 slots lost 14% FP64 and 35% mixed on the 4017-bin workload)
+    const int base = choose_slots(c);
+    const int s = 2 * base;
+    return base >= 4 ? base : (s < 4 ? s : 4);
 }
 
 StepArgs step_args(ns_ctx *c, int k) {
@@ -221,6 +232,9 @@ StepArgs step_args(ns_ctx *c, int k) {
     A.max_stepout = c->max_so;
     A.max_shrink = c->max_sh;
     A.dlogz_stop = c->dlogz;
+    A.active = c->active;
+    A.depth = choose_slots(c);
+    A.tail = c->n_sm;
     return A;
 }
 
@@ -279,7 +293,7 @@ void ns_free(ns_ctx *c) {
                     c->fin_logl, c->fin_logw, c->fin_nlive, c->res, c->rb_J, c->rb_nedge, c->rb_fid,
                     c->rb_fe, c->rb_basis64, c->rb_basis32, c->rb_fe32, c->rb_fm, c->rb_inv_de, c->rb_A0,
                     c->rb_A1, c->rb_B0, c->rb_B1, c->rb_A0f, c->rb_A1f, c->rb_B0f, c->rb_B1f,
-                    c->rb_inv_de_f};
+                    c->rb_inv_de_f, c->active};
     for (void *p : bufs) dfree(p);
     if (c->h_state) cudaFreeHost(c->h_state);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -344,6 +358,7 @@ int ns_init(ns_ctx **out, const ns_prior *prior, const ns_data *data, const ns_p
     std::memset(&c->M, 0, sizeof(Model));
     std::memset(&c->T, 0, sizeof(Tables));
     cudaGetDevice(&c->device);
+    if (cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) c->n_sm = 152;
     Model &M = c->M;
     c->n = o->n_live;
     c->k_default = o->k ? o->k : o->n_live / 2;
@@ -389,6 +404,9 @@ int ns_init(ns_ctx **out, const ns_prior *prior, const ns_data *data, const ns_p
             dim += prior->kind[p] != NS_PRIOR_FIXED;
         }
         M.dim = dim;
+        // large grids: the mixed slice update shares each bin's table loads among
+        // the round's candidates (measured faster from ~16k bins on GB300)
+        M.coop = M.N >= 16384 ? 1 : 0;
         if (!data->ideal)
             for (int dd = 0; dd < M.n_det; dd++)
                 for (int i = 0; i < 3; i++) {
@@ -408,7 +426,7 @@ int ns_init(ns_ctx **out, const ns_prior *prior, const ns_data *data, const ns_p
         (rc = dalloc(&c->chol, (size_t)NS_MAX_DIM * NS_MAX_DIM)) || (rc = dalloc(&c->state, 1)) ||
         (rc = dalloc(&c->fin_u, (size_t)c->n * c->d)) || (rc = dalloc(&c->fin_logl, c->n)) ||
         (rc = dalloc(&c->fin_logw, c->n)) || (rc = dalloc(&c->fin_nlive, c->n)) ||
-        (rc = dalloc(&c->res, kReplicates + 8))) {
+        (rc = dalloc(&c->res, kReplicates + 8)) || (rc = dalloc(&c->active, 1))) {
         ns_free(c);
         return rc;
     }
@@ -755,6 +773,79 @@ int ns_autotune(ns_ctx *c, int trials, int *slots) {
     }
     if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; c->graph_k = -1; }
     if (slots) *slots = best;
+    return NS_OK;
+}
+
+namespace {
+struct CkptHeader {
+    char magic[8];          // "GWNSCKP1"
+    int n, d;
+    long long n_dead;
+    RunState state;
+};
+}  // namespace
+
+int ns_checkpoint(ns_ctx *c, void *buf, size_t *len) {
+    if (!c || !len) return NS_ERR_INVALID_ARG;
+    const size_t nl = (size_t)c->n, d = c->d, nd = (size_t)c->n_dead;
+    const size_t need = sizeof(CkptHeader) + sizeof(double) * (nl * (d + 1) + nd * (d + 3));
+    if (!buf) { *len = need; return NS_OK; }
+    if (*len < need) { *len = need; return NS_ERR_CAPACITY; }
+    CkptHeader h;
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, "GWNSCKP1", 8);
+    h.n = c->n;
+    h.d = c->d;
+    h.n_dead = c->n_dead;
+    CK(cudaMemcpyAsync(&h.state, c->state, sizeof(RunState), cudaMemcpyDeviceToHost, c->stream));
+    double *p = (double *)((char *)buf + sizeof(CkptHeader));
+    CK(cudaMemcpyAsync(p, c->live_u, sizeof(double) * nl * d, cudaMemcpyDeviceToHost, c->stream));
+    p += nl * d;
+    CK(cudaMemcpyAsync(p, c->live_logl, sizeof(double) * nl, cudaMemcpyDeviceToHost, c->stream));
+    p += nl;
+    if (nd) {
+        CK(cudaMemcpyAsync(p, c->dead_u, sizeof(double) * nd * d, cudaMemcpyDeviceToHost, c->stream));
+        p += nd * d;
+        CK(cudaMemcpyAsync(p, c->dead_logl, sizeof(double) * nd, cudaMemcpyDeviceToHost, c->stream));
+        p += nd;
+        CK(cudaMemcpyAsync(p, c->dead_logw, sizeof(double) * nd, cudaMemcpyDeviceToHost, c->stream));
+        p += nd;
+        CK(cudaMemcpyAsync(p, c->dead_nlive, sizeof(double) * nd, cudaMemcpyDeviceToHost, c->stream));
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    std::memcpy(buf, &h, sizeof(h));
+    *len = need;
+    return NS_OK;
+}
+
+int ns_restore(ns_ctx *c, const void *buf, size_t len) {
+    if (!c || !buf || len < sizeof(CkptHeader)) return NS_ERR_INVALID_ARG;
+    CkptHeader h;
+    std::memcpy(&h, buf, sizeof(h));
+    if (std::memcmp(h.magic, "GWNSCKP1", 8) != 0 || h.n != c->n || h.d != c->d || h.n_dead < 0)
+        return NS_ERR_INVALID_ARG;
+    const size_t nl = (size_t)c->n, d = c->d, nd = (size_t)h.n_dead;
+    if (len < sizeof(CkptHeader) + sizeof(double) * (nl * (d + 1) + nd * (d + 3))) return NS_ERR_INVALID_ARG;
+    int rc = ensure_dead_capacity(c, (long long)nd + c->k_default);
+    if (rc) return rc;
+    const double *p = (const double *)((const char *)buf + sizeof(CkptHeader));
+    CK(cudaMemcpyAsync(c->live_u, p, sizeof(double) * nl * d, cudaMemcpyHostToDevice, c->stream));
+    p += nl * d;
+    CK(cudaMemcpyAsync(c->live_logl, p, sizeof(double) * nl, cudaMemcpyHostToDevice, c->stream));
+    p += nl;
+    if (nd) {
+        CK(cudaMemcpyAsync(c->dead_u, p, sizeof(double) * nd * d, cudaMemcpyHostToDevice, c->stream));
+        p += nd * d;
+        CK(cudaMemcpyAsync(c->dead_logl, p, sizeof(double) * nd, cudaMemcpyHostToDevice, c->stream));
+        p += nd;
+        CK(cudaMemcpyAsync(c->dead_logw, p, sizeof(double) * nd, cudaMemcpyHostToDevice, c->stream));
+        p += nd;
+        CK(cudaMemcpyAsync(c->dead_nlive, p, sizeof(double) * nd, cudaMemcpyHostToDevice, c->stream));
+    }
+    *c->h_state = h.state;
+    CK(cudaMemcpyAsync(c->state, c->h_state, sizeof(RunState), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->n_dead = h.n_dead;
     return NS_OK;
 }
 

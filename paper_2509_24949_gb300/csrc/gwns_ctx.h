@@ -32,6 +32,8 @@ struct ns_ctx {
     float2 *basis32 = nullptr, *f32 = nullptr, *w32 = nullptr;
     double *live_u = nullptr, *live_logl = nullptr;
     int *order = nullptr;
+    int *active = nullptr;           // running-chain counter of the slice update
+    int n_sm = 152;
     double *chol = nullptr;
     double *dead_u = nullptr, *dead_logl = nullptr, *dead_logw = nullptr, *dead_nlive = nullptr;
     long long dead_cap = 0;
@@ -64,6 +66,7 @@ struct ns_ctx {
 namespace gwns_host {
 int cuda_fail(cudaError_t e);
 int choose_slots(const ns_ctx *c);
+int slots_alloc(const ns_ctx *c);
 StepArgs step_args(ns_ctx *c, int k);
 int ensure_dead_capacity(ns_ctx *c, long long need);
 }  // namespace gwns_host

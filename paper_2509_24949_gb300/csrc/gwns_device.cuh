@@ -41,6 +41,7 @@ struct Model {
     int model;        // M_GW or M_TOY
     int n_det, N, ideal, cutoff, dim;
     int rb;           // 1: relative-binning likelihood on the coarse bins
+    int coop;         // 1: mixed slice update strides bins with all warps for all candidates
     double f0, df;
     int kind[NPARAM];
     double lo[NPARAM], hi[NPARAM];
@@ -365,6 +366,48 @@ __device__ __forceinline__ void coef_to_mixed_warp(const Coef &c, int n_det, Coe
 }
 
 // ------------------------------------------------------------ bin loops
+// Branch-free FP64 sine and cosine for |x| < 2^16 pi/2 (TaylorF2 phases are
+// below 1e5 rad): Cody-Waite reduction r = x - k pi/2 with pi/2 split into
+// three parts of which the first two have 36 significant bits (k pi/2_i exact
+// for |k| < 2^17), k taken by the 1.5 2^52 rounding shift (its low mantissa
+// bits give the quadrant); then the Taylor series of sin and cos about 0 up to
+// r^15 and r^16 (truncation below 5e-17 for |r| <= pi/4) and the quadrant's
+// swap and signs by selects. Having no branch, two calls interleave.
+__device__ __forceinline__ void sincos_bf(double x, double &s, double &c) {
+    const double shift = 6755399441055744.0;                  // 1.5 * 2^52
+    const double kk = fma(x, 0.6366197723675814, shift);      // 2/pi
+    const int q = __double2loint(kk) & 3;
+    const double k = kk - shift;
+    double r = fma(-k, 1.5707963267923333, x);
+    r = fma(-k, 2.5633441515839558e-12, r);
+    r = fma(-k, 1.0562999066987428e-23, r);
+    const double r2 = r * r;
+    // sin r = r + r^3 (-1/3! + r^2 (1/5! - ...)), up to r^15/15!
+    double ps = -7.647163731819816e-13;
+    ps = fma(ps, r2, 1.6059043836821613e-10);
+    ps = fma(ps, r2, -2.505210838544172e-08);
+    ps = fma(ps, r2, 2.7557319223985893e-06);
+    ps = fma(ps, r2, -0.0001984126984126984);
+    ps = fma(ps, r2, 0.008333333333333333);
+    ps = fma(ps, r2, -0.16666666666666666);
+    const double sn = fma(r * r2, ps, r);
+    // cos r = 1 + r^2 (-1/2! + r^2 (1/4! - ...)), up to r^16/16!
+    double pc = 4.779477332387385e-14;
+    pc = fma(pc, r2, -1.1470745597729725e-11);
+    pc = fma(pc, r2, 2.08767569878681e-09);
+    pc = fma(pc, r2, -2.755731922398589e-07);
+    pc = fma(pc, r2, 2.48015873015873e-05);
+    pc = fma(pc, r2, -0.001388888888888889);
+    pc = fma(pc, r2, 0.041666666666666664);
+    pc = fma(pc, r2, -0.5);
+    const double cs = fma(r2, pc, 1.0);
+    // quadrant q: (sin, cos) = (sn, cs), (cs, -sn), (-sn, -cs), (-cs, sn)
+    const double a = (q & 1) ? cs : sn;
+    const double b = (q & 1) ? sn : cs;
+    s = (q & 2) ? -a : a;
+    c = ((q + 1) & 2) ? -b : b;
+}
+
 // FP64: Psi_j from the basis (FP64 FMAs), exp(i Psi_j) by sincos, the detector
 // factor exp(2 pi i f_j tau_d) by a rotation recurrence along the thread's bins
 // (f advances by stride*df per step).
@@ -385,12 +428,42 @@ __device__ __forceinline__ void bins_fp64(const Tables &T, int N, double f0, dou
             else sincos(TWO_PI_D * (stride * df) * c.tau[d], &pi_[d], &pr[d]);
         }
     }
-    for (int j = tid; j <= c.jcut; j += stride) {
+    int j = tid;
+    // two bins per step (j and j + stride): independent phase and sincos chains
+    for (; j + stride <= c.jcut; j += 2 * stride) {
+        const int j2 = j + stride;
+        double psi = c0, psi2 = c0;
+#pragma unroll
+        for (int m = 0; m < NB; m++) {
+            psi = fma(a[m], __ldg(T.basis64 + (size_t)m * N + j), psi);
+            psi2 = fma(a[m], __ldg(T.basis64 + (size_t)m * N + j2), psi2);
+        }
+        double s, co, s2, co2;
+        sincos_bf(psi, s, co);
+        sincos_bf(psi2, s2, co2);
+#pragma unroll
+        for (int d = 0; d < NDET; d++) {
+            // rotation of the second bin, then both contributions
+            const double r2r = rr[d] * pr[d] - ri[d] * pi_[d];
+            const double r2i = rr[d] * pi_[d] + ri[d] * pr[d];
+            const double er = co * rr[d] - s * ri[d], ei = co * ri[d] + s * rr[d];
+            const double er2 = co2 * r2r - s2 * r2i, ei2 = co2 * r2i + s2 * r2r;
+            const double2 w = __ldg(T.w64 + (size_t)d * N + j);
+            const double2 w2 = __ldg(T.w64 + (size_t)d * N + j2);
+            zr[d] = fma(w.x, er, fma(-w.y, ei, zr[d]));
+            zi[d] = fma(w.x, ei, fma(w.y, er, zi[d]));
+            zr[d] = fma(w2.x, er2, fma(-w2.y, ei2, zr[d]));
+            zi[d] = fma(w2.x, ei2, fma(w2.y, er2, zi[d]));
+            rr[d] = r2r * pr[d] - r2i * pi_[d];
+            ri[d] = r2r * pi_[d] + r2i * pr[d];
+        }
+    }
+    if (j <= c.jcut) {
         double psi = c0;
 #pragma unroll
         for (int m = 0; m < NB; m++) psi = fma(a[m], __ldg(T.basis64 + (size_t)m * N + j), psi);
         double s, co;
-        sincos(psi, &s, &co);
+        sincos_bf(psi, s, co);
 #pragma unroll
         for (int d = 0; d < NDET; d++) {
             const double er = co * rr[d] - s * ri[d];
@@ -398,9 +471,6 @@ __device__ __forceinline__ void bins_fp64(const Tables &T, int N, double f0, dou
             const double2 w = __ldg(T.w64 + (size_t)d * N + j);
             zr[d] = fma(w.x, er, fma(-w.y, ei, zr[d]));
             zi[d] = fma(w.x, ei, fma(w.y, er, zi[d]));
-            const double nr = rr[d] * pr[d] - ri[d] * pi_[d];
-            ri[d] = rr[d] * pi_[d] + ri[d] * pr[d];
-            rr[d] = nr;
         }
     }
 }
@@ -479,6 +549,94 @@ __device__ __forceinline__ void bins_mixed(const Tables &T, int N, const CoefMix
     for (int d = 0; d < NDET; d++) {
         zr[d] = (double)zrh[d] + (double)zrl[d];
         zi[d] = (double)zih[d] + (double)zil[d];
+    }
+}
+
+// Mixed, several candidates at once: every thread of the CTA strides over the
+// bins and applies each of the ns candidates (coefficients in shared memory) to
+// the bin's table values, which are loaded once. Candidate s only takes bins
+// j <= jcut[s]. Per (candidate, detector) the thread keeps FP32 partials over
+// FLUSH bins and double-float running sums (zh, zl), returned unreduced.
+template <int NDET, int S>
+__device__ __forceinline__ void bins_mixed_multi(const Tables &T, int N, const CoefMixed *cm, const int *jcut,
+                                                 int ns, int tid, int stride, float zrh[S][NDET],
+                                                 float zrl[S][NDET], float zih[S][NDET], float zil[S][NDET]) {
+    int jmax = -1;
+    for (int s = 0; s < ns; s++) jmax = max(jmax, jcut[s]);
+#pragma unroll
+    for (int s = 0; s < S; s++)
+#pragma unroll
+        for (int d = 0; d < NDET; d++) zrh[s][d] = zrl[s][d] = zih[s][d] = zil[s][d] = 0.f;
+    constexpr int FLUSH = 16;
+    int j = tid;
+    while (j <= jmax) {
+        float pr[S][NDET], pim[S][NDET];
+#pragma unroll
+        for (int s = 0; s < S; s++)
+#pragma unroll
+            for (int d = 0; d < NDET; d++) pr[s][d] = pim[s][d] = 0.f;
+        for (int it = 0; it < FLUSH && j <= jmax; it++, j += stride) {
+            float2 b[NB];
+#pragma unroll
+            for (int m = 0; m < NB; m++) b[m] = __ldg(T.basis32 + (size_t)m * N + j);
+            const float2 fj = __ldg(T.f32 + j);
+            float2 w[NDET];
+#pragma unroll
+            for (int d = 0; d < NDET; d++) w[d] = __ldg(T.w32 + (size_t)d * N + j);
+#pragma unroll
+            for (int s = 0; s < S; s++) {
+                if (s >= ns || j > jcut[s]) continue;
+                const CoefMixed &c = cm[s];
+                float sh = c.c0h, sl = c.c0l;
+#pragma unroll
+                for (int m = 0; m < NB; m++) {
+                    const float ah = c.ah[m], al = c.al[m];
+                    const float p = ah * b[m].x;
+                    float e = fmaf(ah, b[m].x, -p);
+                    e = fmaf(ah, b[m].y, e);
+                    e = fmaf(al, b[m].x, e);
+                    float s2, e2;
+                    two_sum(sh, p, s2, e2);
+                    sh = s2;
+                    sl += e2 + e;
+                }
+#pragma unroll
+                for (int d = 0; d < NDET; d++) {
+                    const float th = c.tauh[d], tl = c.taul[d];
+                    const float p = th * fj.x;
+                    float e = fmaf(th, fj.x, -p);
+                    e = fmaf(th, fj.y, e);
+                    e = fmaf(tl, fj.x, e);
+                    float s2, e2;
+                    two_sum(sh, p, s2, e2);
+                    const float n = rintf(s2);
+                    const float r = (s2 - n) + (sl + (e2 + e));
+                    float sv, cv;
+                    __sincosf(r * 6.283185307179586f, &sv, &cv);
+                    pr[s][d] = fmaf(w[d].x, cv, fmaf(-w[d].y, sv, pr[s][d]));
+                    pim[s][d] = fmaf(w[d].x, sv, fmaf(w[d].y, cv, pim[s][d]));
+                }
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < S; s++)
+#pragma unroll
+            for (int d = 0; d < NDET; d++) {
+                df_acc(zrh[s][d], zrl[s][d], pr[s][d]);
+                df_acc(zih[s][d], zil[s][d], pim[s][d]);
+            }
+    }
+}
+
+// Double-float warp sum (TwoSum of the high parts, low parts added).
+__device__ __forceinline__ void warp_sum_df(float &h, float &l) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
+        float s, e;
+        two_sum(h, oh, s, e);
+        h = s;
+        l = l + ol + e;
     }
 }
 

@@ -413,26 +413,44 @@ cudaError_t launch_evidence(const Model &M, const StepArgs &A, cudaStream_t s) {
 __device__ void cov_chol_body(const Model &M, const StepArgs &A) {
     __shared__ double mean[MAXD];
     __shared__ double cov[MAXD * MAXD];
-    __shared__ double scratch[32];
+    __shared__ double xs[64][MAXD + 1];     // a tile of survivors, centred
     const int d = M.dim, n = A.n, k = A.k, m = n - k;
-    for (int i = 0; i < d; i++) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    // means: warp w sums coordinate w (and w + nw, ...) over all survivors
+    for (int i = warp; i < d; i += nw) {
         double s = 0.0;
-        for (int p = threadIdx.x; p < m; p += blockDim.x) s += A.live_u[(size_t)A.order[k + p] * d + i];
-        s = block_sum(s, scratch);
-        if (threadIdx.x == 0) mean[i] = s / m;
+        for (int p = lane; p < m; p += 32) s += A.live_u[(size_t)A.order[k + p] * d + i];
+        s = warp_sum(s);
+        if (lane == 0) mean[i] = s / m;
     }
     __syncthreads();
-    for (int i = 0; i < d; i++) {
-        for (int j = 0; j <= i; j++) {
-            double s = 0.0;
-            for (int p = threadIdx.x; p < m; p += blockDim.x) {
-                const double *x = A.live_u + (size_t)A.order[k + p] * d;
-                s += (x[i] - mean[i]) * (x[j] - mean[j]);
-            }
-            s = block_sum(s, scratch);
-            if (threadIdx.x == 0) { cov[i * d + j] = s / (m - 1); cov[j * d + i] = s / (m - 1); }
-        }
+    // covariance: thread t owns entries (i, j), j <= i, t = i (i + 1)/2 + j, and
+    // accumulates them over tiles of 64 centred survivors held in shared memory
+    const int npair = d * (d + 1) / 2;
+    int pi = 0, pj = 0;
+    if ((int)threadIdx.x < npair) {
+        int t = threadIdx.x;
+        while (t > pi) { t -= pi + 1; pi++; }
+        pj = t;
     }
+    double acc = 0.0;
+    for (int p0 = 0; p0 < m; p0 += 64) {
+        for (int e = threadIdx.x; e < 64 * d; e += blockDim.x) {
+            const int p = e / d, i = e % d;
+            xs[p][i] = (p0 + p < m) ? A.live_u[(size_t)A.order[k + p0 + p] * d + i] - mean[i] : 0.0;
+        }
+        __syncthreads();
+        if ((int)threadIdx.x < npair) {
+            const int pe = min(64, m - p0);
+            for (int p = 0; p < pe; p++) acc += xs[p][pi] * xs[p][pj];
+        }
+        __syncthreads();
+    }
+    if ((int)threadIdx.x < npair) {
+        cov[pi * d + pj] = acc / (m - 1);
+        cov[pj * d + pi] = acc / (m - 1);
+    }
+    if (threadIdx.x == 0 && A.active) *A.active = A.k;     // chains of the coming slice update
     __syncthreads();
     if (threadIdx.x < 32) {
         const int lane = threadIdx.x;
@@ -640,11 +658,12 @@ __device__ void chain_run(const Model &M, const StepArgs &A, Chain &c, int chain
 // ysh[slot][*] and their keys to pk/pi; returns the number of slots used.
 template <int S>
 __device__ int chain_plan(const Model &M, const StepArgs &A, const Chain &c, int chain, uint32_t iter,
-                          double (*ysh)[MAXD], int *pk, int *pidx) {
+                          double (*ysh)[MAXD], int *pk, int *pidx, int depth) {
     const int lane = threadIdx.x & 31, d = M.dim;
     int ns = 0;
     const int room = CACHE_MAX - c.ncache;
-    const int cap = S < room ? S : room;
+    const int lim = depth < S ? depth : S;
+    const int cap = lim < room ? lim : room;
     if (c.phase == PH_OUT) {
         // the side in progress first (half the slots if the other side is
         // still open), then the other side; each looks at most S candidates
@@ -691,6 +710,8 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
     __shared__ double ysh[S][MAXD];
     __shared__ double lval[S];
     __shared__ int nslot;
+    __shared__ int jc[S];
+    __shared__ double part[S][S][NDET][2];
     if (chain >= A.k) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, d = M.dim;
     const uint32_t iter = (uint32_t)A.state->iter;
@@ -713,7 +734,14 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
     for (;;) {
         if (warp == 0) {
             chain_run(M, A, c, chain, iter, lstar);
-            int ns = (c.phase == PH_DONE) ? 0 : chain_plan<S>(M, A, c, chain, iter, ysh, pk, pidx);
+            // plan the base depth while many chains run; the stragglers of the
+            // update (fewer running chains than the tail threshold) use every warp
+            int depth = S;
+            if (A.active) {
+                const int running = *((volatile int *)A.active);
+                if (running > A.tail) depth = A.depth;
+            }
+            int ns = (c.phase == PH_DONE) ? 0 : chain_plan<S>(M, A, c, chain, iter, ysh, pk, pidx, depth);
             if (ns == 0 && c.phase != PH_DONE) {
                 // cannot happen with the bounds above; end the chain at its
                 // current (in-slice) point and flag the run state
@@ -743,6 +771,40 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
             if (lane == 0) {
                 lval[warp] = v;
                 coef[warp].jcut = T.rb.nb - 1;     // bins counted for the work statistics
+            }
+        } else if (PREC == 1 && S > 1 && S <= 4 && M.model == M_GW && !M.rb && M.coop) {
+            // mixed: all warps stride the bins for all candidates of the round
+            if (warp < ns) coef_to_mixed_warp(coef[warp], M.n_det, &cm[warp]);
+            if (lane == 0 && warp < ns) jc[warp] = coef[warp].jcut;
+            __syncthreads();
+            float zrh[S][NDET], zrl[S][NDET], zih[S][NDET], zil[S][NDET];
+            bins_mixed_multi<NDET, S>(T, M.N, cm, jc, ns, threadIdx.x, S * 32, zrh, zrl, zih, zil);
+#pragma unroll
+            for (int sc = 0; sc < S; sc++)
+#pragma unroll
+                for (int dd = 0; dd < NDET; dd++) {
+                    warp_sum_df(zrh[sc][dd], zrl[sc][dd]);
+                    warp_sum_df(zih[sc][dd], zil[sc][dd]);
+                    if (lane == 0) {
+                        part[warp][sc][dd][0] = (double)zrh[sc][dd] + (double)zrl[sc][dd];
+                        part[warp][sc][dd][1] = (double)zih[sc][dd] + (double)zil[sc][dd];
+                    }
+                }
+            __syncthreads();
+            if (warp == 0) {
+                // lane = (candidate, detector): sum over warps, then log L per candidate
+                double v = 0.0;
+                const int sc = lane / NDET, dd = lane % NDET;
+                if (sc < ns && lane < S * NDET) {
+                    double ZR = 0.0, ZI = 0.0;
+                    for (int w2 = 0; w2 < S; w2++) { ZR += part[w2][sc][dd][0]; ZI += part[w2][sc][dd][1]; }
+                    v = coef[sc].gre[dd] * ZR - coef[sc].gim[dd] * ZI;
+                }
+                for (int sc2 = 0; sc2 < ns; sc2++) {
+                    double t = (lane / NDET == sc2 && lane < S * NDET) ? v : 0.0;
+                    t = warp_sum(t);
+                    if (lane == 0) lval[sc2] = t - 0.5 * coef[sc2].hh;
+                }
             }
         } else if (warp < ns) {
             // one candidate per slot warp: bins and warp reduction
@@ -778,6 +840,7 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
         if (lane < d) A.live_u[(size_t)dst * d + lane] = c.x;
         if (lane == 0) {
             A.live_logl[dst] = c.lx;
+            if (A.active) atomicSub(A.active, 1);
             atomicAdd(&A.state->evals, (unsigned long long)c.evals);
             atomicAdd(&A.state->caps, (unsigned long long)c.caps);
             atomicAdd(&A.state->point_bins, c.bins);

@@ -38,6 +38,9 @@ struct StepArgs {
     uint64_t seed;
     int n, k, steps, max_stepout, max_shrink;
     double dlogz_stop;
+    int *active;          // chains of the current slice update still running
+    int depth;            // candidates planned per round while many chains run
+    int tail;             // below this many running chains, plan as many as there are warps
 };
 
 // One analysis' iteration arguments, for the multi-analysis launches.

@@ -14,6 +14,8 @@
 #include <chrono>
 #include <cstring>
 #include <deque>
+#include <map>
+#include <utility>
 #include <new>
 #include <unordered_map>
 #include <vector>
@@ -157,7 +159,9 @@ int iterate_all(ns_server *s) {
     const int na = (int)s->running.size();
     if (na == 0) return NS_OK;
     std::vector<Desc> desc(na);
-    std::vector<int2> map[NS_MAX_DET + 1];
+    // slice-update launches grouped by (detector count, warps per chain): every
+    // analysis always runs at its own width, whatever the mix
+    std::map<std::pair<int, int>, std::vector<int2>> groups;
     for (int a = 0; a < na; a++) {
         ns_ctx *c = s->reqs[s->running[a]].ctx;
         const int k = c->k_default;
@@ -166,7 +170,8 @@ int iterate_all(ns_server *s) {
         desc[a].M = c->M;
         desc[a].T = c->T;
         desc[a].A = step_args(c, k);
-        for (int ch = 0; ch < k; ch++) map[c->M.n_det].push_back(make_int2(a, ch));
+        std::vector<int2> &g = groups[std::make_pair(c->M.n_det, slots_alloc(c))];
+        for (int ch = 0; ch < k; ch++) g.push_back(make_int2(a, ch));
     }
     if (na > s->desc_cap) {
         cudaFree(s->d_desc);
@@ -175,7 +180,7 @@ int iterate_all(ns_server *s) {
         s->desc_cap = na * 2;
     }
     size_t nmap = 0;
-    for (auto &m : map) nmap += m.size();
+    for (auto &kv : groups) nmap += kv.second.size();
     if ((int)nmap > s->map_cap) {
         cudaFree(s->d_map);
         s->d_map = nullptr;
@@ -185,14 +190,12 @@ int iterate_all(ns_server *s) {
     SCK(cudaMemcpyAsync(s->d_desc, desc.data(), sizeof(Desc) * na, cudaMemcpyHostToDevice, s->stream));
     SCK(gwns::launch_iteration_multi_head(s->d_desc, na, s->stream));
     size_t off = 0;
-    for (int nd = 1; nd <= NS_MAX_DET; nd++) {
-        if (map[nd].empty()) continue;
-        SCK(cudaMemcpyAsync(s->d_map + off, map[nd].data(), sizeof(int2) * map[nd].size(),
-                            cudaMemcpyHostToDevice, s->stream));
-        const int slots = choose_slots(s->reqs[s->running[map[nd][0].x]].ctx);
-        SCK(gwns::launch_slice_multi(s->d_desc, s->d_map + off, (int)map[nd].size(), s->o.precision, nd, slots,
-                                     s->stream));
-        off += map[nd].size();
+    for (auto &kv : groups) {
+        const std::vector<int2> &g = kv.second;
+        SCK(cudaMemcpyAsync(s->d_map + off, g.data(), sizeof(int2) * g.size(), cudaMemcpyHostToDevice, s->stream));
+        SCK(gwns::launch_slice_multi(s->d_desc, s->d_map + off, (int)g.size(), s->o.precision, kv.first.first,
+                                     kv.first.second, s->stream));
+        off += g.size();
     }
     SCK(gwns::launch_iteration_multi_tail(s->d_desc, na, s->stream));
     for (int a = 0; a < na; a++) {

@@ -1,0 +1,46 @@
+"""bench.py's multi-GPU mode runs independent replicas (one analysis per rank,
+no collective on the data path); its whole-job numbers are the slowest rank's
+time and the sum of all ranks' evaluations. Checked with two gloo ranks on CPU."""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _rank(rank, port, out):
+    import torch.distributed as dist
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE="2")
+    dist.init_process_group("gloo", rank=rank, world_size=2)
+    ms, ev = bench.reduce_ranks(dist, total_ms=100.0 + 50.0 * rank, evals=1000 + rank)
+    out.put((rank, ms, ev))
+    dist.destroy_process_group()
+
+
+def test_replica_aggregation_two_ranks():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_rank, args=(r, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in ps)
+    for p in ps:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for r, ms, ev in res:
+        assert ms == 150.0 and ev == 2001.0
+
+
+def test_single_rank_passthrough():
+    import bench
+    assert bench.reduce_ranks(None, 12.5, 7) == (12.5, 7.0)

@@ -344,3 +344,79 @@ def test_autotune_keeps_the_trajectory(gw):
     s = sp.stats()
     assert s["iterations"] == 2 and s["evals"] == st.evals
     sp.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_checkpoint_resume_is_bit_identical(gw, precision):
+    w, pb, th = problem("c0")
+    args = dict(n_live=100, k=50, steps_per_dim=w.steps_per_dim, seed=w.seed_sampler)
+    with sampler_from(gw, pb, precision, **args) as a:
+        for _ in range(3):
+            a.step()
+        blob = a.checkpoint()
+        for _ in range(4):
+            a.step()
+        ua, la = a.live()
+        ra = a.result()
+    with sampler_from(gw, pb, precision, **args) as b:
+        b.restore(blob)
+        for _ in range(4):
+            b.step()
+        ub, lb = b.live()
+        rb = b.result()
+    assert np.array_equal(ua, ub) and np.array_equal(la, lb)
+    assert ra["logZ"] == rb["logZ"] and np.array_equal(ra["logw"], rb["logw"])
+
+
+def test_shrink_cap_keeps_the_chain_in_the_slice(gw):
+    """A stuck chain (no shrink draw allowed) keeps its current point, counts a
+    cap hit per step and the run goes on."""
+    w, pb, th = problem("c0")
+    with sampler_from(gw, pb, 0, n_live=60, k=30, steps_per_dim=2, seed=3, max_shrink=1) as sp:
+        lstar_prev = -np.inf
+        for _ in range(3):
+            sp.step()
+            s = sp.stats()
+            _, l = sp.live()
+            assert np.all(l > s["lstar"]) and s["lstar"] >= lstar_prev
+            lstar_prev = s["lstar"]
+        assert s["cap_hits"] > 0 and s["status"] == 0
+
+
+@pytest.mark.parametrize("slots", [2, 4])
+def test_mixed_large_grid_cooperative_bins(gw, slots):
+    """Grids of 16k bins or more use the cooperative mixed bin loop (all warps,
+    all candidates of a round): same per-point tolerance against the oracle,
+    through the sampler (live points after one iteration are re-evaluated by
+    the oracle)."""
+    w, pb, th = problem("c2")
+    with sampler_from(gw, pb, 1, n_live=60, k=30, steps_per_dim=2, seed=5, slots=slots) as sp:
+        sp.step()
+        u, l = sp.live()
+    want = pb.loglike(u)
+    assert np.max(np.abs(l - want)) < MIXED_ATOL
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_c1_model_run_against_oracle(gw, precision):
+    """The 3-detector, 11-parameter, 4017-bin model (300 live points, 150
+    deleted per iteration): log Z within 3 combined sigma of the oracle's and a
+    per-parameter two-sample KS test of the posteriors at p > 0.01."""
+    w, pb, th = problem("c1")
+    n_live, k = 300, 150
+    ref = ons.run(pb, n_live=n_live, k=k, steps=w.steps_per_dim * pb.dim, seed=w.seed_sampler)
+    with sampler_from(gw, pb, precision, n_live=n_live, k=k, steps_per_dim=w.steps_per_dim,
+                      seed=w.seed_sampler) as sp:
+        sp.run()
+        r = sp.result()
+    sig = math.hypot(r["dlogZ"], ref["dlogZ"])
+    assert abs(r["logZ"] - ref["logZ"]) < 3 * sig, (r["logZ"], ref["logZ"], sig)
+    lw_g = r["logw"] + r["logl"] - r["logZ"]
+    lw_o = ref["logw"] + ref["logl"] - ref["logZ"]
+    sg = ons.equal_weight_resample(r["u"], lw_g, 1)
+    so = ons.equal_weight_resample(ref["samples_u"], lw_o, 2)
+    for i in range(pb.dim):
+        assert stats.ks_2samp(sg[:, i], so[:, i]).pvalue > 0.01, i
+    if precision == 0:
+        # same draws, FP64 on both sides: the same run
+        assert r["logZ"] == pytest.approx(ref["logZ"], abs=1e-6)
