@@ -48,7 +48,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # detectors, in FMA-equivalents: 8 basis FMAs + one sincos (32 FMA-equivalents
 # on this GPU) + per detector 4 (phasor product) + 4 (complex MAC) + 4
 # (phasor rotation). 1 FMA = 2 flops.
-K_SLICE_FP64_C1_DRAM_BYTES = None   # re-captured after the kernel changes
+K_SLICE_FP64_C1_DRAM_BYTES = 297216   # re-captured after the kernel changes
 
 
 def fp64_flops_per_point_bin(n_det: int) -> float:
@@ -189,19 +189,21 @@ def run_gpu(args):
 
     # time-to-logZ, FP64 and mixed, full runs from ns_init to ns_result
     ttl = {}
-    for name, prec in (("fp64", g.NS_FP64), ("mixed", g.NS_MIXED)):
-        ttl[name] = time_to_logz(g, w, prec, stream)
+    if not args.core_only:
+        for name, prec in (("fp64", g.NS_FP64), ("mixed", g.NS_MIXED)):
+            ttl[name] = time_to_logz(g, w, prec, stream)
 
     # end-to-end through the C ABI with host buffers: ns_init from host arrays,
     # then K ns_step_host calls that copy each iteration's dead points to host
     e2e = e2e_run(g, w, args.steps, stream)
 
     # the serving workload (64 analyses arriving at 2/s): p50/p99 time-to-logZ
-    serving = serving_stream(g) if rank == 0 else None
-    agreement = precision_agreement(g, w, stream) if rank == 0 else None
+    extras = rank == 0 and not args.core_only
+    serving = serving_stream(g) if extras else None
+    agreement = precision_agreement(g, w, stream) if extras else None
 
     if rank == 0:
-        cpu = cpu_baseline() if ws == 1 else None
+        cpu = cpu_baseline() if ws == 1 and not args.core_only else None
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps,
@@ -455,6 +457,10 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gwns", choices=["gwns", "reference"])
+    ap.add_argument("--core-only", action="store_true",
+                    help="measure the timed steps and e2e only, without the time-to-logZ, serving, "
+                         "agreement and CPU-baseline reports (for profiler runs); the timed region "
+                         "is the same")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
