@@ -1,7 +1,8 @@
 """Build the C-ABI shared library libgwns.so in-tree with nvcc for sm_103a.
 
-The translation units are compiled in parallel and linked with the static CUDA
-runtime; the result lands in paper_2509_24949_gb300/_build/libgwns.so.
+The translation units (the likelihood and slice kernels are instantiated in one
+unit per precision and detector count) are compiled in parallel and linked with
+the static CUDA runtime; the result lands in paper_2509_24949_gb300/_build/libgwns.so.
 """
 from __future__ import annotations
 
@@ -15,7 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libgwns.so")
-SOURCES = ["gwns_abi.cu", "gwns_kernels.cu", "gwns_serve.cu"]
+SOURCES = ["gwns_abi.cu", "gwns_kernels.cu", "gwns_serve.cu"] + [
+    f"gwns_inst_p{p}_d{d}.cu" for p in (0, 1) for d in (1, 2, 3, 4)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

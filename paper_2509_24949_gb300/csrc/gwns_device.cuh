@@ -628,6 +628,18 @@ __device__ __forceinline__ void bins_mixed_multi(const Tables &T, int N, const C
     }
 }
 
+// ------------------------------------------------------------- warp helpers
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
 // Double-float warp sum (TwoSum of the high parts, low parts added).
 __device__ __forceinline__ void warp_sum_df(float &h, float &l) {
 #pragma unroll

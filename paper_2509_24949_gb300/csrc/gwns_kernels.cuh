@@ -50,6 +50,15 @@ struct Desc {
     StepArgs A;
 };
 
+// Copy of an analysis' descriptor into shared memory by the whole block
+// (multi-analysis launches); ends with a barrier.
+__device__ __forceinline__ void load_desc(const Desc *g, Desc &s) {
+    const int *src = (const int *)g;
+    int *dst = (int *)&s;
+    for (int i = threadIdx.x; i < (int)(sizeof(Desc) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+}
+
 struct ResultArgs {
     const double *dead_logl, *dead_logw, *dead_nlive;
     const double *fin_logl, *fin_logw, *fin_nlive;   // [n] final live points, ascending
@@ -69,6 +78,16 @@ constexpr size_t NOALLOC_DOUBLES = (size_t)NOALLOC_MAX_POINTS * (MAXD + 1);
 // Device address of that staging array on the current device (looked up once
 // per device and cached; never allocates).
 cudaError_t noalloc_scratch_address(double **ptr);
+
+// Likelihood and slice-update launchers per (precision, detectors), defined in
+// gwns_slice.cuh and instantiated in gwns_inst_p<P>_d<D>.cu.
+template <int PREC, int NDET>
+cudaError_t eval_launch(const Model &M, const Tables &T, int warps, const double *in, int th, int m,
+                        double *logl, cudaStream_t s);
+template <int PREC, int NDET>
+cudaError_t slice_launch(const Model &M, const Tables &T, int slots, const StepArgs &A, cudaStream_t s);
+template <int PREC, int NDET>
+cudaError_t slice_multi_launch(const Desc *D, const int2 *map, int nblocks, int slots, cudaStream_t s);
 
 // Launchers (return cudaGetLastError()).
 cudaError_t launch_build_tables(const Model &M, const double *data_re, const double *data_im,

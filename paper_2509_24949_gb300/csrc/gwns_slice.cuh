@@ -1,0 +1,508 @@
+// gwns_slice.cuh -- the per-candidate likelihood and the slice-sampling
+// update (paper Sec. 2) as templates over precision and detector count. Each
+// gwns_inst_p<P>_d<D>.cu translation unit instantiates one (precision,
+// detectors) pair, so the kernels compile in parallel.
+#pragma once
+#include "gwns_kernels.cuh"
+
+namespace gwns {
+
+// Coefficients of one point from warp 0 (shared), then all warps run the bin
+// loop and the CTA reduces Z_d. Returns log L in *lval (shared) after the
+// second barrier; every thread of the CTA must call it.
+template <int PREC, int NDET, int W>
+__device__ __forceinline__ void cta_loglike_bins(const Model &M, const Tables &T, Coef &coef,
+                                                 CoefMixed &cm, double (*red)[2 * MAXDET], double *lval) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double zr[NDET], zi[NDET];
+    if (PREC == 0) {
+        bins_fp64<NDET>(T, M.N, M.f0, M.df, coef, threadIdx.x, W * 32, zr, zi);
+    } else {
+        bins_mixed<NDET>(T, M.N, cm, coef.jcut, threadIdx.x, W * 32, zr, zi);
+    }
+#pragma unroll
+    for (int d = 0; d < NDET; d++) {
+        zr[d] = warp_sum(zr[d]);
+        zi[d] = warp_sum(zi[d]);
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int d = 0; d < NDET; d++) { red[warp][2 * d] = zr[d]; red[warp][2 * d + 1] = zi[d]; }
+    }
+    __syncthreads();
+    if (warp == 0) {
+        double v = 0.0;
+        if (lane < NDET) {
+            double ZR = 0.0, ZI = 0.0;
+            for (int w = 0; w < W; w++) { ZR += red[w][2 * lane]; ZI += red[w][2 * lane + 1]; }
+            v = coef.gre[lane] * ZR - coef.gim[lane] * ZI;
+        }
+        v = warp_sum(v);
+        if (lane == 0) *lval = (M.model == M_TOY) ? coef.toy : v - 0.5 * coef.hh;
+    }
+}
+
+// Warp 0 computes the coefficients of the point with unit-cube coordinates u
+// (or physical parameters theta when in_is_theta).
+__device__ __forceinline__ void warp_point_coef(const Model &M, const Tables &T, const double *in,
+                                                int in_is_theta, int precision, Coef *coef,
+                                                CoefMixed *cm) {
+    const int lane = threadIdx.x & 31;
+    if (M.model == M_TOY) {
+        point_coef_warp(M, T, in, coef);
+        return;
+    }
+    if (in_is_theta) {
+        // a model whose parameters are all FIXED at theta
+        Model Mt = M;
+#pragma unroll
+        for (int p = 0; p < NPARAM; p++) { Mt.kind[p] = K_FIXED; Mt.lo[p] = in[p]; }
+        point_coef_warp(Mt, T, in, coef);
+    } else {
+        point_coef_warp(M, T, in, coef);
+    }
+    __syncwarp();
+    if (precision == 1) coef_to_mixed_warp(*coef, M.n_det, cm, M.rb ? T.rb.fid : nullptr);
+    (void)lane;
+}
+
+template <int PREC, int NDET, int W>
+__global__ void __launch_bounds__(W * 32) k_eval(Model M, Tables T, const double *in, int in_is_theta,
+                                                 int m, double *logl) {
+    __shared__ Coef coef;
+    __shared__ CoefMixed cm;
+    __shared__ double red[W][2 * MAXDET];
+    __shared__ double lval;
+    __shared__ double pt[NPARAM + MAXD];
+    const int i = blockIdx.x;
+    if (i >= m) return;
+    const int stride_in = in_is_theta ? NPARAM : M.dim;
+    if (threadIdx.x < stride_in) pt[threadIdx.x] = in[(size_t)i * stride_in + threadIdx.x];
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0) warp_point_coef(M, T, pt, in_is_theta, PREC, &coef, &cm);
+    __syncthreads();
+    if (M.rb) {
+        // relative-binning sums: one warp
+        if ((threadIdx.x >> 5) == 0) {
+            const int lane = threadIdx.x & 31;
+            const double v = rb_loglike_warp<NDET, PREC>(M, T.rb, coef, cm, lane);
+            if (lane == 0) logl[i] = v;
+        }
+        return;
+    }
+    cta_loglike_bins<PREC, NDET, W>(M, T, coef, cm, red, &lval);
+    if (threadIdx.x == 0) logl[i] = lval;
+}
+
+template <int PREC, int NDET>
+cudaError_t eval_launch(const Model &M, const Tables &T, int warps, const double *in, int th, int m,
+                        double *logl, cudaStream_t s) {
+    switch (warps) {
+        case 1: k_eval<PREC, NDET, 1><<<m, 32, 0, s>>>(M, T, in, th, m, logl); break;
+        case 2: k_eval<PREC, NDET, 2><<<m, 64, 0, s>>>(M, T, in, th, m, logl); break;
+        case 4: k_eval<PREC, NDET, 4><<<m, 128, 0, s>>>(M, T, in, th, m, logl); break;
+        default: k_eval<PREC, NDET, 8><<<m, 256, 0, s>>>(M, T, in, th, m, logl); break;
+    }
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ slice update
+// One CTA per chain, S warps ("slots"). Warp 0 owns the chain: the point x,
+// the direction e and the bracket (lane i < d holds coordinate i). Every slice
+// step draws a direction and a bracket offset, steps out to the left and to the
+// right, then shrinks (Neal 2003, Sec. 4, along a hit-and-run direction).
+//
+// The candidates of each stage form sequences fixed by the draws alone:
+// stepping out to the left visits x + (a - q) e, to the right x + (b + q) e,
+// and the q-th shrink draw is determined once the earlier draws are known to be
+// rejected. Each round, warp 0 plans the next S candidates of these sequences
+// that lie inside the prior box and are not yet evaluated; every slot warp
+// computes one candidate's coefficients and bins; warp 0 then consumes the
+// results strictly in the sequential order (left stepping out, right stepping
+// out, shrinkage) and keeps results it could not consume yet in a small cache.
+// Evaluations the sequential order never reaches are discarded. The trajectory,
+// the evaluation count and every draw are those of the sequential algorithm;
+// the slots only shorten the chain's critical path.
+enum { PH_NEWSTEP = 0, PH_OUT = 1, PH_SHRINK = 2, PH_DONE = 3 };
+enum { KIND_L = 0, KIND_R = 1, KIND_SH = 2 };
+constexpr int CACHE_MAX = 16;
+
+struct Chain {
+    double x, e, lrow[MAXD];
+    double lx, a, b;
+    int s, phase, nl, nr, nsh, caps, left_done, right_done;
+    long long evals;
+    unsigned long long bins;
+    // cache of evaluated, not yet consumed candidates
+    int ncache;
+    int ckind[CACHE_MAX], cidx[CACHE_MAX], cbins[CACHE_MAX];
+    double cval[CACHE_MAX];
+};
+
+__device__ __forceinline__ bool warp_inbox(double y, int lane, int d) {
+    return __all_sync(0xffffffffu, lane >= d || (y >= 0.0 && y <= 1.0));
+}
+
+__device__ __forceinline__ int cache_find(const Chain &c, int kind, int idx) {
+    for (int i = 0; i < c.ncache; i++)
+        if (c.ckind[i] == kind && c.cidx[i] == idx) return i;
+    return -1;
+}
+
+__device__ __forceinline__ void cache_drop(Chain &c, int i) {
+    c.ncache--;
+    c.ckind[i] = c.ckind[c.ncache];
+    c.cidx[i] = c.cidx[c.ncache];
+    c.cval[i] = c.cval[c.ncache];
+    c.cbins[i] = c.cbins[c.ncache];
+}
+
+// Drop every cached result of one stepping-out side (once that side has ended,
+// its later candidates are never consumed).
+__device__ __forceinline__ void cache_purge(Chain &c, int kind) {
+    for (int i = c.ncache - 1; i >= 0; i--)
+        if (c.ckind[i] == kind) cache_drop(c, i);
+}
+
+__device__ __forceinline__ void end_side(Chain &c, bool left) {
+    if (left) { c.left_done = 1; cache_purge(c, KIND_L); }
+    else { c.right_done = 1; cache_purge(c, KIND_R); }
+}
+
+__device__ __forceinline__ double shrink_t(const StepArgs &A, double a, double b, int nsh, int step,
+                                           int chain, uint32_t iter) {
+    const uint4 w = draw(A.seed, SLOT_SHRINK0 + (uint32_t)nsh, (uint32_t)step, (uint32_t)chain, iter);
+    return __dadd_rn(a, __dmul_rn(__dsub_rn(b, a), u01(w.x, w.y)));
+}
+
+// Apply every transition that needs no new evaluation: new steps (direction and
+// bracket draws), cap and prior-box outcomes, and results already in the cache.
+// Returns when the next transition needs an evaluation not in the cache, or the
+// chain is done.
+static __device__ void chain_run(const Model &M, const StepArgs &A, Chain &c, int chain, uint32_t iter,
+                          double lstar) {
+    const int lane = threadIdx.x & 31, d = M.dim;
+    for (int guard = 0; guard < (1 << 22); guard++) {
+        if (c.phase == PH_DONE) return;
+        if (c.phase == PH_NEWSTEP) {
+            if (c.s >= A.steps) { c.phase = PH_DONE; return; }
+            // direction e = L z / |z|, z ~ N(0, I) by Box-Muller, two normals per draw
+            double z = 0.0;
+            if (lane < d) {
+                const uint4 w = draw(A.seed, (uint32_t)(lane >> 1), (uint32_t)c.s, (uint32_t)chain, iter);
+                const double u1 = u01(w.x, w.y), u2 = u01(w.z, w.w);
+                const double r = sqrt(-2.0 * log(u1));
+                double sn, cs;
+                sincos(TWO_PI_D * u2, &sn, &cs);
+                z = (lane & 1) ? r * sn : r * cs;
+            }
+            const double nz = sqrt(warp_sum(z * z));
+            double acc = 0.0;
+            for (int j = 0; j < d; j++) {
+                const double zj = __shfl_sync(0xffffffffu, z, j);
+                if (j <= lane) acc = __dadd_rn(acc, __dmul_rn(c.lrow[j], zj));
+            }
+            c.e = (lane < d) ? acc / nz : 0.0;
+            const uint4 w = draw(A.seed, SLOT_OFFSET, (uint32_t)c.s, (uint32_t)chain, iter);
+            const double r = u01(w.x, w.y);
+            c.a = -r;
+            c.b = 1.0 - r;
+            c.nl = c.nr = c.nsh = 0;
+            c.left_done = c.right_done = 0;
+            c.ncache = 0;
+            c.phase = PH_OUT;
+            continue;
+        }
+        if (c.phase == PH_OUT) {
+            const bool left = !c.left_done;
+            if (!left && c.right_done) { c.phase = PH_SHRINK; continue; }
+            const int n = left ? c.nl : c.nr;
+            if (n >= A.max_stepout) {
+                end_side(c, left);
+                continue;
+            }
+            const double t = left ? c.a : c.b;
+            const double y = (lane < d) ? __dadd_rn(c.x, __dmul_rn(t, c.e)) : 0.5;
+            if (!warp_inbox(y, lane, d)) {
+                end_side(c, left);
+                continue;
+            }
+            const int ci = cache_find(c, left ? KIND_L : KIND_R, n);
+            if (ci < 0) return;
+            const bool in = c.cval[ci] > lstar;
+            c.evals++;
+            c.bins += (unsigned long long)c.cbins[ci];
+            cache_drop(c, ci);
+            if (left) { if (in) { c.a -= 1.0; c.nl++; } else end_side(c, true); }
+            else { if (in) { c.b += 1.0; c.nr++; } else end_side(c, false); }
+            continue;
+        }
+        // PH_SHRINK
+        if (c.nsh >= A.max_shrink) {
+            c.caps++;
+            c.s++;
+            c.phase = PH_NEWSTEP;
+            continue;
+        }
+        const double t = shrink_t(A, c.a, c.b, c.nsh, c.s, chain, iter);
+        const double y = (lane < d) ? __dadd_rn(c.x, __dmul_rn(t, c.e)) : 0.5;
+        if (warp_inbox(y, lane, d)) {
+            const int ci = cache_find(c, KIND_SH, c.nsh);
+            if (ci < 0) return;
+            const double val = c.cval[ci];
+            c.evals++;
+            c.bins += (unsigned long long)c.cbins[ci];
+            cache_drop(c, ci);
+            if (val > lstar) {
+                c.x = y;
+                c.lx = val;
+                c.s++;
+                c.phase = PH_NEWSTEP;
+                continue;
+            }
+        }
+        if (t < 0.0) c.a = t; else c.b = t;
+        c.nsh++;
+    }
+    c.phase = PH_DONE;   // unreachable with finite caps; keeps the loop bounded
+}
+
+// Plan up to S candidates to evaluate in the next round (in-box, not cached),
+// continuing the current stage's sequences. Writes their coordinates to
+// ysh[slot][*] and their keys to pk/pi; returns the number of slots used.
+template <int S>
+__device__ int chain_plan(const Model &M, const StepArgs &A, const Chain &c, int chain, uint32_t iter,
+                          double (*ysh)[MAXD], int *pk, int *pidx, int depth) {
+    const int lane = threadIdx.x & 31, d = M.dim;
+    int ns = 0;
+    const int room = CACHE_MAX - c.ncache;
+    const int lim = depth < S ? depth : S;
+    const int cap = lim < room ? lim : room;
+    if (c.phase == PH_OUT) {
+        // the side in progress first (half the slots if the other side is
+        // still open), then the other side; each looks at most S candidates
+        // ahead of its consumed position, so the cache holds at most 2S entries
+        for (int side = 0; side < 2 && ns < cap; side++) {
+            const bool left = (side == 0);
+            if (left ? c.left_done : c.right_done) continue;
+            const int limit = (left && !c.right_done) ? (cap + 1) / 2 : cap;
+            double t = left ? c.a : c.b;
+            const int n0 = left ? c.nl : c.nr;
+            for (int n = n0; n < n0 + S && n < A.max_stepout && ns < limit; n++) {
+                const double y = (lane < d) ? __dadd_rn(c.x, __dmul_rn(t, c.e)) : 0.5;
+                if (!warp_inbox(y, lane, d)) break;
+                if (cache_find(c, left ? KIND_L : KIND_R, n) < 0) {
+                    if (lane < d) ysh[ns][lane] = y;
+                    pk[ns] = left ? KIND_L : KIND_R;
+                    pidx[ns] = n;
+                    ns++;
+                }
+                if (left) t -= 1.0; else t += 1.0;
+            }
+        }
+    } else if (c.phase == PH_SHRINK) {
+        double a = c.a, b = c.b;
+        for (int n = c.nsh; n < c.nsh + S && n < A.max_shrink && ns < cap; n++) {
+            const double t = shrink_t(A, a, b, n, c.s, chain, iter);
+            const double y = (lane < d) ? __dadd_rn(c.x, __dmul_rn(t, c.e)) : 0.5;
+            if (warp_inbox(y, lane, d) && cache_find(c, KIND_SH, n) < 0) {
+                if (lane < d) ysh[ns][lane] = y;
+                pk[ns] = KIND_SH;
+                pidx[ns] = n;
+                ns++;
+            }
+            if (t < 0.0) a = t; else b = t;     // as if rejected
+        }
+    }
+    return ns;
+}
+
+template <int PREC, int NDET, int S>
+__device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, const int chain) {
+    __shared__ Coef coef[S];
+    __shared__ CoefMixed cm[S];
+    __shared__ double ysh[S][MAXD];
+    __shared__ double lval[S];
+    __shared__ int nslot;
+    __shared__ int jc[S];
+    __shared__ double part[S][S][NDET][2];
+    if (chain >= A.k) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, d = M.dim;
+    const uint32_t iter = (uint32_t)A.state->iter;
+    const double lstar = A.state->lstar;
+    Chain c;
+    int pk[S], pidx[S];
+    if (warp == 0) {
+        const int m = A.n - A.k;
+        const uint4 w = draw(A.seed, 0u, STEP_START, (uint32_t)chain, iter);
+        int idx = (int)(u01(w.x, w.y) * m);
+        if (idx >= m) idx = m - 1;
+        const int src = A.order[A.k + idx];
+        c.x = (lane < d) ? A.live_u[(size_t)src * d + lane] : 0.0;
+        c.lx = A.live_logl[src];
+        for (int j = 0; j < MAXD; j++) c.lrow[j] = (lane < d && j < d) ? A.chol[lane * d + j] : 0.0;
+        c.e = 0.0; c.a = 0.0; c.b = 0.0;
+        c.s = 0; c.phase = PH_NEWSTEP; c.nl = c.nr = c.nsh = 0; c.caps = 0; c.evals = 0; c.bins = 0;
+        c.left_done = c.right_done = 0; c.ncache = 0;
+    }
+    for (;;) {
+        if (warp == 0) {
+            chain_run(M, A, c, chain, iter, lstar);
+            // plan the base depth while many chains run; the stragglers of the
+            // update (fewer running chains than the tail threshold) use every warp
+            int depth = S;
+            if (A.active) {
+                const int running = *((volatile int *)A.active);
+                if (running > A.tail) depth = A.depth;
+            }
+            int ns = (c.phase == PH_DONE) ? 0 : chain_plan<S>(M, A, c, chain, iter, ysh, pk, pidx, depth);
+            if (ns == 0 && c.phase != PH_DONE) {
+                // cannot happen with the bounds above; end the chain at its
+                // current (in-slice) point and flag the run state
+                c.phase = PH_DONE;
+                if (lane == 0) atomicOr(&A.state->status, 1);
+            }
+            if (lane == 0) nslot = ns;
+        }
+        __syncthreads();
+        const int ns = nslot;
+        if (ns == 0) break;
+        // coefficients: warp w computes candidates 4w .. 4w+3 (8 lanes each)
+        if (M.model == M_TOY) {
+            if (warp < ns) point_coef_warp(M, T, ysh[warp], &coef[warp]);
+        } else if (4 * warp < ns) {
+            const int cnt = ns - 4 * warp < 4 ? ns - 4 * warp : 4;
+            point_coef_group(M, T, ysh[4 * warp], MAXD, &coef[4 * warp], cnt, PREC == 0 ? 32 : 0);
+        }
+        __syncthreads();
+        if (warp < ns && M.rb) {
+            // relative-binning likelihood of the slot's candidate
+            if (PREC == 1) {
+                coef_to_mixed_warp(coef[warp], M.n_det, &cm[warp], T.rb.fid);
+                __syncwarp();
+            }
+            const double v = rb_loglike_warp<NDET, PREC>(M, T.rb, coef[warp], cm[warp], lane);
+            if (lane == 0) {
+                lval[warp] = v;
+                coef[warp].jcut = T.rb.nb - 1;     // bins counted for the work statistics
+            }
+        } else if (PREC == 1 && S > 1 && S <= 4 && M.model == M_GW && !M.rb && M.coop) {
+            // mixed: all warps stride the bins for all candidates of the round
+            if (warp < ns) coef_to_mixed_warp(coef[warp], M.n_det, &cm[warp]);
+            if (lane == 0 && warp < ns) jc[warp] = coef[warp].jcut;
+            __syncthreads();
+            float zrh[S][NDET], zrl[S][NDET], zih[S][NDET], zil[S][NDET];
+            bins_mixed_multi<NDET, S>(T, M.N, cm, jc, ns, threadIdx.x, S * 32, zrh, zrl, zih, zil);
+#pragma unroll
+            for (int sc = 0; sc < S; sc++)
+#pragma unroll
+                for (int dd = 0; dd < NDET; dd++) {
+                    warp_sum_df(zrh[sc][dd], zrl[sc][dd]);
+                    warp_sum_df(zih[sc][dd], zil[sc][dd]);
+                    if (lane == 0) {
+                        part[warp][sc][dd][0] = (double)zrh[sc][dd] + (double)zrl[sc][dd];
+                        part[warp][sc][dd][1] = (double)zih[sc][dd] + (double)zil[sc][dd];
+                    }
+                }
+            __syncthreads();
+            if (warp == 0) {
+                // lane = (candidate, detector): sum over warps, then log L per candidate
+                double v = 0.0;
+                const int sc = lane / NDET, dd = lane % NDET;
+                if (sc < ns && lane < S * NDET) {
+                    double ZR = 0.0, ZI = 0.0;
+                    for (int w2 = 0; w2 < S; w2++) { ZR += part[w2][sc][dd][0]; ZI += part[w2][sc][dd][1]; }
+                    v = coef[sc].gre[dd] * ZR - coef[sc].gim[dd] * ZI;
+                }
+                for (int sc2 = 0; sc2 < ns; sc2++) {
+                    double t = (lane / NDET == sc2 && lane < S * NDET) ? v : 0.0;
+                    t = warp_sum(t);
+                    if (lane == 0) lval[sc2] = t - 0.5 * coef[sc2].hh;
+                }
+            }
+        } else if (warp < ns) {
+            // one candidate per slot warp: bins and warp reduction
+            if (PREC == 1) {
+                coef_to_mixed_warp(coef[warp], M.n_det, &cm[warp]);
+                __syncwarp();
+            }
+            double zr[NDET], zi[NDET];
+            if (PREC == 0) bins_fp64<NDET, true>(T, M.N, M.f0, M.df, coef[warp], lane, 32, zr, zi);
+            else bins_mixed<NDET>(T, M.N, cm[warp], coef[warp].jcut, lane, 32, zr, zi);
+            double v = 0.0;
+#pragma unroll
+            for (int dd = 0; dd < NDET; dd++) {
+                const double ZR = warp_sum(zr[dd]), ZI = warp_sum(zi[dd]);
+                v += coef[warp].gre[dd] * ZR - coef[warp].gim[dd] * ZI;
+            }
+            if (lane == 0) lval[warp] = (M.model == M_TOY) ? coef[warp].toy : v - 0.5 * coef[warp].hh;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            for (int sl = 0; sl < ns; sl++) {
+                c.ckind[c.ncache] = pk[sl];
+                c.cidx[c.ncache] = pidx[sl];
+                c.cval[c.ncache] = lval[sl];
+                c.cbins[c.ncache] = coef[sl].jcut + 1;
+                c.ncache++;
+            }
+        }
+        // coef/lval are rewritten only after the next barrier's plan
+    }
+    if (warp == 0) {
+        const int dst = A.order[chain];
+        if (lane < d) A.live_u[(size_t)dst * d + lane] = c.x;
+        if (lane == 0) {
+            A.live_logl[dst] = c.lx;
+            if (A.active) atomicSub(A.active, 1);
+            atomicAdd(&A.state->evals, (unsigned long long)c.evals);
+            atomicAdd(&A.state->caps, (unsigned long long)c.caps);
+            atomicAdd(&A.state->point_bins, c.bins);
+        }
+    }
+}
+
+template <int PREC, int NDET, int S>
+__global__ void __launch_bounds__(S * 32) k_slice(Model M, Tables T, StepArgs A) {
+    slice_body<PREC, NDET, S>(M, T, A, blockIdx.x);
+}
+
+template <int PREC, int NDET>
+cudaError_t slice_launch(const Model &M, const Tables &T, int slots, const StepArgs &A, cudaStream_t s) {
+    switch (slots) {
+        case 1: k_slice<PREC, NDET, 1><<<A.k, 32, 0, s>>>(M, T, A); break;
+        case 2: k_slice<PREC, NDET, 2><<<A.k, 64, 0, s>>>(M, T, A); break;
+        case 4: k_slice<PREC, NDET, 4><<<A.k, 128, 0, s>>>(M, T, A); break;
+        default: k_slice<PREC, NDET, 8><<<A.k, 256, 0, s>>>(M, T, A); break;
+    }
+    return cudaGetLastError();
+}
+
+template <int PREC, int NDET, int S>
+__global__ void __launch_bounds__(S * 32) k_slice_multi(const Desc *D, const int2 *map) {
+    __shared__ Desc d;
+    const int2 ac = map[blockIdx.x];
+    load_desc(D + ac.x, d);
+    slice_body<PREC, NDET, S>(d.M, d.T, d.A, ac.y);
+}
+
+template <int PREC, int NDET>
+cudaError_t slice_multi_launch(const Desc *D, const int2 *map, int nblocks, int slots, cudaStream_t s) {
+    switch (slots) {
+        case 1: k_slice_multi<PREC, NDET, 1><<<nblocks, 32, 0, s>>>(D, map); break;
+        case 2: k_slice_multi<PREC, NDET, 2><<<nblocks, 64, 0, s>>>(D, map); break;
+        case 4: k_slice_multi<PREC, NDET, 4><<<nblocks, 128, 0, s>>>(D, map); break;
+        default: k_slice_multi<PREC, NDET, 8><<<nblocks, 256, 0, s>>>(D, map); break;
+    }
+    return cudaGetLastError();
+}
+
+// Explicit instantiation of the launchers of one (precision, detectors) pair.
+#define GWNS_INSTANTIATE(P, D)                                                                       \
+    template cudaError_t eval_launch<P, D>(const Model &, const Tables &, int, const double *, int, int, \
+                                           double *, cudaStream_t);                                 \
+    template cudaError_t slice_launch<P, D>(const Model &, const Tables &, int, const StepArgs &,     \
+                                            cudaStream_t);                                          \
+    template cudaError_t slice_multi_launch<P, D>(const Desc *, const int2 *, int, int, cudaStream_t);
+
+}  // namespace gwns
