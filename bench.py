@@ -451,6 +451,160 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+FP32_LANE_OPS = 152 * 128 * 2.070e9    # FP32 pipe: 128 lanes/clk/SM x 152 SMs x 2070 MHz
+
+
+def mixed_fp32_per_point_bin(n_det: int, tile: int) -> float:
+    """FP32 instructions of the mixed form per point-bin (per-tile or per-flush
+    work not counted). Tiled form (tile > 0): C_1 x as an error-free product
+    (3), the Horner sum of C_2..C_6 (5), the reduction of C_1 x (2), x^2 (1);
+    per detector 4 (phase) + 2 (reduction) + 1 (scale) + 4 (complex MAC), the
+    sine/cosine pair on the MUFU pipe. Per-bin form: the double-float dot
+    product of 8 basis terms (12 each) and per detector the double-float delay
+    term, reduction and MAC (20)."""
+    if tile:
+        return 11.0 + 11.0 * n_det
+    return 96.0 + 20.0 * n_det
+
+
+def _timed_steps(sp, stream, max_steps):
+    """ns_step until done (or max_steps), each bracketed by CUDA events on the
+    library's stream; returns (per-step ms, iterations, done)."""
+    import torch
+    ms, done, it = [], False, 0
+    while not done and it < max_steps:
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        done = sp.step()
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+        it += 1
+    return ms, it, done
+
+
+def _rb_analysis(g, w, precision, stream, coarse_bins=1024):
+    """The workload's data on the full grid, sampled on coarse relative-binning
+    bins about the injection (the fiducial point)."""
+    probe, th = g.make_analysis(w, precision=g.NS_FP64, n_live=2, k=1, stream=stream.cuda_stream)
+    data = probe.waveform(th)
+    probe.close()
+    if w.noise:
+        data = data + gi.noise(w.seed_noise, np.tile(gi.psd_analytic(w.freqs()), (w.n_det, 1)), w.df)
+    return g.sampler_for_workload(w, data=data, precision=precision, coarse_bins=coarse_bins, theta_fid=th,
+                                  stream=stream.cuda_stream), th
+
+
+def table_row(g, name, precision, stream, max_steps=100000, coarse=False):
+    import torch
+    w = gi.workload(name)
+    t0 = time.perf_counter()
+    if coarse:
+        sp, th = _rb_analysis(g, w, precision, stream)
+    else:
+        sp, th = g.make_analysis(w, precision=precision, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    st0 = sp.stats()
+    t1 = time.perf_counter()
+    ms, it, done = _timed_steps(sp, stream, max_steps)
+    r = sp.result(samples=False) if done else None
+    t2 = time.perf_counter()
+    st1 = sp.stats()
+    sp.close()
+    ev = st1["evals"] - st0["evals"]
+    pb = st1["point_bins"] - st0["point_bins"]
+    slice_ms = st1["kernel_ms"][3] - st0["kernel_ms"][3]
+    if precision == g.NS_FP64:
+        frac = pb * fp64_flops_per_point_bin(w.n_det) / (slice_ms / 1e3) / (FP64_PEAK_TFLOPS * 1e12)
+        pipe = "FP64"
+    else:
+        frac = pb * mixed_fp32_per_point_bin(w.n_det, st1["mixed_tile"]) / (slice_ms / 1e3) / FP32_LANE_OPS
+        pipe = "FP32"
+    return {"config": name + (" (1024 coarse bins)" if coarse else ""),
+            "form": "fp64" if precision == g.NS_FP64 else "mixed", "iterations": it, "done": done,
+            "evals": ev, "evals_per_s": ev / (sum(ms) / 1e3), "point_bins_per_s": pb / (sum(ms) / 1e3),
+            "bins_per_eval": pb / max(ev, 1), "k_slice_frac": frac, "k_slice_pipe": pipe,
+            "mixed_tile": st1["mixed_tile"] if precision != g.NS_FP64 else None,
+            "time_to_logZ_s": (t2 - t1) if done else None, "setup_s": setup_s,
+            "p50_step_ms": float(np.percentile(ms, 50)), "p99_step_ms": float(np.percentile(ms, 99)),
+            "logZ": r["logZ"] if r else None, "dlogZ": r["dlogZ"] if r else None}
+
+
+def batch_eval_row(g, name, precision, stream, points=2048):
+    """Batched likelihood throughput (ns_eval_lnl on prior draws)."""
+    import torch
+    w = gi.workload(name)
+    sp, th = g.make_analysis(w, precision=precision, n_live=8, k=4, stream=stream.cuda_stream)
+    u = torch.tensor(gi.unit_cube(99, points, w.dim), dtype=torch.float64, device="cuda")
+    sp.eval_lnl(u)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sp.eval_lnl(u)
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    sp.close()
+    return {"config": name, "form": "fp64" if precision == g.NS_FP64 else "mixed", "batch_points": points,
+            "batch_evals_per_s": points / t}
+
+
+def oracle_rate(name: str, chains: int, steps_per_dim: int, target_s: float):
+    """Oracle evaluations per second inside slice-sampling chains of a
+    workload's first iteration (plain FP64 C, OpenMP over chains)."""
+    import oracle
+    from oracle import ns as ons
+    w = gi.workload(name)
+    pb, th = oracle.make_problem(w)
+    st0 = ons.initial_state(pb, w.n_live, w.seed_sampler)
+    order = np.argsort(st0.live_logl, kind="stable")
+    k, d = w.k, pb.dim
+    surv = np.ascontiguousarray(st0.live_u[order[k:]])
+    surv_l = np.ascontiguousarray(st0.live_logl[order[k:]])
+    chol = np.ascontiguousarray(ons.survivor_cholesky(surv))
+    lstar = float(st0.live_logl[order[k - 1]])
+    nt = oracle.max_threads()
+    tot_ev, tot_s, rep = 0, 0.0, 0
+    while tot_s < target_s:
+        new_u, new_l = np.zeros((chains, d)), np.zeros(chains)
+        caps = np.zeros(1, dtype=np.int32)
+        t0 = time.perf_counter()
+        ev = oracle.lib().or_evolve(pb.c, nt, w.seed_sampler, rep, chains, oracle._ptr(surv), oracle._ptr(surv_l),
+                                    w.n_live - k, oracle._ptr(chol), lstar, steps_per_dim * d, 64, 64,
+                                    oracle._ptr(new_u), oracle._ptr(new_l), oracle._ptr(caps))
+        tot_s += time.perf_counter() - t0
+        tot_ev += ev
+        rep += 1
+    return {"config": name, "form": "oracle", "evals_per_s": tot_ev / tot_s, "cores": nt,
+            "sample": f"{rep} x {chains} chains of {steps_per_dim * d} slice steps from the first iteration "
+                      f"({tot_ev} evaluations, {tot_s:.1f} s)"}
+
+
+def run_table(args):
+    """One JSON line per (workload, form): full runs of c0, c1, c2 and c4 on
+    1024 coarse bins (FP64 and mixed), c4 on the full grid (mixed: 2 iterations;
+    FP64: batched likelihood), and the oracle's rate per workload."""
+    import torch
+    import paper_2509_24949_gb300 as g
+    from paper_2509_24949_gb300 import _build
+    if not _build.up_to_date():
+        _build.build()
+    stream = torch.cuda.Stream()
+    rows = []
+    for name in ("c0", "c1", "c2"):
+        for prec in (g.NS_FP64, g.NS_MIXED):
+            rows.append(table_row(g, name, prec, stream))
+    for prec in (g.NS_FP64, g.NS_MIXED):
+        rows.append(table_row(g, "c4", prec, stream, coarse=True))
+    rows.append(table_row(g, "c4", g.NS_MIXED, stream, max_steps=2))
+    rows.append(batch_eval_row(g, "c4", g.NS_FP64, stream))
+    rows.append(batch_eval_row(g, "c4", g.NS_MIXED, stream))
+    if not args.no_oracle:
+        for name, chains, spd in (("c0", 64, 5), ("c1", 64, 5), ("c2", 32, 2), ("c4", 16, 1)):
+            rows.append(oracle_rate(name, chains, spd, 8.0))
+    for r in rows:
+        print(json.dumps(r), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -461,9 +615,16 @@ def main():
                     help="measure the timed steps and e2e only, without the time-to-logZ, serving, "
                          "agreement and CPU-baseline reports (for profiler runs); the timed region "
                          "is the same")
+    ap.add_argument("--table", action="store_true",
+                    help="per-workload table (full runs of c0-c2 and c4 on coarse bins, c4 full grid, "
+                         "oracle rates): one JSON line each")
+    ap.add_argument("--no-oracle", action="store_true", help="with --table: skip the oracle rates")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.table:
+        run_table(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -204,6 +204,8 @@ typedef struct {
     double kernel_ms[5];    /* cumulative device time of the iteration's kernels, from CUDA
                                events recorded on the context's stream inside the iteration's
                                graph: select, evidence, covariance, slice update, finish */
+    int mixed_tile;         /* mixed precision: bins per lane tile of the tiled form (grids fine
+                               enough for its Taylor expansion), 0 for the per-bin form */
 } ns_stats;
 
 int ns_get_stats(ns_ctx *ctx, ns_stats *st);

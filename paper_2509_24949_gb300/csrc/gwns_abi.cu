@@ -287,8 +287,8 @@ void ns_free(ns_ctx *c) {
     if (c->graph) cudaGraphExecDestroy(c->graph);
     for (cudaEvent_t e : c->ev)
         if (e) cudaEventDestroy(e);
-    void *bufs[] = {c->d_re, c->d_im, c->d_psd, c->basis64, c->f64, c->prefix, c->w64, c->basis32,
-                    c->f32, c->w32, c->live_u, c->live_logl, c->order, c->chol, c->dead_u,
+    void *bufs[] = {c->d_re, c->d_im, c->d_psd, c->basis64, c->f64, c->prefix, c->w64, c->X.basis32,
+                    c->X.f32, c->X.w32, c->X.tb0, c->X.tb1, c->X.tbk, c->X.fc, c->X.wt, c->live_u, c->live_logl, c->order, c->chol, c->dead_u,
                     c->dead_logl, c->dead_logw, c->dead_nlive, c->state, c->scratch, c->fin_u,
                     c->fin_logl, c->fin_logw, c->fin_nlive, c->res, c->rb_J, c->rb_nedge, c->rb_fid,
                     c->rb_fe, c->rb_basis64, c->rb_basis32, c->rb_fe32, c->rb_fm, c->rb_inv_de, c->rb_A0,
@@ -344,6 +344,49 @@ static int validate(const ns_prior *prior, const ns_data *data, const ns_psd *ps
     const size_t nn = (size_t)data->n_det * grid->N;
     for (size_t i = 0; i < nn; i++)
         if (!(psd->S[i] > 0.0) || !is_fin(psd->S[i])) return NS_ERR_PSD_NONPOS;
+    return NS_OK;
+}
+
+// Mixed form: the tiled form when the Taylor remainder of the basis about each
+// tile's centre stays below 1e-8 rad for every point of the prior, else the
+// per-bin form. The bound: the basis terms of the phase sum to at most twice
+// the Newtonian phase 3/128 (pi T_sun Mc f)^(-5/3) at the lowest chirp mass and
+// frequency (leading-order and 1.5PN terms dominate at f0); the degree-TK
+// remainder of f^(-5/3) over half a tile h is below 4.4 (h/f0)^(TK+1) times the
+// term; a factor 64 covers both with margin. The longest tile that passes is
+// taken (it amortises the per-tile anchor best).
+static void choose_tiles(Model &M) {
+    M.tlg = 0;
+    M.np = M.N;
+    const double mc = M.lo[P_MC] > 0.0 ? M.lo[P_MC] : 1.0;
+    const double phin = 3.0 / 128.0 * std::pow(M_PI * TSUN * mc * M.f0, -5.0 / 3.0);
+    for (int lg = 6; lg >= 3; lg--) {
+        const double h = 0.5 * (double)(1 << lg) * M.df;
+        if (64.0 * phin * std::pow(h / M.f0, TK + 1) <= 1e-8) {
+            M.tlg = lg;
+            const int gb = 32 << lg;
+            M.np = (M.N + gb - 1) / gb * gb;
+            return;
+        }
+    }
+}
+
+static int alloc_mixed(ns_ctx *c) {
+    const Model &M = c->M;
+    const size_t N = M.N, nd = M.n_det;
+    if (M.model != M_GW) return NS_OK;
+    if (!M.tlg) {
+        int rc;
+        if ((rc = dalloc(&c->X.basis32, NB * N)) || (rc = dalloc(&c->X.f32, N)) || (rc = dalloc(&c->X.w32, nd * N)))
+            return rc;
+        return NS_OK;
+    }
+    const size_t np = M.np, nt = np >> M.tlg;
+    int rc;
+    if ((rc = dalloc(&c->X.tb0, NB * nt)) || (rc = dalloc(&c->X.tb1, NB * nt)) ||
+        (rc = dalloc(&c->X.tbk, (size_t)(TK - 1) * NB * nt)) || (rc = dalloc(&c->X.fc, nt)) ||
+        (rc = dalloc(&c->X.wt, nd * np)))
+        return rc;
     return NS_OK;
 }
 
@@ -407,6 +450,7 @@ int ns_init(ns_ctx **out, const ns_prior *prior, const ns_data *data, const ns_p
         // large grids: the mixed slice update shares each bin's table loads among
         // the round's candidates (measured faster from ~16k bins on GB300)
         M.coop = M.N >= 16384 ? 1 : 0;
+        choose_tiles(M);
         if (!data->ideal)
             for (int dd = 0; dd < M.n_det; dd++)
                 for (int i = 0; i < 3; i++) {
@@ -420,8 +464,7 @@ int ns_init(ns_ctx **out, const ns_prior *prior, const ns_data *data, const ns_p
     const size_t N = M.N, nd = M.n_det, nn = nd * N;
     if ((rc = dalloc(&c->d_re, nn)) || (rc = dalloc(&c->d_im, nn)) || (rc = dalloc(&c->d_psd, nn)) ||
         (rc = dalloc(&c->basis64, NB * N)) || (rc = dalloc(&c->f64, N)) || (rc = dalloc(&c->prefix, nn)) ||
-        (rc = dalloc(&c->w64, nn)) || (rc = dalloc(&c->basis32, NB * N)) || (rc = dalloc(&c->f32, N)) ||
-        (rc = dalloc(&c->w32, nn)) || (rc = dalloc(&c->live_u, (size_t)c->n * c->d)) ||
+        (rc = dalloc(&c->w64, nn)) || (rc = alloc_mixed(c)) || (rc = dalloc(&c->live_u, (size_t)c->n * c->d)) ||
         (rc = dalloc(&c->live_logl, c->n)) || (rc = dalloc(&c->order, c->n)) ||
         (rc = dalloc(&c->chol, (size_t)NS_MAX_DIM * NS_MAX_DIM)) || (rc = dalloc(&c->state, 1)) ||
         (rc = dalloc(&c->fin_u, (size_t)c->n * c->d)) || (rc = dalloc(&c->fin_logl, c->n)) ||
@@ -448,7 +491,7 @@ int ns_init(ns_ctx **out, const ns_prior *prior, const ns_data *data, const ns_p
         }
         if (e == cudaSuccess)
             e = launch_build_tables(M, c->d_re, c->d_im, c->d_psd, c->basis64, c->f64, c->w64, c->prefix,
-                                    c->basis32, c->f32, c->w32, c->stream);
+                                    c->X, c->stream);
     }
     if (e != cudaSuccess) { ns_free(c); return cuda_fail(e); }
     if (M.model == M_GW && grid->coarse_bins > 0) {
@@ -459,9 +502,14 @@ int ns_init(ns_ctx **out, const ns_prior *prior, const ns_data *data, const ns_p
     c->T.f64 = c->f64;
     c->T.w64 = c->w64;
     c->T.prefix = c->prefix;
-    c->T.basis32 = c->basis32;
-    c->T.f32 = c->f32;
-    c->T.w32 = c->w32;
+    c->T.basis32 = c->X.basis32;
+    c->T.f32 = c->X.f32;
+    c->T.w32 = c->X.w32;
+    c->T.tb0 = c->X.tb0;
+    c->T.tb1 = c->X.tb1;
+    c->T.tbk = c->X.tbk;
+    c->T.fc = c->X.fc;
+    c->T.wt = c->X.wt;
     if (c->rb_B > 0 && (rc = build_rb(c))) { ns_free(c); return rc; }
     RunState s0;
     std::memset(&s0, 0, sizeof(s0));
@@ -484,8 +532,8 @@ int ns_set_data(ns_ctx *c, const double *re, const double *im) {
     const size_t nn = (size_t)c->M.n_det * c->M.N;
     CK(cudaMemcpyAsync(c->d_re, re, nn * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->d_im, im, nn * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    CK(launch_build_tables(c->M, c->d_re, c->d_im, c->d_psd, c->basis64, c->f64, c->w64, c->prefix,
-                           c->basis32, c->f32, c->w32, c->stream));
+    CK(launch_build_tables(c->M, c->d_re, c->d_im, c->d_psd, c->basis64, c->f64, c->w64, c->prefix, c->X,
+                           c->stream));
     int rc;
     if (c->rb_B > 0 && (rc = build_rb(c))) return rc;
     rc = eval_points(c, c->live_u, 0, c->n, c->live_logl);
@@ -559,6 +607,7 @@ int ns_get_stats(ns_ctx *c, ns_stats *st) {
     st->point_bins = (long long)s.point_bins;
     st->status = s.status;
     for (int i = 0; i < 5; i++) st->kernel_ms[i] = c->timing ? c->kernel_ms[i] : -1.0;
+    st->mixed_tile = c->M.tlg ? 1 << c->M.tlg : 0;
     return NS_OK;
 }
 

@@ -9,6 +9,7 @@
 
 using gwns::Coef;
 using gwns::Desc;
+using gwns::MixedTables;
 using gwns::Model;
 using gwns::RBTables;
 using gwns::RunState;
@@ -29,7 +30,7 @@ struct ns_ctx {
     double *d_re = nullptr, *d_im = nullptr, *d_psd = nullptr;
     double *basis64 = nullptr, *f64 = nullptr, *prefix = nullptr;
     double2 *w64 = nullptr;
-    float2 *basis32 = nullptr, *f32 = nullptr, *w32 = nullptr;
+    MixedTables X = {};   // mixed-form tables (per-bin or tiled)
     double *live_u = nullptr, *live_logl = nullptr;
     int *order = nullptr;
     int *active = nullptr;           // running-chain counter of the slice update

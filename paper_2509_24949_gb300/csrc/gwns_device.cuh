@@ -41,7 +41,9 @@ struct Model {
     int model;        // M_GW or M_TOY
     int n_det, N, ideal, cutoff, dim;
     int rb;           // 1: relative-binning likelihood on the coarse bins
-    int coop;         // 1: mixed slice update strides bins with all warps for all candidates
+    int coop;         // 1: mixed slice update spreads each candidate's tile groups over all warps
+    int tlg;          // mixed form: 0 per bin, else log2 of the bins per lane tile (tiled form)
+    int np;           // tiled form: N padded to whole groups of 32 tiles
     double f0, df;
     int kind[NPARAM];
     double lo[NPARAM], hi[NPARAM];
@@ -75,9 +77,17 @@ struct Tables {
     const double *f64;       // [N]       f_j
     const double2 *w64;      // [n_det][N] weighted data
     const double *prefix;    // [n_det][N] P_d(j)
+    // mixed form, per bin (Model::tlg == 0)
     const float2 *basis32;   // [NB][N]   B_m(f_j) as (hi, lo) floats
     const float2 *f32;       // [N]       f_j as (hi, lo)
     const float2 *w32;       // [n_det][N]
+    // mixed form, tiled (Model::tlg > 0): tile t = bins tL .. tL + L - 1 about
+    // its centre c = tL + L/2, L = 1 << tlg, nt = np / L tiles
+    const float2 *tb0;       // [NB][nt]  B_m(f_c) as (hi, lo)
+    const float2 *tb1;       // [NB][nt]  B_m'(f_c) df as (hi, lo)
+    const float *tbk;        // [TK-1][NB][nt] B_m^(k)(f_c) df^k / k!, k = 2..TK
+    const float2 *fc;        // [nt]      f_c as (hi, lo)
+    const float2 *wt;        // [n_det][np] weighted data, pair-tile order (zero beyond N)
     RBTables rb;             // used when Model::rb is set
 };
 
@@ -100,6 +110,7 @@ struct CoefMixed {
     float ah[NB], al[NB];
     float c0h, c0l;
     float tauh[MAXDET], taul[MAXDET];
+    float dtau[MAXDET];     // df tau_d: phase advance per bin [turns]
 };
 
 // ------------------------------------------------------------------ Philox
@@ -356,13 +367,15 @@ __device__ __forceinline__ void split_df(double x, float &h, float &l) {
 
 // Mixed-precision coefficients (phase in turns), from lane-parallel
 // conversions; with fid, the differences from the fiducial point's.
-__device__ __forceinline__ void coef_to_mixed_warp(const Coef &c, int n_det, CoefMixed *m,
+__device__ __forceinline__ void coef_to_mixed_warp(const Coef &c, int n_det, double df, CoefMixed *m,
                                                    const Coef *fid = nullptr) {
     const int lane = threadIdx.x & 31;
     if (lane < NB) split_df((c.a[lane] - (fid ? fid->a[lane] : 0.0)) * INV_TWO_PI_D, m->ah[lane], m->al[lane]);
     else if (lane == NB) split_df((c.c0 - (fid ? fid->c0 : 0.0)) * INV_TWO_PI_D, m->c0h, m->c0l);
     else if (lane >= 16 && lane < 16 + n_det)
         split_df(c.tau[lane - 16] - (fid ? fid->tau[lane - 16] : 0.0), m->tauh[lane - 16], m->taul[lane - 16]);
+    else if (lane >= 24 && lane < 24 + n_det)
+        m->dtau[lane - 24] = __double2float_rn(df * (c.tau[lane - 24] - (fid ? fid->tau[lane - 24] : 0.0)));
 }
 
 // ------------------------------------------------------------ bin loops
@@ -475,10 +488,11 @@ __device__ __forceinline__ void bins_fp64(const Tables &T, int N, double f0, dou
     }
 }
 
-// Mixed: the phase in turns accumulated as a double-float dot product
-// (error-free FP32 products via FMA, TwoSum accumulation), reduced mod 1,
-// then FP32 __sincosf and FP32 products. Partial sums are flushed every
-// FLUSH bins into double-float accumulators (compensated summation).
+// Mixed form, per bin (grids too coarse for the tiled form below): the phase
+// in turns accumulated as a double-float dot product (error-free FP32 products
+// via FMA, TwoSum accumulation), reduced mod 1, then FP32 __sincosf and FP32
+// products. Partial sums are flushed every FLUSH bins into double-float
+// accumulators (compensated summation).
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
     s = a + b;
     float bb = s - a;
@@ -640,6 +654,154 @@ __device__ __forceinline__ double warp_max(double v) {
     return v;
 }
 
+// Mixed form, tiled (fine grids). Lane l of a warp owns tile t = 32 g + l of
+// group g, the L bins j = tL + i about the centre c = tL + L/2 (x = i - L/2).
+// The phase in turns of bin j at detector d is
+//   [c0 + sum_m a_m B_m(f_c) + f_c tau_d] + sum_{k=1..TK} C_k x^k + x df tau_d,
+// C_k = sum_m a_m B_m^(k)(f_c) df^k / k!: the Taylor expansion of each basis
+// function about the tile centre, its remainder bounded on the host below 1e-8
+// rad when the tiled form is chosen. Per lane and tile, the anchor in brackets
+// and C_1 are double-float dot products (error-free FP32 products via FMA,
+// TwoSum), C_2..C_TK plain FP32 (they contribute below 0.1 turn); per bin, C_1 x
+// is an error-free FP32 product reduced mod 1, the rest a short Horner sum,
+// then FP32 __sincosf and complex MACs, flushed once per tile into double-float
+// accumulators. The only per-bin table is the weighted data.
+constexpr int TK = 6;
+
+// Position of bin j in the pair-tile order of the weighted data: at step i of
+// a tile, lanes read consecutive float4s (bins i, i + 1 of their tiles).
+__device__ __forceinline__ int tile_pos2(int j, int lg) {
+    const int t = j >> lg, i = j & ((1 << lg) - 1);
+    return ((t >> 5) << (lg + 5)) + ((i >> 1) << 6) + ((t & 31) << 1) + (i & 1);
+}
+
+// One warp's double-float sums over tile groups g0, g0 + gstride, ... for nc <= NC
+// candidates (coefficients cm[c], last bins jcut[c]) sharing the table loads:
+// zh/zl[c][d][0/1] = real/imaginary part of sum_j w_dj exp(2 pi i phase_dj),
+// not yet reduced over the warp.
+template <int NDET, int NC>
+__device__ __forceinline__ void tile_bins(const Tables &T, int lg, int np, const CoefMixed *cm,
+                                          const int *jcut, int nc, int g0, int gstride,
+                                          float zh[NC][NDET][2], float zl[NC][NDET][2]) {
+    const int lane = threadIdx.x & 31;
+    const int L = 1 << lg, half = L >> 1, nt = np >> lg;
+#pragma unroll
+    for (int c = 0; c < NC; c++)
+#pragma unroll
+        for (int d = 0; d < NDET; d++) zh[c][d][0] = zh[c][d][1] = zl[c][d][0] = zl[c][d][1] = 0.f;
+    int jmax = -1;
+#pragma unroll
+    for (int c = 0; c < NC; c++)
+        if (c < nc) jmax = max(jmax, jcut[c]);
+    const int ngroups = jmax < 0 ? 0 : (jmax >> (lg + 5)) + 1;
+    const float4 *wt4 = reinterpret_cast<const float4 *>(T.wt);
+    for (int g = g0; g < ngroups; g += gstride) {
+        const int t = (g << 5) + lane, s = t << lg;
+        int cnt[NC];
+        int nmax = 0;
+        float c1h[NC], c1l[NC], ck[NC][TK - 1], Ah[NC][NDET], Al[NC][NDET];
+        const float2 fc = __ldg(T.fc + t);
+#pragma unroll
+        for (int c = 0; c < NC; c++) {
+            cnt[c] = (c < nc) ? min(max(jcut[c] - s + 1, 0), L) : 0;
+            nmax = max(nmax, (c < nc) ? min(max(jcut[c] - (g << (lg + 5)) + 1, 0), L) : 0);
+            float sh = cm[c].c0h, sl = cm[c].c0l, h1 = 0.f, l1 = 0.f;
+#pragma unroll
+            for (int k = 0; k < TK - 1; k++) ck[c][k] = 0.f;
+#pragma unroll
+            for (int m = 0; m < NB; m++) {
+                const float ah = cm[c].ah[m], al = cm[c].al[m];
+                // anchor term a_m B_m(f_c)
+                const float2 b0 = __ldg(T.tb0 + (size_t)m * nt + t);
+                float p = ah * b0.x;
+                float e = fmaf(ah, b0.x, -p);
+                e = fmaf(ah, b0.y, e);
+                e = fmaf(al, b0.x, e);
+                float s2, e2;
+                two_sum(sh, p, s2, e2);
+                sh = s2;
+                sl += e2 + e;
+                // first-order term a_m B_m'(f_c) df
+                const float2 b1 = __ldg(T.tb1 + (size_t)m * nt + t);
+                p = ah * b1.x;
+                e = fmaf(ah, b1.x, -p);
+                e = fmaf(ah, b1.y, e);
+                e = fmaf(al, b1.x, e);
+                two_sum(h1, p, s2, e2);
+                h1 = s2;
+                l1 += e2 + e;
+#pragma unroll
+                for (int k = 0; k < TK - 1; k++)
+                    ck[c][k] = fmaf(ah, __ldg(T.tbk + ((size_t)k * NB + m) * nt + t), ck[c][k]);
+            }
+            c1h[c] = h1 + l1;
+            c1l[c] = l1 - (c1h[c] - h1);
+            sh -= rintf(sh);
+#pragma unroll
+            for (int d = 0; d < NDET; d++) {
+                const float th = cm[c].tauh[d], tl = cm[c].taul[d];
+                const float p = th * fc.x;
+                float e = fmaf(th, fc.x, -p);
+                e = fmaf(th, fc.y, e);
+                e = fmaf(tl, fc.x, e);
+                float s2, e2;
+                two_sum(sh, p, s2, e2);
+                Ah[c][d] = s2 - rintf(s2);
+                Al[c][d] = sl + (e2 + e);
+            }
+        }
+        float pr[NC][NDET], pim[NC][NDET];
+#pragma unroll
+        for (int c = 0; c < NC; c++)
+#pragma unroll
+            for (int d = 0; d < NDET; d++) pr[c][d] = pim[c][d] = 0.f;
+        const size_t gb = (size_t)g << (lg + 5);
+        for (int q = 0; q < nmax; q += 4) {
+            float4 w[NDET][2];
+#pragma unroll
+            for (int d = 0; d < NDET; d++) {
+                const size_t base = ((size_t)d * np + gb) >> 1;
+                w[d][0] = __ldg(wt4 + base + (q << 4) + lane);
+                w[d][1] = __ldg(wt4 + base + (q << 4) + 32 + lane);
+            }
+#pragma unroll
+            for (int r = 0; r < 4; r++) {
+                const int i = q + r;
+                const float x = (float)(i - half), x2 = x * x;
+#pragma unroll
+                for (int c = 0; c < NC; c++) {
+                    if (i >= cnt[c]) continue;
+                    const float p = c1h[c] * x;
+                    float e = fmaf(c1h[c], x, -p);
+                    e = fmaf(c1l[c], x, e);
+                    float hq = ck[c][TK - 2];
+#pragma unroll
+                    for (int k = TK - 3; k >= 0; k--) hq = fmaf(hq, x, ck[c][k]);
+                    const float sm = fmaf(hq, x2, e);
+                    const float P = p - rintf(p);
+#pragma unroll
+                    for (int d = 0; d < NDET; d++) {
+                        const float y = (P + Ah[c][d]) + (sm + fmaf(x, cm[c].dtau[d], Al[c][d]));
+                        const float red = y - rintf(y);
+                        float sv, cv;
+                        __sincosf(red * 6.283185307179586f, &sv, &cv);
+                        const float4 ww = w[d][r >> 1];
+                        const float wr = (r & 1) ? ww.z : ww.x, wi = (r & 1) ? ww.w : ww.y;
+                        pr[c][d] = fmaf(wr, cv, fmaf(-wi, sv, pr[c][d]));
+                        pim[c][d] = fmaf(wr, sv, fmaf(wi, cv, pim[c][d]));
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < NC; c++)
+#pragma unroll
+            for (int d = 0; d < NDET; d++) {
+                df_acc(zh[c][d][0], zl[c][d][0], pr[c][d]);
+                df_acc(zh[c][d][1], zl[c][d][1], pim[c][d]);
+            }
+    }
+}
 // Double-float warp sum (TwoSum of the high parts, low parts added).
 __device__ __forceinline__ void warp_sum_df(float &h, float &l) {
 #pragma unroll

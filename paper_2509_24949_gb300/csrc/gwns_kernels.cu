@@ -66,47 +66,112 @@ __device__ double block_max(double v, double *scratch) {
 }
 
 // ----------------------------------------------------------------- tables
-// Per bin: f_j, the phase basis B_m(f_j) (FP64 and double-float), the weighted
-// data w_dj = 4 df f^(-7/6) d_dj / S_dj and the terms 4 df f^(-7/3) / S_dj of
-// the <h|h> prefix sums (scanned by k_prefix_scan).
+// Phase basis {f^-5/3, f^-1, f^-2/3, f^-1/3, ln f, f^1/3, f^1/3 ln f, f^2/3}.
+__device__ __forceinline__ void basis_at(double f, double B[NB]) {
+    const double lf = log(f);
+    const double c = cbrt(f);          // f^(1/3)
+    const double ic = 1.0 / c;
+    B[0] = ic * ic * ic * ic * ic;
+    B[1] = 1.0 / f;
+    B[2] = ic * ic;
+    B[3] = ic;
+    B[4] = lf;
+    B[5] = c;
+    B[6] = c * lf;
+    B[7] = c * c;
+}
+
+// Taylor coefficients D[k][m] = B_m^(k)(f) df^k / k!, k = 0..TK, of the basis
+// about f: binomial series for the powers, the log series for ln f, and their
+// Cauchy product for f^(1/3) ln f.
+__device__ __forceinline__ void basis_taylor(double f, double df, double D[TK + 1][NB]) {
+    const double r = df / f;
+    double B[NB];
+    basis_at(f, B);
+    const double pw[NB] = {-5.0 / 3.0, -1.0, -2.0 / 3.0, -1.0 / 3.0, 0.0, 1.0 / 3.0, 0.0, 2.0 / 3.0};
+#pragma unroll
+    for (int m = 0; m < NB; m++) {
+        if (m == 4 || m == 6) continue;
+        double cf = 1.0;
+        D[0][m] = B[m];
+        for (int k = 1; k <= TK; k++) {
+            cf *= (pw[m] - (k - 1)) / k * r;
+            D[k][m] = B[m] * cf;
+        }
+    }
+    D[0][4] = B[4];
+    double rk = 1.0;
+    for (int k = 1; k <= TK; k++) {
+        rk *= r;
+        D[k][4] = ((k & 1) ? rk : -rk) / k;
+    }
+    for (int k = 0; k <= TK; k++) {
+        double acc = 0.0;
+        for (int i = 0; i <= k; i++) acc += D[i][5] * D[k - i][4];
+        D[k][6] = acc;
+    }
+}
+
+// Per bin: f_j, the phase basis B_m(f_j), the weighted data
+// w_dj = 4 df f^(-7/6) d_dj / S_dj and the terms 4 df f^(-7/3) / S_dj of the
+// <h|h> prefix sums (scanned by k_prefix_scan). Mixed form per bin: B_m(f_j),
+// f_j and w_dj as floats. Tiled form: w_dj in pair-tile order over the padded
+// grid (zero beyond N) and, per tile, the basis Taylor coefficients about its
+// centre and the centre frequency.
 __global__ void k_build_tables(Model M, const double *dre, const double *dim, const double *psd,
-                               double *basis64, double *f64, double2 *w64, double *prefix,
-                               float2 *basis32, float2 *f32, float2 *w32) {
-    const int N = M.N;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += gridDim.x * blockDim.x) {
+                               double *basis64, double *f64, double2 *w64, double *prefix, float2 *basis32,
+                               float2 *f32, float2 *w32, float2 *tb0, float2 *tb1, float *tbk, float2 *fc,
+                               float2 *wt) {
+    const int N = M.N, lg = M.tlg;
+    const int jend = lg ? M.np : N;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < jend; j += gridDim.x * blockDim.x) {
+        if (lg && (j & ((1 << lg) - 1)) == 0) {
+            const int t = j >> lg, nt = M.np >> lg;
+            const double fcen = __dadd_rn(M.f0, __dmul_rn((double)(j + (1 << (lg - 1))), M.df));
+            double D[TK + 1][NB];
+            basis_taylor(fcen, M.df, D);
+#pragma unroll
+            for (int m = 0; m < NB; m++) {
+                float h = __double2float_rn(D[0][m]);
+                tb0[(size_t)m * nt + t] = make_float2(h, __double2float_rn(D[0][m] - (double)h));
+                h = __double2float_rn(D[1][m]);
+                tb1[(size_t)m * nt + t] = make_float2(h, __double2float_rn(D[1][m] - (double)h));
+                for (int k = 2; k <= TK; k++) tbk[((size_t)(k - 2) * NB + m) * nt + t] = __double2float_rn(D[k][m]);
+            }
+            const float h = __double2float_rn(fcen);
+            fc[t] = make_float2(h, __double2float_rn(fcen - (double)h));
+        }
+        if (j >= N) {
+            for (int d = 0; d < M.n_det; d++) wt[(size_t)d * M.np + tile_pos2(j, lg)] = make_float2(0.f, 0.f);
+            continue;
+        }
         const double f = __dadd_rn(M.f0, __dmul_rn((double)j, M.df));
-        const double lf = log(f);
-        const double c = cbrt(f);          // f^(1/3)
-        const double ic = 1.0 / c;
         double B[NB];
-        B[0] = ic * ic * ic * ic * ic;      // f^(-5/3)
-        B[1] = 1.0 / f;                     // f^(-1)
-        B[2] = ic * ic;                     // f^(-2/3)
-        B[3] = ic;                          // f^(-1/3)
-        B[4] = lf;                          // ln f
-        B[5] = c;                           // f^(1/3)
-        B[6] = c * lf;                      // f^(1/3) ln f
-        B[7] = c * c;                       // f^(2/3)
+        basis_at(f, B);
 #pragma unroll
         for (int m = 0; m < NB; m++) {
             basis64[(size_t)m * N + j] = B[m];
-            float h = __double2float_rn(B[m]);
-            basis32[(size_t)m * N + j] = make_float2(h, __double2float_rn(B[m] - (double)h));
+            if (!lg) {
+                const float h = __double2float_rn(B[m]);
+                basis32[(size_t)m * N + j] = make_float2(h, __double2float_rn(B[m] - (double)h));
+            }
         }
         f64[j] = f;
-        {
-            float h = __double2float_rn(f);
+        if (!lg) {
+            const float h = __double2float_rn(f);
             f32[j] = make_float2(h, __double2float_rn(f - (double)h));
         }
         const double f76 = pow(f, -7.0 / 6.0);
         for (int d = 0; d < M.n_det; d++) {
             const size_t o = (size_t)d * N + j;
-            const double s = psd[o];
-            const double wr = 4.0 * M.df * f76 * dre[o] / s;
-            const double wi = 4.0 * M.df * f76 * dim[o] / s;
+            const double sd = psd[o];
+            const double wr = 4.0 * M.df * f76 * dre[o] / sd;
+            const double wi = 4.0 * M.df * f76 * dim[o] / sd;
             w64[o] = make_double2(wr, wi);
-            w32[o] = make_float2(__double2float_rn(wr), __double2float_rn(wi));
-            prefix[o] = 4.0 * M.df * f76 * f76 / s;
+            const float2 wf = make_float2(__double2float_rn(wr), __double2float_rn(wi));
+            if (lg) wt[(size_t)d * M.np + tile_pos2(j, lg)] = wf;
+            else w32[o] = wf;
+            prefix[o] = 4.0 * M.df * f76 * f76 / sd;
         }
     }
 }
@@ -134,11 +199,11 @@ __global__ void k_prefix_scan(double *prefix, int N) {
 
 cudaError_t launch_build_tables(const Model &M, const double *data_re, const double *data_im,
                                 const double *psd, double *basis64, double *f64, double2 *w64,
-                                double *prefix, float2 *basis32, float2 *f32, float2 *w32,
-                                cudaStream_t s) {
-    int blocks = min((M.N + 255) / 256, 152 * 8);
-    k_build_tables<<<blocks, 256, 0, s>>>(M, data_re, data_im, psd, basis64, f64, w64, prefix, basis32,
-                                          f32, w32);
+                                double *prefix, const MixedTables &X, cudaStream_t s) {
+    const int n = M.tlg ? M.np : M.N;
+    int blocks = min((n + 255) / 256, 152 * 8);
+    k_build_tables<<<blocks, 256, 0, s>>>(M, data_re, data_im, psd, basis64, f64, w64, prefix, X.basis32,
+                                          X.f32, X.w32, X.tb0, X.tb1, X.tbk, X.fc, X.wt);
     k_prefix_scan<<<M.n_det, 1024, 0, s>>>(prefix, M.N);
     return cudaGetLastError();
 }

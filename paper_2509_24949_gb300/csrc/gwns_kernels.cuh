@@ -59,6 +59,14 @@ __device__ __forceinline__ void load_desc(const Desc *g, Desc &s) {
     __syncthreads();
 }
 
+// Writable mixed-form tables (per-bin or tiled set, by Model::tlg).
+struct MixedTables {
+    float2 *basis32, *f32, *w32;
+    float2 *tb0, *tb1;
+    float *tbk;
+    float2 *fc, *wt;
+};
+
 struct ResultArgs {
     const double *dead_logl, *dead_logw, *dead_nlive;
     const double *fin_logl, *fin_logw, *fin_nlive;   // [n] final live points, ascending
@@ -92,8 +100,7 @@ cudaError_t slice_multi_launch(const Desc *D, const int2 *map, int nblocks, int 
 // Launchers (return cudaGetLastError()).
 cudaError_t launch_build_tables(const Model &M, const double *data_re, const double *data_im,
                                 const double *psd, double *basis64, double *f64, double2 *w64,
-                                double *prefix, float2 *basis32, float2 *f32, float2 *w32,
-                                cudaStream_t s);
+                                double *prefix, const MixedTables &X, cudaStream_t s);
 cudaError_t launch_init_live(const Model &M, uint64_t seed, int n, double *live_u, cudaStream_t s);
 cudaError_t launch_eval(const Model &M, const Tables &T, int precision, int warps, const double *in,
                         int in_is_theta, int m, double *logl, cudaStream_t s);

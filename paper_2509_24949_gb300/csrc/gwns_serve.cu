@@ -41,12 +41,13 @@ struct Request {
 };
 
 size_t footprint(const Request &r) {
-    // tables: basis (FP64 + float2), f, weighted data (double2 + float2),
-    // prefix, data and PSD copies; live, final and dead sets; fixed overhead
+    // tables: FP64 basis, f, weighted data, prefix, data and PSD copies; the
+    // mixed form's tiled increments, weighted data and tile anchors (grid
+    // padded by less than 1024 bins); live, final and dead sets; fixed overhead
     int d = 0;
     for (int p = 0; p < NS_NPARAM; p++) d += r.prior.kind[p] != NS_PRIOR_FIXED;
     const size_t N = r.N, D = r.n_det, n = r.opts.n_live;
-    size_t b = (144 + 56 * D) * N;
+    size_t b = (72 + 48 * D) * N + (37 + 8 * D) * (N + 1024);
     b += n * (16 * d + 40);
     b += 64 * n * (size_t)(d + 3) * 8;
     if (r.coarse_bins > 0) b += (size_t)(r.coarse_bins + 1) * (160 + 64 * D) + 16 * D * N;

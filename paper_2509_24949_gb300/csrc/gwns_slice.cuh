@@ -17,13 +17,29 @@ __device__ __forceinline__ void cta_loglike_bins(const Model &M, const Tables &T
     double zr[NDET], zi[NDET];
     if (PREC == 0) {
         bins_fp64<NDET>(T, M.N, M.f0, M.df, coef, threadIdx.x, W * 32, zr, zi);
+#pragma unroll
+        for (int d = 0; d < NDET; d++) {
+            zr[d] = warp_sum(zr[d]);
+            zi[d] = warp_sum(zi[d]);
+        }
+    } else if (M.tlg) {
+        // tiled form: warp w takes tile groups w, w + W, ...
+        float zh[1][NDET][2], zl[1][NDET][2];
+        tile_bins<NDET, 1>(T, M.tlg, M.np, &cm, &coef.jcut, 1, warp, W, zh, zl);
+#pragma unroll
+        for (int d = 0; d < NDET; d++) {
+            warp_sum_df(zh[0][d][0], zl[0][d][0]);
+            warp_sum_df(zh[0][d][1], zl[0][d][1]);
+            zr[d] = (double)zh[0][d][0] + (double)zl[0][d][0];
+            zi[d] = (double)zh[0][d][1] + (double)zl[0][d][1];
+        }
     } else {
         bins_mixed<NDET>(T, M.N, cm, coef.jcut, threadIdx.x, W * 32, zr, zi);
-    }
 #pragma unroll
-    for (int d = 0; d < NDET; d++) {
-        zr[d] = warp_sum(zr[d]);
-        zi[d] = warp_sum(zi[d]);
+        for (int d = 0; d < NDET; d++) {
+            zr[d] = warp_sum(zr[d]);
+            zi[d] = warp_sum(zi[d]);
+        }
     }
     if (lane == 0) {
 #pragma unroll
@@ -62,7 +78,7 @@ __device__ __forceinline__ void warp_point_coef(const Model &M, const Tables &T,
         point_coef_warp(M, T, in, coef);
     }
     __syncwarp();
-    if (precision == 1) coef_to_mixed_warp(*coef, M.n_det, cm, M.rb ? T.rb.fid : nullptr);
+    if (precision == 1) coef_to_mixed_warp(*coef, M.n_det, M.df, cm, M.rb ? T.rb.fid : nullptr);
     (void)lane;
 }
 
@@ -378,7 +394,7 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
         if (warp < ns && M.rb) {
             // relative-binning likelihood of the slot's candidate
             if (PREC == 1) {
-                coef_to_mixed_warp(coef[warp], M.n_det, &cm[warp], T.rb.fid);
+                coef_to_mixed_warp(coef[warp], M.n_det, M.df, &cm[warp], T.rb.fid);
                 __syncwarp();
             }
             const double v = rb_loglike_warp<NDET, PREC>(M, T.rb, coef[warp], cm[warp], lane);
@@ -387,23 +403,44 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
                 coef[warp].jcut = T.rb.nb - 1;     // bins counted for the work statistics
             }
         } else if (PREC == 1 && S > 1 && S <= 4 && M.model == M_GW && !M.rb && M.coop) {
-            // mixed: all warps stride the bins for all candidates of the round
-            if (warp < ns) coef_to_mixed_warp(coef[warp], M.n_det, &cm[warp]);
+            // mixed, every warp on every candidate of the round: the tiled form
+            // shares out the tile groups (two candidates per pass on one table
+            // load), the per-bin form strides the bins
+            if (warp < ns) coef_to_mixed_warp(coef[warp], M.n_det, M.df, &cm[warp]);
             if (lane == 0 && warp < ns) jc[warp] = coef[warp].jcut;
             __syncthreads();
-            float zrh[S][NDET], zrl[S][NDET], zih[S][NDET], zil[S][NDET];
-            bins_mixed_multi<NDET, S>(T, M.N, cm, jc, ns, threadIdx.x, S * 32, zrh, zrl, zih, zil);
+            if (M.tlg) {
+                for (int c0 = 0; c0 < ns; c0 += 2) {
+                    float zh[2][NDET][2], zl[2][NDET][2];
+                    tile_bins<NDET, 2>(T, M.tlg, M.np, cm + c0, jc + c0, ns - c0 < 2 ? ns - c0 : 2, warp, S, zh,
+                                       zl);
 #pragma unroll
-            for (int sc = 0; sc < S; sc++)
+                    for (int sc = 0; sc < 2; sc++)
 #pragma unroll
-                for (int dd = 0; dd < NDET; dd++) {
-                    warp_sum_df(zrh[sc][dd], zrl[sc][dd]);
-                    warp_sum_df(zih[sc][dd], zil[sc][dd]);
-                    if (lane == 0) {
-                        part[warp][sc][dd][0] = (double)zrh[sc][dd] + (double)zrl[sc][dd];
-                        part[warp][sc][dd][1] = (double)zih[sc][dd] + (double)zil[sc][dd];
-                    }
+                        for (int dd = 0; dd < NDET; dd++) {
+                            warp_sum_df(zh[sc][dd][0], zl[sc][dd][0]);
+                            warp_sum_df(zh[sc][dd][1], zl[sc][dd][1]);
+                            if (lane == 0 && c0 + sc < S) {
+                                part[warp][c0 + sc][dd][0] = (double)zh[sc][dd][0] + (double)zl[sc][dd][0];
+                                part[warp][c0 + sc][dd][1] = (double)zh[sc][dd][1] + (double)zl[sc][dd][1];
+                            }
+                        }
                 }
+            } else {
+                float zrh[S][NDET], zrl[S][NDET], zih[S][NDET], zil[S][NDET];
+                bins_mixed_multi<NDET, S>(T, M.N, cm, jc, ns, threadIdx.x, S * 32, zrh, zrl, zih, zil);
+#pragma unroll
+                for (int sc = 0; sc < S; sc++)
+#pragma unroll
+                    for (int dd = 0; dd < NDET; dd++) {
+                        warp_sum_df(zrh[sc][dd], zrl[sc][dd]);
+                        warp_sum_df(zih[sc][dd], zil[sc][dd]);
+                        if (lane == 0) {
+                            part[warp][sc][dd][0] = (double)zrh[sc][dd] + (double)zrl[sc][dd];
+                            part[warp][sc][dd][1] = (double)zih[sc][dd] + (double)zil[sc][dd];
+                        }
+                    }
+            }
             __syncthreads();
             if (warp == 0) {
                 // lane = (candidate, detector): sum over warps, then log L per candidate
@@ -422,18 +459,39 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
             }
         } else if (warp < ns) {
             // one candidate per slot warp: bins and warp reduction
-            if (PREC == 1) {
-                coef_to_mixed_warp(coef[warp], M.n_det, &cm[warp]);
-                __syncwarp();
-            }
-            double zr[NDET], zi[NDET];
-            if (PREC == 0) bins_fp64<NDET, true>(T, M.N, M.f0, M.df, coef[warp], lane, 32, zr, zi);
-            else bins_mixed<NDET>(T, M.N, cm[warp], coef[warp].jcut, lane, 32, zr, zi);
             double v = 0.0;
+            if (PREC == 0) {
+                double zr[NDET], zi[NDET];
+                bins_fp64<NDET, true>(T, M.N, M.f0, M.df, coef[warp], lane, 32, zr, zi);
 #pragma unroll
-            for (int dd = 0; dd < NDET; dd++) {
-                const double ZR = warp_sum(zr[dd]), ZI = warp_sum(zi[dd]);
-                v += coef[warp].gre[dd] * ZR - coef[warp].gim[dd] * ZI;
+                for (int dd = 0; dd < NDET; dd++) {
+                    const double ZR = warp_sum(zr[dd]), ZI = warp_sum(zi[dd]);
+                    v += coef[warp].gre[dd] * ZR - coef[warp].gim[dd] * ZI;
+                }
+            } else if (M.tlg) {
+                coef_to_mixed_warp(coef[warp], M.n_det, M.df, &cm[warp]);
+                if (lane == 0) jc[warp] = coef[warp].jcut;
+                __syncwarp();
+                float zh[1][NDET][2], zl[1][NDET][2];
+                tile_bins<NDET, 1>(T, M.tlg, M.np, &cm[warp], &jc[warp], 1, 0, 1, zh, zl);
+#pragma unroll
+                for (int dd = 0; dd < NDET; dd++) {
+                    warp_sum_df(zh[0][dd][0], zl[0][dd][0]);
+                    warp_sum_df(zh[0][dd][1], zl[0][dd][1]);
+                    const double ZR = (double)zh[0][dd][0] + (double)zl[0][dd][0];
+                    const double ZI = (double)zh[0][dd][1] + (double)zl[0][dd][1];
+                    v += coef[warp].gre[dd] * ZR - coef[warp].gim[dd] * ZI;
+                }
+            } else {
+                coef_to_mixed_warp(coef[warp], M.n_det, M.df, &cm[warp]);
+                __syncwarp();
+                double zr[NDET], zi[NDET];
+                bins_mixed<NDET>(T, M.N, cm[warp], coef[warp].jcut, lane, 32, zr, zi);
+#pragma unroll
+                for (int dd = 0; dd < NDET; dd++) {
+                    const double ZR = warp_sum(zr[dd]), ZI = warp_sum(zi[dd]);
+                    v += coef[warp].gre[dd] * ZR - coef[warp].gim[dd] * ZI;
+                }
             }
             if (lane == 0) lval[warp] = (M.model == M_TOY) ? coef[warp].toy : v - 0.5 * coef[warp].hh;
         }

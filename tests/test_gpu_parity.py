@@ -69,9 +69,12 @@ def test_lnl_fp64_parity(gw, name, over, warps):
 
 
 @pytest.mark.parametrize("name,over", [("c0", {}), ("c1", {}), ("c1", {"N": 1013}),
-                                       ("c1", {"N": 33, "df": 4.0})])
+                                       ("c1", {"N": 33, "df": 4.0}), ("c1", {"N": 8000, "df": 0.03125}),
+                                       ("c1", {"N": 3001, "df": 0.03125})])
 @pytest.mark.parametrize("warps", [1, 2, 8])
 def test_lnl_mixed_parity(gw, name, over, warps):
+    """Coarse grids take the per-bin mixed form, fine ones (df = 1/32 Hz here:
+    16-bin tiles, the second with a ragged last group) the tiled form."""
     w, pb, th = problem(name, **over)
     u = pts_for(pb, th)
     want = pb.loglike(u)
@@ -391,6 +394,19 @@ def test_mixed_large_grid_cooperative_bins(gw, slots):
     the oracle)."""
     w, pb, th = problem("c2")
     with sampler_from(gw, pb, 1, n_live=60, k=30, steps_per_dim=2, seed=5, slots=slots) as sp:
+        sp.step()
+        u, l = sp.live()
+    want = pb.loglike(u)
+    assert np.max(np.abs(l - want)) < MIXED_ATOL
+
+
+@pytest.mark.parametrize("slots", [1, 2, 4])
+def test_mixed_tiled_form_in_slice_update(gw, slots):
+    """A fine grid below the cooperative size (8000 bins at 1/32 Hz): each slot
+    warp runs the tiled mixed form on its own candidate; live points after one
+    iteration agree with the oracle per point."""
+    w, pb, th = problem("c1", N=8000, df=0.03125)
+    with sampler_from(gw, pb, 1, n_live=60, k=30, steps_per_dim=2, seed=7, slots=slots) as sp:
         sp.step()
         u, l = sp.live()
     want = pb.loglike(u)
