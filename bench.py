@@ -515,7 +515,9 @@ def table_row(g, name, precision, stream, max_steps=100000, coarse=False):
     ev = st1["evals"] - st0["evals"]
     pb = st1["point_bins"] - st0["point_bins"]
     slice_ms = st1["kernel_ms"][3] - st0["kernel_ms"][3]
-    if precision == g.NS_FP64:
+    if coarse:
+        frac, pipe = None, None     # relative-binning sums, not the per-bin work these counts describe
+    elif precision == g.NS_FP64:
         frac = pb * fp64_flops_per_point_bin(w.n_det) / (slice_ms / 1e3) / (FP64_PEAK_TFLOPS * 1e12)
         pipe = "FP64"
     else:
@@ -525,7 +527,7 @@ def table_row(g, name, precision, stream, max_steps=100000, coarse=False):
             "form": "fp64" if precision == g.NS_FP64 else "mixed", "iterations": it, "done": done,
             "evals": ev, "evals_per_s": ev / (sum(ms) / 1e3), "point_bins_per_s": pb / (sum(ms) / 1e3),
             "bins_per_eval": pb / max(ev, 1), "k_slice_frac": frac, "k_slice_pipe": pipe,
-            "mixed_tile": st1["mixed_tile"] if precision != g.NS_FP64 else None,
+            "mixed_tile": st1["mixed_tile"] if precision != g.NS_FP64 and not coarse else None,
             "time_to_logZ_s": (t2 - t1) if done else None, "setup_s": setup_s,
             "p50_step_ms": float(np.percentile(ms, 50)), "p99_step_ms": float(np.percentile(ms, 99)),
             "logZ": r["logZ"] if r else None, "dlogZ": r["dlogZ"] if r else None}
@@ -605,6 +607,31 @@ def run_table(args):
         print(json.dumps(r), flush=True)
 
 
+def run_profile_case(args):
+    """A few iterations of one workload and form, untimed, for profiler captures
+    of its kernels (e.g. ncu -k regex:k_slice -s <warm-up launches> -c 1)."""
+    import torch
+    import paper_2509_24949_gb300 as g
+    from paper_2509_24949_gb300 import _build
+    if not _build.up_to_date():
+        _build.build()
+    w = gi.workload(args.profile_case)
+    if args.n_live:
+        w.n_live = args.n_live
+    if args.k:
+        w.k = args.k
+    prec = g.NS_MIXED if args.precision == "mixed" else g.NS_FP64
+    stream = torch.cuda.Stream()
+    sp, th = g.make_analysis(w, precision=prec, stream=stream.cuda_stream)
+    for _ in range(args.steps):
+        sp.step()
+    st = sp.stats()
+    sp.close()
+    print(json.dumps({"profile_case": args.profile_case, "precision": args.precision, "n_live": w.n_live,
+                      "k": w.k, "iterations": st["iterations"], "evals": st["evals"],
+                      "point_bins": st["point_bins"], "mixed_tile": st["mixed_tile"], "status": st["status"]}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -619,11 +646,19 @@ def main():
                     help="per-workload table (full runs of c0-c2 and c4 on coarse bins, c4 full grid, "
                          "oracle rates): one JSON line each")
     ap.add_argument("--no-oracle", action="store_true", help="with --table: skip the oracle rates")
+    ap.add_argument("--profile-case", default=None,
+                    help="workload (c0..c4): run --steps untimed iterations for a profiler capture")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--n-live", type=int, default=0)
+    ap.add_argument("--k", type=int, default=0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.table:
         run_table(args)
+        return
+    if args.profile_case:
+        run_profile_case(args)
         return
     if args.impl == "reference":
         run_reference(args)

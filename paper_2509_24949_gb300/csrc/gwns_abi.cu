@@ -198,8 +198,9 @@ int choose_slots(const ns_ctx *c) {
     if (c->M.model == M_TOY) return 1;
     const int bins = c->M.rb ? c->T.rb.nb : c->M.N;
     // measured on GB300 (512 / 4017 / 64,897-bin workloads): FP64 binds on its
-    // pipe beyond small grids, the mixed form on latency up to large grids
-    if (c->precision == NS_FP64) return bins <= 1024 ? 4 : (bins <= 131072 ? 2 : 1);
+    // pipe beyond small grids (one slot plus tail speculation from 64,897 bins),
+    // the mixed form on latency up to large grids
+    if (c->precision == NS_FP64) return bins <= 1024 ? 4 : (bins <= 16384 ? 2 : 1);
     return bins <= 1024 ? 8 : (c->M.coop ? 2 : 4);
 }
 
@@ -447,6 +448,17 @@ int ns_init(ns_ctx **out, const ns_prior *prior, const ns_data *data, const ns_p
             dim += prior->kind[p] != NS_PRIOR_FIXED;
         }
         M.dim = dim;
+        M.inv_df = 1.0 / M.df;
+        for (int p = 0; p < NS_NPARAM; p++) {
+            const double lo = M.lo[p], hi = M.hi[p];
+            if (M.kind[p] == K_VOLUME) {
+                M.pbase[p] = lo * lo * lo;
+                M.pspan[p] = hi * hi * hi - lo * lo * lo;
+            } else {
+                M.pbase[p] = lo;
+                M.pspan[p] = hi - lo;
+            }
+        }
         // large grids: the mixed slice update shares each bin's table loads among
         // the round's candidates (measured faster from ~16k bins on GB300)
         M.coop = M.N >= 16384 ? 1 : 0;

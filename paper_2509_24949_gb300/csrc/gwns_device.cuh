@@ -45,8 +45,10 @@ struct Model {
     int tlg;          // mixed form: 0 per bin, else log2 of the bins per lane tile (tiled form)
     int np;           // tiled form: N padded to whole groups of 32 tiles
     double f0, df;
+    double inv_df;    // 1 / df
     int kind[NPARAM];
     double lo[NPARAM], hi[NPARAM];
+    double pbase[NPARAM], pspan[NPARAM];   // uniform: lo, hi - lo; volume: lo^3, hi^3 - lo^3
     double pos[MAXDET][3], xarm[MAXDET][3], yarm[MAXDET][3];
     // toy: x = toy_lo + (toy_hi - toy_lo) u, Sigma_ij = rho^|i-j|
     double toy_lo, toy_hi, toy_rho, toy_lognorm;
@@ -178,6 +180,36 @@ __device__ __forceinline__ int cutoff_index(const Model &M, double fisco) {
     return j;
 }
 
+// The same index from the grid's frequency table (f64[j] holds exactly the
+// rounded f0 + j*df compared above): a first guess by one multiplication, then
+// at most a step either way against the table.
+__device__ __forceinline__ int cutoff_index_tab(const Model &M, const double *f64, double fisco) {
+    if (!M.cutoff) return M.N - 1;
+    const double jf = floor((fisco - M.f0) * M.inv_df);
+    if (!(jf >= -1.0)) return -1;
+    int j = jf > (double)(M.N - 1) ? M.N - 1 : (int)jf;
+    for (int it = 0; it < 4 && j + 1 <= M.N - 1 && __ldg(f64 + j + 1) <= fisco; it++) j++;
+    for (int it = 0; it < 4 && j >= 0 && __ldg(f64 + j) > fisco; it++) j--;
+    return j;
+}
+
+// eta-polynomial part of each phase coefficient, c0 + c1 eta + c2 eta^2 + c3 eta^3,
+// in basis order (f^-5/3, f^-1, f^-2/3, f^-1/3, ln f, f^1/3, f^1/3 ln f, f^2/3):
+// 1; phi_2; phi_3 without spin; phi_4 without spin; phi_5 without spin (the
+// ln v part of the 2.5PN term, 3 ln v = 3 ln a + ln f); phi_6 without its log
+// term; the f^1/3 ln f part -6848/63 of the 3PN log; phi_7.
+__device__ const double PN_POLY[NB * 4] = {
+    1.0, 0.0, 0.0, 0.0,
+    3715.0 / 756.0, 55.0 / 9.0, 0.0, 0.0,
+    -16.0 * PI_D, 0.0, 0.0, 0.0,
+    15293365.0 / 508032.0, 27145.0 / 504.0, 3085.0 / 72.0, 0.0,
+    PI_D * 38645.0 / 756.0, -PI_D * 65.0 / 9.0, 0.0, 0.0,
+    11583231236531.0 / 4694215680.0 - 640.0 / 3.0 * PI_D * PI_D - 6848.0 / 21.0 * GAMMA_E,
+    -15737765635.0 / 3048192.0 + 2255.0 / 12.0 * PI_D * PI_D, 76055.0 / 1728.0, -127825.0 / 1296.0,
+    -6848.0 / 63.0, 0.0, 0.0, 0.0,
+    PI_D * 77096675.0 / 254016.0, PI_D * 378515.0 / 1512.0, -PI_D * 74045.0 / 756.0, 0.0,
+};
+
 // Per-point coefficients, computed by lane groups of 8: group g of the calling
 // warp handles point g (g < count), so one warp computes up to four points at
 // the cost of one (FP64 costs one warp instruction whatever the number of
@@ -208,10 +240,9 @@ __device__ inline void point_coef_group(const Model &M, const Tables &T, const d
             if (M.kind[p] == K_FIXED) {
                 th[p] = M.lo[p];
             } else if (M.kind[p] == K_UNIFORM) {
-                th[p] = __dadd_rn(M.lo[p], __dmul_rn(__dsub_rn(M.hi[p], M.lo[p]), u[i++]));
+                th[p] = fma(M.pspan[p], u[i++], M.pbase[p]);
             } else {
-                const double lo3 = M.lo[p] * M.lo[p] * M.lo[p], hi3 = M.hi[p] * M.hi[p] * M.hi[p];
-                const double v = __dadd_rn(lo3, __dmul_rn(u[i++], __dsub_rn(hi3, lo3)));
+                const double v = fma(M.pspan[p], u[i++], M.pbase[p]);
                 if (p == P_DL) { dl_vol = true; dl_arg = v; th[p] = 0.0; }
                 else th[p] = cbrt(v);
             }
@@ -248,36 +279,37 @@ __device__ inline void point_coef_group(const Model &M, const Tables &T, const d
     const double K = __shfl_sync(FULL, ex, 3, 8);
     const double amp = __shfl_sync(FULL, ex, 4, 8);
     // f_ISCO = 1/(6^(3/2) pi T_M)
-    const int jcut = cutoff_index(M, inv_pitm * 0.06804138174397717);
+    const int jcut = cutoff_index_tab(M, T.f64, inv_pitm * 0.06804138174397717);
 
-    // TaylorF2 phasing (3.5PN non-spinning + aligned-spin beta, sigma, gamma)
+    // TaylorF2 phasing (3.5PN non-spinning + aligned-spin beta, sigma, gamma):
+    // sub-lane m computes basis coefficient m = K a^e_m (P_m(eta) + s_m), with
+    // K v^(k-5) = K a^(k-5) f^((k-5)/3), P_m the eta polynomial of its PN order
+    // and s_m its spin (or log) term.
     const double pi = PI_D;
+    const double beta = (113.0 / 12.0) * (chis + delta * chia - (76.0 / 113.0) * eta * chis);
+    const double sigma = (79.0 / 8.0) * eta * th[P_CHI1] * th[P_CHI2];
+    const double gamma = (732985.0 / 2268.0 - 24260.0 / 81.0 * eta - 340.0 / 9.0 * eta * eta) * chis
+                       + (732985.0 / 2268.0 + 140.0 / 9.0 * eta) * delta * chia;
+    {
+        const int m = sl;
+        // |e_m| for e = (-5, -3, -2, -1, 0, 1, 1, 2); negative powers from 1/a
+        const int e = m == 0 ? 5 : m == 1 ? 3 : (m == 2 || m == 7) ? 2 : m == 4 ? 0 : 1;
+        const double base = m < 4 ? ia : a;
+        const double b2 = base * base;
+        double pw = (e & 1) ? base : 1.0;
+        pw *= (e & 2) ? b2 : 1.0;
+        pw *= (e & 4) ? b2 * b2 : 1.0;
+        const double *pc = PN_POLY + 4 * m;
+        const double poly = fma(fma(fma(__ldg(pc + 3), eta, __ldg(pc + 2)), eta, __ldg(pc + 1)), eta, __ldg(pc));
+        const double sp = m == 2 ? 4.0 * beta
+                        : m == 3 ? -10.0 * sigma
+                        : m == 4 ? -gamma
+                        : m == 5 ? -6848.0 / 21.0 * (1.3862943611198906 + ln_a) : 0.0;
+        if (writer) out->a[m] = K * pw * (poly + sp);
+    }
     if (sl == 0 && writer) {
-        const double beta = (113.0 / 12.0) * (chis + delta * chia - (76.0 / 113.0) * eta * chis);
-        const double sigma = (79.0 / 8.0) * eta * th[P_CHI1] * th[P_CHI2];
-        const double gamma = (732985.0 / 2268.0 - 24260.0 / 81.0 * eta - 340.0 / 9.0 * eta * eta) * chis
-                           + (732985.0 / 2268.0 + 140.0 / 9.0 * eta) * delta * chia;
-        const double phi2 = 3715.0 / 756.0 + 55.0 / 9.0 * eta;
-        const double phi3 = -16.0 * pi + 4.0 * beta;
-        const double phi4 = 15293365.0 / 508032.0 + 27145.0 / 504.0 * eta + 3085.0 / 72.0 * eta * eta
-                          - 10.0 * sigma;
-        const double phi5 = pi * (38645.0 / 756.0 - 65.0 / 9.0 * eta) - gamma;   // x (1 + 3 ln(v sqrt 6))
-        const double phi6 = 11583231236531.0 / 4694215680.0 - 640.0 / 3.0 * pi * pi
-                          - 6848.0 / 21.0 * GAMMA_E
-                          + eta * (-15737765635.0 / 3048192.0 + 2255.0 / 12.0 * pi * pi)
-                          + 76055.0 / 1728.0 * eta * eta - 127825.0 / 1296.0 * eta * eta * eta;
-        const double phi7 = pi * (77096675.0 / 254016.0 + 378515.0 / 1512.0 * eta - 74045.0 / 756.0 * eta * eta);
-        // K v^(k-5) = K a^(k-5) f^((k-5)/3)
-        const double ia2 = ia * ia, ia3 = ia2 * ia, ia5 = ia3 * ia2;
-        out->a[0] = K * ia5;                       // f^(-5/3)
-        out->a[1] = K * phi2 * ia3;                // f^(-1)
-        out->a[2] = K * phi3 * ia2;                // f^(-2/3)
-        out->a[3] = K * phi4 * ia;                 // f^(-1/3)
-        out->a[4] = K * phi5;                      // ln f   (3 ln v = 3 ln a + ln f)
-        out->a[5] = K * a * (phi6 - 6848.0 / 21.0 * (1.3862943611198906 + ln_a));   // f^(1/3)
-        out->a[6] = -K * a * (6848.0 / 63.0);      // f^(1/3) ln f
-        out->a[7] = K * phi7 * a * a;              // f^(2/3)
         // constant: -phi_c - pi/4 + K phi5 (1 + 3 ln sqrt 6 + 3 ln a), reduced mod 2 pi
+        const double phi5 = pi * (38645.0 / 756.0 - 65.0 / 9.0 * eta) - gamma;
         const double c0 = -th[P_PHIC] - 0.25 * pi + K * phi5 * (1.0 + 3.0 * 0.8958797346140275 + 3.0 * ln_a);
         out->c0 = c0 - TWO_PI_D * rint(c0 * INV_TWO_PI_D);
         out->jcut = jcut;
