@@ -607,6 +607,36 @@ def run_table(args):
         print(json.dumps(r), flush=True)
 
 
+def run_scaling_study(args):
+    """Runtime of whole runs against the live-point count (k = n/2) and against
+    the deletion count k at n = 1000 (the paper's parallelism study, Sec. 4),
+    on the 3-detector 4017-bin workload; one JSON line per run."""
+    import torch
+    import paper_2509_24949_gb300 as g
+    from paper_2509_24949_gb300 import _build
+    if not _build.up_to_date():
+        _build.build()
+    prec = g.NS_MIXED if args.precision == "mixed" else g.NS_FP64
+    stream = torch.cuda.Stream()
+    runs = [(n, n // 2) for n in (125, 250, 500, 1000, 2000, 4000)]
+    runs += [(1000, k) for k in (10, 50, 100, 250, 750, 900)]
+    for n, k in runs:
+        w = gi.workload("c1")
+        w.n_live, w.k = n, k
+        sp, th = g.make_analysis(w, precision=prec, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        it = sp.run()
+        r = sp.result(samples=False)
+        t1 = time.perf_counter()
+        st = sp.stats()
+        sp.close()
+        print(json.dumps({"study": "runtime vs n and k", "workload": "c1", "precision": args.precision,
+                          "n_live": n, "k": k, "iterations": it, "seconds": t1 - t0, "evals": st["evals"],
+                          "evals_per_s": st["evals"] / (t1 - t0), "logZ": r["logZ"], "dlogZ": r["dlogZ"]}),
+              flush=True)
+
+
 def run_profile_case(args):
     """A few iterations of one workload and form, untimed, for profiler captures
     of its kernels (e.g. ncu -k regex:k_slice -s <warm-up launches> -c 1)."""
@@ -649,6 +679,8 @@ def main():
     ap.add_argument("--profile-case", default=None,
                     help="workload (c0..c4): run --steps untimed iterations for a profiler capture")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--scaling-study", action="store_true",
+                    help="whole-run time against n_live (k = n/2) and against k at n = 1000 (c1)")
     ap.add_argument("--n-live", type=int, default=0)
     ap.add_argument("--k", type=int, default=0)
     args = ap.parse_args()
@@ -659,6 +691,9 @@ def main():
         return
     if args.profile_case:
         run_profile_case(args)
+        return
+    if args.scaling_study:
+        run_scaling_study(args)
         return
     if args.impl == "reference":
         run_reference(args)

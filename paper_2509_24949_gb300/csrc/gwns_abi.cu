@@ -236,6 +236,7 @@ StepArgs step_args(ns_ctx *c, int k) {
     A.active = c->active;
     A.depth = choose_slots(c);
     A.tail = c->n_sm;
+    A.tail_coop = c->n_sm;
     return A;
 }
 

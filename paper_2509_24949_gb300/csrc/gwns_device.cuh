@@ -103,6 +103,7 @@ struct Coef {
     double toy;            // toy model log L
     double rot_re[MAXDET], rot_im[MAXDET];   // exp(2 pi i rot_stride df tau_d) (FP64 loop)
     double fisco;          // f_ISCO [Hz]
+    double amp;            // Newtonian amplitude factor A
     int jcut;              // last bin with f_j <= f_ISCO (-1: none)
     int pad;
 };
@@ -223,7 +224,7 @@ __device__ const double PN_POLY[NB * 4] = {
 // exp(2 pi i rot_stride df tau_d), the rotation between bins rot_stride apart
 // used by the FP64 bin loop. GW model only; all 32 lanes must call.
 __device__ inline void point_coef_group(const Model &M, const Tables &T, const double *u0, int ustride,
-                                        Coef *out0, int count, int rot_stride) {
+                                        Coef *out0, int count, int rot_stride, int half = 0) {
     constexpr unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, g = lane >> 3, sl = lane & 7;
     const bool writer = g < count;
@@ -249,72 +250,80 @@ __device__ inline void point_coef_group(const Model &M, const Tables &T, const d
         }
         if (!dl_vol) dl_arg = th[P_DL];
     }
-    const double q = th[P_Q];
-    const double r1q = 1.0 / (1.0 + q);
-    const double eta = q * r1q * r1q;               // m1 m2 / M^2
-    const double delta = (1.0 - q) * r1q;           // (m1 - m2)/M, m1 >= m2
-    const double chis = 0.5 * (th[P_CHI1] + th[P_CHI2]);
-    const double chia = 0.5 * (th[P_CHI1] - th[P_CHI2]);
-    const double tmc = th[P_MC] * TSUN;
-    // packed log: sub-lane 0 ln(eta), 1 ln(T_Mc), others ln(D_L) (or of D_L^3)
-    const double lg = log(sl == 0 ? eta : (sl == 1 ? tmc : dl_arg));
-    const double ln_eta = __shfl_sync(FULL, lg, 0, 8);
-    const double ln_tmc = __shfl_sync(FULL, lg, 1, 8);
-    const double ln_dlx = __shfl_sync(FULL, lg, 2, 8);
-    const double ln_dl = dl_vol ? ln_dlx * (1.0 / 3.0) : ln_dlx;
-    // ln(pi T_M) with T_M = T_Mc eta^(-3/5); a = (pi T_M)^(1/3), v = a f^(1/3)
-    const double ln_x = 1.1447298858494002 + ln_tmc - 0.6 * ln_eta;
-    const double ln_a = ln_x * (1.0 / 3.0);
-    // packed exp: 0 a, 1 1/a, 2 1/(pi T_M), 3 K = 3/(128 eta),
-    // others A = sqrt(5/24) pi^(-2/3) c T_Mc^(5/6) / D_L (D_L in Mpc)
-    const double ex_arg = sl == 0 ? ln_a
-                        : sl == 1 ? -ln_a
-                        : sl == 2 ? -ln_x
-                        : sl == 3 ? -3.7534179752515073 - ln_eta
-                        : -33.81250354619071 + (5.0 / 6.0) * ln_tmc - ln_dl;
-    const double ex = exp(ex_arg);
-    const double a = __shfl_sync(FULL, ex, 0, 8);
-    const double ia = __shfl_sync(FULL, ex, 1, 8);
-    const double inv_pitm = __shfl_sync(FULL, ex, 2, 8);
-    const double K = __shfl_sync(FULL, ex, 3, 8);
-    const double amp = __shfl_sync(FULL, ex, 4, 8);
-    // f_ISCO = 1/(6^(3/2) pi T_M)
-    const int jcut = cutoff_index_tab(M, T.f64, inv_pitm * 0.06804138174397717);
+    // mass and phase part (half 0 or 1)
+    double amp = 0.0;
+    int jcut = -1;
+    if (half != 2) {
+        const double q = th[P_Q];
+        const double r1q = 1.0 / (1.0 + q);
+        const double eta = q * r1q * r1q;               // m1 m2 / M^2
+        const double delta = (1.0 - q) * r1q;           // (m1 - m2)/M, m1 >= m2
+        const double chis = 0.5 * (th[P_CHI1] + th[P_CHI2]);
+        const double chia = 0.5 * (th[P_CHI1] - th[P_CHI2]);
+        const double tmc = th[P_MC] * TSUN;
+        // packed log: sub-lane 0 ln(eta), 1 ln(T_Mc), others ln(D_L) (or of D_L^3)
+        const double lg = log(sl == 0 ? eta : (sl == 1 ? tmc : dl_arg));
+        const double ln_eta = __shfl_sync(FULL, lg, 0, 8);
+        const double ln_tmc = __shfl_sync(FULL, lg, 1, 8);
+        const double ln_dlx = __shfl_sync(FULL, lg, 2, 8);
+        const double ln_dl = dl_vol ? ln_dlx * (1.0 / 3.0) : ln_dlx;
+        // ln(pi T_M) with T_M = T_Mc eta^(-3/5); a = (pi T_M)^(1/3), v = a f^(1/3)
+        const double ln_x = 1.1447298858494002 + ln_tmc - 0.6 * ln_eta;
+        const double ln_a = ln_x * (1.0 / 3.0);
+        // packed exp: 0 a, 1 1/a, 2 1/(pi T_M), 3 K = 3/(128 eta),
+        // others A = sqrt(5/24) pi^(-2/3) c T_Mc^(5/6) / D_L (D_L in Mpc)
+        const double ex_arg = sl == 0 ? ln_a
+                            : sl == 1 ? -ln_a
+                            : sl == 2 ? -ln_x
+                            : sl == 3 ? -3.7534179752515073 - ln_eta
+                            : -33.81250354619071 + (5.0 / 6.0) * ln_tmc - ln_dl;
+        const double ex = exp(ex_arg);
+        const double a = __shfl_sync(FULL, ex, 0, 8);
+        const double ia = __shfl_sync(FULL, ex, 1, 8);
+        const double inv_pitm = __shfl_sync(FULL, ex, 2, 8);
+        const double K = __shfl_sync(FULL, ex, 3, 8);
+        amp = __shfl_sync(FULL, ex, 4, 8);
+        // f_ISCO = 1/(6^(3/2) pi T_M)
+        jcut = cutoff_index_tab(M, T.f64, inv_pitm * 0.06804138174397717);
 
-    // TaylorF2 phasing (3.5PN non-spinning + aligned-spin beta, sigma, gamma):
-    // sub-lane m computes basis coefficient m = K a^e_m (P_m(eta) + s_m), with
-    // K v^(k-5) = K a^(k-5) f^((k-5)/3), P_m the eta polynomial of its PN order
-    // and s_m its spin (or log) term.
-    const double pi = PI_D;
-    const double beta = (113.0 / 12.0) * (chis + delta * chia - (76.0 / 113.0) * eta * chis);
-    const double sigma = (79.0 / 8.0) * eta * th[P_CHI1] * th[P_CHI2];
-    const double gamma = (732985.0 / 2268.0 - 24260.0 / 81.0 * eta - 340.0 / 9.0 * eta * eta) * chis
-                       + (732985.0 / 2268.0 + 140.0 / 9.0 * eta) * delta * chia;
-    {
-        const int m = sl;
-        // |e_m| for e = (-5, -3, -2, -1, 0, 1, 1, 2); negative powers from 1/a
-        const int e = m == 0 ? 5 : m == 1 ? 3 : (m == 2 || m == 7) ? 2 : m == 4 ? 0 : 1;
-        const double base = m < 4 ? ia : a;
-        const double b2 = base * base;
-        double pw = (e & 1) ? base : 1.0;
-        pw *= (e & 2) ? b2 : 1.0;
-        pw *= (e & 4) ? b2 * b2 : 1.0;
-        const double *pc = PN_POLY + 4 * m;
-        const double poly = fma(fma(fma(__ldg(pc + 3), eta, __ldg(pc + 2)), eta, __ldg(pc + 1)), eta, __ldg(pc));
-        const double sp = m == 2 ? 4.0 * beta
-                        : m == 3 ? -10.0 * sigma
-                        : m == 4 ? -gamma
-                        : m == 5 ? -6848.0 / 21.0 * (1.3862943611198906 + ln_a) : 0.0;
-        if (writer) out->a[m] = K * pw * (poly + sp);
+        // TaylorF2 phasing (3.5PN non-spinning + aligned-spin beta, sigma, gamma):
+        // sub-lane m computes basis coefficient m = K a^e_m (P_m(eta) + s_m), with
+        // K v^(k-5) = K a^(k-5) f^((k-5)/3), P_m the eta polynomial of its PN order
+        // and s_m its spin (or log) term.
+        const double pi = PI_D;
+        const double beta = (113.0 / 12.0) * (chis + delta * chia - (76.0 / 113.0) * eta * chis);
+        const double sigma = (79.0 / 8.0) * eta * th[P_CHI1] * th[P_CHI2];
+        const double gamma = (732985.0 / 2268.0 - 24260.0 / 81.0 * eta - 340.0 / 9.0 * eta * eta) * chis
+                           + (732985.0 / 2268.0 + 140.0 / 9.0 * eta) * delta * chia;
+        {
+            const int m = sl;
+            // |e_m| for e = (-5, -3, -2, -1, 0, 1, 1, 2); negative powers from 1/a
+            const int e = m == 0 ? 5 : m == 1 ? 3 : (m == 2 || m == 7) ? 2 : m == 4 ? 0 : 1;
+            const double base = m < 4 ? ia : a;
+            const double b2 = base * base;
+            double pw = (e & 1) ? base : 1.0;
+            pw *= (e & 2) ? b2 : 1.0;
+            pw *= (e & 4) ? b2 * b2 : 1.0;
+            const double *pc = PN_POLY + 4 * m;
+            const double poly = fma(fma(fma(__ldg(pc + 3), eta, __ldg(pc + 2)), eta, __ldg(pc + 1)), eta, __ldg(pc));
+            const double sp = m == 2 ? 4.0 * beta
+                            : m == 3 ? -10.0 * sigma
+                            : m == 4 ? -gamma
+                            : m == 5 ? -6848.0 / 21.0 * (1.3862943611198906 + ln_a) : 0.0;
+            if (writer) out->a[m] = K * pw * (poly + sp);
+        }
+        if (sl == 0 && writer) {
+            // constant: -phi_c - pi/4 + K phi5 (1 + 3 ln sqrt 6 + 3 ln a), reduced mod 2 pi
+            const double phi5 = pi * (38645.0 / 756.0 - 65.0 / 9.0 * eta) - gamma;
+            const double c0 = -th[P_PHIC] - 0.25 * pi + K * phi5 * (1.0 + 3.0 * 0.8958797346140275 + 3.0 * ln_a);
+            out->c0 = c0 - TWO_PI_D * rint(c0 * INV_TWO_PI_D);
+            out->jcut = jcut;
+            out->fisco = inv_pitm * 0.06804138174397717;
+            out->amp = amp;
+        }
     }
-    if (sl == 0 && writer) {
-        // constant: -phi_c - pi/4 + K phi5 (1 + 3 ln sqrt 6 + 3 ln a), reduced mod 2 pi
-        const double phi5 = pi * (38645.0 / 756.0 - 65.0 / 9.0 * eta) - gamma;
-        const double c0 = -th[P_PHIC] - 0.25 * pi + K * phi5 * (1.0 + 3.0 * 0.8958797346140275 + 3.0 * ln_a);
-        out->c0 = c0 - TWO_PI_D * rint(c0 * INV_TWO_PI_D);
-        out->jcut = jcut;
-        out->fisco = inv_pitm * 0.06804138174397717;
-    }
+    // sky and detector part (half 0 or 2)
+    if (half == 1) return;
     const double ci = th[P_COSI];
     // packed sincos: sub-lane 0 ra, others psi
     double sn, cs;
@@ -349,19 +358,42 @@ __device__ inline void point_coef_group(const Model &M, const Tables &T, const d
         tau = th[P_TC] + dt;
         if (writer) {
             out->tau[dd] = tau;
-            out->gre[dd] = amp * qre;
-            out->gim[dd] = -amp * qim;
+            // half 2 leaves the amplitude to point_coef_join
+            out->gre[dd] = half == 2 ? qre : amp * qre;
+            out->gim[dd] = half == 2 ? -qim : -amp * qim;
         }
-        if (jcut >= 0) hh_part = amp * amp * (qre * qre + qim * qim) * T.prefix[(size_t)dd * M.N + jcut];
+        if (half == 0 && jcut >= 0)
+            hh_part = amp * amp * (qre * qre + qim * qim) * T.prefix[(size_t)dd * M.N + jcut];
     }
     if (rot_stride > 0) {
         double rs, rc;
         sincos(TWO_PI_D * ((double)rot_stride * M.df) * tau, &rs, &rc);
         if (sl < M.n_det && writer) { out->rot_re[sl] = rc; out->rot_im[sl] = rs; }
     }
+    if (half == 2) return;
 #pragma unroll
     for (int o = 4; o > 0; o >>= 1) hh_part += __shfl_xor_sync(FULL, hh_part, o, 8);
     if (sl == 0 && writer) out->hh = hh_part;
+}
+
+// After the two halves of point_coef_group ran on ns points (different warps,
+// then a barrier): one warp applies the amplitude to G_d and forms <h|h>.
+// Lane = (point, detector).
+__device__ __forceinline__ void point_coef_join(const Model &M, const Tables &T, Coef *c, int ns) {
+    const int lane = threadIdx.x & 31, nd = M.n_det;
+    const int pnt = lane / nd, dd = lane - pnt * nd;
+    double hh = 0.0;
+    if (pnt < ns && lane < 32 / nd * nd) {
+        const double amp = c[pnt].amp, qre = c[pnt].gre[dd], nqim = c[pnt].gim[dd];
+        c[pnt].gre[dd] = amp * qre;
+        c[pnt].gim[dd] = amp * nqim;
+        const int jcut = c[pnt].jcut;
+        if (jcut >= 0) hh = amp * amp * (qre * qre + nqim * nqim) * T.prefix[(size_t)dd * M.N + jcut];
+    }
+    // sum over the point's detectors (lanes pnt*nd .. pnt*nd + nd - 1)
+    double t = hh;
+    for (int k = 1; k < nd; k++) t += __shfl_down_sync(0xffffffffu, hh, k);
+    if (dd == 0 && pnt < ns && lane < 32 / nd * nd) c[pnt].hh = t;
 }
 
 // Coefficients of one point by one warp (toy model, or GW via lane group 0).
@@ -456,9 +488,12 @@ __device__ __forceinline__ void sincos_bf(double x, double &s, double &c) {
 // FP64: Psi_j from the basis (FP64 FMAs), exp(i Psi_j) by sincos, the detector
 // factor exp(2 pi i f_j tau_d) by a rotation recurrence along the thread's bins
 // (f advances by stride*df per step).
+// With PRE_ROT the coefficients carry the rotation for a stride of 32 bins;
+// the stride here is 32 << rot_sq (the rotation squared rot_sq times).
 template <int NDET, bool PRE_ROT = false>
 __device__ __forceinline__ void bins_fp64(const Tables &T, int N, double f0, double df, const Coef &c,
-                                          int tid, int stride, double zr[NDET], double zi[NDET]) {
+                                          int tid, int stride, double zr[NDET], double zi[NDET],
+                                          int rot_sq = 0) {
     double a[NB];
 #pragma unroll
     for (int m = 0; m < NB; m++) a[m] = c.a[m];
@@ -468,9 +503,18 @@ __device__ __forceinline__ void bins_fp64(const Tables &T, int N, double f0, dou
     for (int d = 0; d < NDET; d++) {
         zr[d] = 0.0; zi[d] = 0.0;
         if (tid <= c.jcut) {
-            sincos(TWO_PI_D * (f0 + tid * df) * c.tau[d], &ri[d], &rr[d]);
-            if (PRE_ROT) { pr[d] = c.rot_re[d]; pi_[d] = c.rot_im[d]; }
-            else sincos(TWO_PI_D * (stride * df) * c.tau[d], &pi_[d], &pr[d]);
+            sincos_bf(TWO_PI_D * (f0 + tid * df) * c.tau[d], ri[d], rr[d]);
+            if (PRE_ROT) {
+                pr[d] = c.rot_re[d];
+                pi_[d] = c.rot_im[d];
+                for (int q = 0; q < rot_sq; q++) {
+                    const double re = pr[d] * pr[d] - pi_[d] * pi_[d];
+                    pi_[d] = 2.0 * pr[d] * pi_[d];
+                    pr[d] = re;
+                }
+            } else {
+                sincos(TWO_PI_D * (stride * df) * c.tau[d], &pi_[d], &pr[d]);
+            }
         }
     }
     int j = tid;

@@ -41,6 +41,7 @@ struct StepArgs {
     int *active;          // chains of the current slice update still running
     int depth;            // candidates planned per round while many chains run
     int tail;             // below this many running chains, plan as many as there are warps
+    int tail_coop;        // FP64, below this many: base depth, spare warps share the candidates' bins
 };
 
 // One analysis' iteration arguments, for the multi-analysis launches.

@@ -339,7 +339,7 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
     __shared__ CoefMixed cm[S];
     __shared__ double ysh[S][MAXD];
     __shared__ double lval[S];
-    __shared__ int nslot;
+    __shared__ int nslot, tailmode;
     __shared__ int jc[S];
     __shared__ double part[S][S][NDET][2];
     if (chain >= A.k) return;
@@ -366,10 +366,16 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
             chain_run(M, A, c, chain, iter, lstar);
             // plan the base depth while many chains run; the stragglers of the
             // update (fewer running chains than the tail threshold) use every warp
-            int depth = S;
+            // FP64 among the very last chains keeps the base depth and gives the
+            // spare warps to the candidates' bins instead (FP64 branch below)
+            int depth = S, tail = 1;
             if (A.active) {
                 const int running = *((volatile int *)A.active);
-                if (running > A.tail) depth = A.depth;
+                if (running > A.tail) { depth = A.depth; tail = 0; }
+                else if (PREC == 0 && M.model == M_GW && !M.rb && running <= A.tail_coop) {
+                    depth = A.depth;
+                    tail = 2;
+                }
             }
             int ns = (c.phase == PH_DONE) ? 0 : chain_plan<S>(M, A, c, chain, iter, ysh, pk, pidx, depth);
             if (ns == 0 && c.phase != PH_DONE) {
@@ -378,19 +384,35 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
                 c.phase = PH_DONE;
                 if (lane == 0) atomicOr(&A.state->status, 1);
             }
-            if (lane == 0) nslot = ns;
+            if (lane == 0) { nslot = ns; tailmode = tail; }
         }
         __syncthreads();
         const int ns = nslot;
         if (ns == 0) break;
-        // coefficients: warp w computes candidates 4w .. 4w+3 (8 lanes each)
+        // coefficients: candidates 4j .. 4j+3 (8 lanes each) by one warp, or,
+        // with two warps per group of four, the mass/phase half on warp 2j and
+        // the sky/detector half on warp 2j + 1 (independent FP64 chains on two
+        // sub-partitions), joined after the barrier
         if (M.model == M_TOY) {
             if (warp < ns) point_coef_warp(M, T, ysh[warp], &coef[warp]);
-        } else if (4 * warp < ns) {
-            const int cnt = ns - 4 * warp < 4 ? ns - 4 * warp : 4;
-            point_coef_group(M, T, ysh[4 * warp], MAXD, &coef[4 * warp], cnt, PREC == 0 ? 32 : 0);
+            __syncthreads();
+        } else if (S >= 2) {
+            const int grp = warp >> 1;
+            if (4 * grp < ns && 2 * grp + 1 < S) {
+                const int cnt = ns - 4 * grp < 4 ? ns - 4 * grp : 4;
+                point_coef_group(M, T, ysh[4 * grp], MAXD, &coef[4 * grp], cnt, PREC == 0 ? 32 : 0,
+                                 1 + (warp & 1));
+            }
+            __syncthreads();
+            if (warp == 0) point_coef_join(M, T, coef, ns);
+            __syncthreads();
+        } else {
+            if (4 * warp < ns) {
+                const int cnt = ns - 4 * warp < 4 ? ns - 4 * warp : 4;
+                point_coef_group(M, T, ysh[4 * warp], MAXD, &coef[4 * warp], cnt, PREC == 0 ? 32 : 0);
+            }
+            __syncthreads();
         }
-        __syncthreads();
         if (warp < ns && M.rb) {
             // relative-binning likelihood of the slot's candidate
             if (PREC == 1) {
@@ -449,6 +471,44 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
                 if (sc < ns && lane < S * NDET) {
                     double ZR = 0.0, ZI = 0.0;
                     for (int w2 = 0; w2 < S; w2++) { ZR += part[w2][sc][dd][0]; ZI += part[w2][sc][dd][1]; }
+                    v = coef[sc].gre[dd] * ZR - coef[sc].gim[dd] * ZI;
+                }
+                for (int sc2 = 0; sc2 < ns; sc2++) {
+                    double t = (lane / NDET == sc2 && lane < S * NDET) ? v : 0.0;
+                    t = warp_sum(t);
+                    if (lane == 0) lval[sc2] = t - 0.5 * coef[sc2].hh;
+                }
+            }
+        } else if (PREC == 0 && S > 1 && M.model == M_GW && !M.rb && tailmode == 2) {
+            // FP64 among the update's last chains: each candidate's bins are
+            // spread over wpc = S / ns warps (rounded down to a power of two;
+            // warps on different SM sub-partitions issue FP64 independently),
+            // partial sums meet in shared memory. While many chains run, the
+            // duplicated per-warp start values would cost more FP64 issue than
+            // the shorter loop saves.
+            int lg = 0;
+            while ((ns << (lg + 1)) <= S) lg++;
+            const int wpc = 1 << lg, cand = warp >> lg, sub = warp & (wpc - 1);
+            if (cand < ns) {
+                double zr[NDET], zi[NDET];
+                bins_fp64<NDET, true>(T, M.N, M.f0, M.df, coef[cand], sub * 32 + lane, wpc * 32, zr, zi, lg);
+#pragma unroll
+                for (int dd = 0; dd < NDET; dd++) {
+                    const double ZR = warp_sum(zr[dd]), ZI = warp_sum(zi[dd]);
+                    if (lane == 0) { part[warp][0][dd][0] = ZR; part[warp][0][dd][1] = ZI; }
+                }
+            }
+            __syncthreads();
+            if (warp == 0) {
+                // lane = (candidate, detector): sum over the candidate's warps
+                double v = 0.0;
+                const int sc = lane / NDET, dd = lane % NDET;
+                if (sc < ns && lane < S * NDET) {
+                    double ZR = 0.0, ZI = 0.0;
+                    for (int w2 = 0; w2 < wpc; w2++) {
+                        ZR += part[sc * wpc + w2][0][dd][0];
+                        ZI += part[sc * wpc + w2][0][dd][1];
+                    }
                     v = coef[sc].gre[dd] * ZR - coef[sc].gim[dd] * ZI;
                 }
                 for (int sc2 = 0; sc2 < ns; sc2++) {
@@ -520,8 +580,14 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
     }
 }
 
+// At most 128 registers, so that 512 threads of chains fit on an SM: measured
+// on GB300 against the uncapped 168 (3 CTAs of 4 warps per SM), c1 FP64 10.9 ->
+// 9.8 ms, c1 mixed 4.7 -> 3.4 ms, c4 mixed 631 -> 550 ms per slice update, in
+// spite of ~100 bytes of spills in the mixed tile loop.
+#define SLICE_MIN_BLOCKS(PREC, S) (16 / (S))
+
 template <int PREC, int NDET, int S>
-__global__ void __launch_bounds__(S * 32) k_slice(Model M, Tables T, StepArgs A) {
+__global__ void __launch_bounds__(S * 32, SLICE_MIN_BLOCKS(PREC, S)) k_slice(Model M, Tables T, StepArgs A) {
     slice_body<PREC, NDET, S>(M, T, A, blockIdx.x);
 }
 
@@ -537,7 +603,7 @@ cudaError_t slice_launch(const Model &M, const Tables &T, int slots, const StepA
 }
 
 template <int PREC, int NDET, int S>
-__global__ void __launch_bounds__(S * 32) k_slice_multi(const Desc *D, const int2 *map) {
+__global__ void __launch_bounds__(S * 32, SLICE_MIN_BLOCKS(PREC, S)) k_slice_multi(const Desc *D, const int2 *map) {
     __shared__ Desc d;
     const int2 ac = map[blockIdx.x];
     load_desc(D + ac.x, d);
