@@ -132,6 +132,12 @@ typedef struct {
     double dlogz_stop;   /* stop when log(Z + X Lmax) - log Z < this [0.1] */
     uint64_t seed;       /* Philox key */
     void *stream;        /* cudaStream_t to run on [NULL: library-owned stream] */
+    unsigned periodic;   /* bit p set (p = NS_MC..NS_SINDEC): parameter p is periodic over
+                            its prior range (phi_c, psi, RA with their full-period uniform
+                            priors): its unit-cube coordinate wraps mod 1 on the slice line
+                            instead of leaving the prior box [0: none]. Toy model: bit i
+                            is unit-cube coordinate i. The paper (Sec. 2) names better
+                            handling of such parameters as future work. */
 } ns_options;
 
 typedef struct ns_ctx ns_ctx;

@@ -59,6 +59,7 @@ class _Problem(ctypes.Structure):
         ("toy_lognorm", ctypes.c_double), ("toy_lo", ctypes.c_double), ("toy_hi", ctypes.c_double),
         ("rb_nedge", ctypes.c_int), ("rb_J", ctypes.c_void_p), ("rb_sum", ctypes.c_void_p * 6),
         ("rb_theta_fid", ctypes.c_void_p),
+        ("periodic", ctypes.c_uint),
     ]
 
 
@@ -164,6 +165,27 @@ class Problem:
     @property
     def c(self):
         return ctypes.byref(self._c)
+
+    def set_periodic(self, params) -> int:
+        """Mark parameters as periodic (indices in gwinputs' parameter order; for
+        the toy model, unit-cube coordinates): their unit-cube coordinates wrap
+        mod 1 on the slice line instead of leaving the prior box. Returns the
+        mask over unit-cube coordinates."""
+        params = set(int(p) for p in params)
+        mask = 0
+        if self.model == MODEL_TOY:
+            for i in params:
+                mask |= 1 << i
+        else:
+            i = 0
+            for p in range(gi.NPARAM):
+                if int(self.kind[p]) == gi.PRIOR_FIXED:
+                    continue
+                if p in params:
+                    mask |= 1 << i
+                i += 1
+        self._c.periodic = mask
+        return mask
 
     @property
     def dim(self) -> int:

@@ -79,6 +79,9 @@ typedef struct {
     const int *rb_J;
     const double *rb_sum[6];  /* A0re, A0im, A1re, A1im, B0, B1: [n_det][nedge-1] */
     const double *rb_theta_fid;
+    /* bit i set: unit-cube coordinate i is periodic (uniform prior on a
+     * periodic parameter): slice positions wrap mod 1 instead of leaving the box */
+    unsigned periodic;
 } or_problem;
 
 /* ------------------------------------------------------------------ prior */
@@ -413,6 +416,15 @@ void or_replicate_uniforms(uint64_t seed, int replicate, long long m, double *ou
 
 /* -------------------------------------------------------- slice sampling */
 
+/* Candidate on the line x + t e; periodic coordinates wrapped into [0, 1). */
+static void line_point(const or_problem *pb, int d, const double *x, double t, const double *e, double *y)
+{
+    for (int i = 0; i < d; i++) {
+        y[i] = x[i] + t * e[i];
+        if ((pb->periodic >> i) & 1u) y[i] -= floor(y[i]);
+    }
+}
+
 static int in_slice(const or_problem *pb, int d, const double *y, double lstar, double *ly, long long *evals)
 {
     for (int i = 0; i < d; i++)
@@ -464,12 +476,12 @@ static void evolve_chain(const or_problem *pb, uint64_t seed, uint32_t iter, int
         double r = or_u01(w[0], w[1]);
         double a = -r, b = 1.0 - r, ly;
         for (int n = 0; n < max_stepout; n++) {
-            for (int i = 0; i < d; i++) y[i] = x[i] + a * e[i];
+            line_point(pb, d, x, a, e, y);
             if (!in_slice(pb, d, y, lstar, &ly, evals)) break;
             a -= 1.0;
         }
         for (int n = 0; n < max_stepout; n++) {
-            for (int i = 0; i < d; i++) y[i] = x[i] + b * e[i];
+            line_point(pb, d, x, b, e, y);
             if (!in_slice(pb, d, y, lstar, &ly, evals)) break;
             b += 1.0;
         }
@@ -478,7 +490,7 @@ static void evolve_chain(const or_problem *pb, uint64_t seed, uint32_t iter, int
         for (int n = 0; n < max_shrink; n++) {
             draw(seed, SLOT_SHRINK0 + (uint32_t)n, (uint32_t)s, (uint32_t)chain, iter, w);
             double t = a + (b - a) * or_u01(w[0], w[1]);
-            for (int i = 0; i < d; i++) y[i] = x[i] + t * e[i];
+            line_point(pb, d, x, t, e, y);
             if (in_slice(pb, d, y, lstar, &ly, evals)) {
                 for (int i = 0; i < d; i++) x[i] = y[i];
                 lx = ly;

@@ -426,6 +426,7 @@ int ns_init(ns_ctx **out, const ns_prior *prior, const ns_data *data, const ns_p
     if (o->model == NS_MODEL_TOY) {
         M.model = M_TOY;
         M.dim = o->toy_dim;
+        M.periodic = o->periodic;
         M.toy_lo = -10.0;
         M.toy_hi = 10.0;
         M.toy_rho = o->toy_dim > 1 ? 0.9 : 0.0;
@@ -450,6 +451,13 @@ int ns_init(ns_ctx **out, const ns_prior *prior, const ns_data *data, const ns_p
         }
         M.dim = dim;
         M.inv_df = 1.0 / M.df;
+        // periodic parameters -> unit-cube coordinates
+        M.periodic = 0;
+        for (int p = 0, i = 0; p < NS_NPARAM; p++) {
+            if (M.kind[p] == K_FIXED) continue;
+            if ((o->periodic >> p) & 1u) M.periodic |= 1u << i;
+            i++;
+        }
         for (int p = 0; p < NS_NPARAM; p++) {
             const double lo = M.lo[p], hi = M.hi[p];
             if (M.kind[p] == K_VOLUME) {

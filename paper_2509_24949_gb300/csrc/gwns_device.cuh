@@ -42,6 +42,7 @@ struct Model {
     int n_det, N, ideal, cutoff, dim;
     int rb;           // 1: relative-binning likelihood on the coarse bins
     int coop;         // 1: mixed slice update spreads each candidate's tile groups over all warps
+    unsigned periodic;   // bit i: unit-cube coordinate i wraps mod 1 on the slice line
     int tlg;          // mixed form: 0 per bin, else log2 of the bins per lane tile (tiled form)
     int np;           // tiled form: N padded to whole groups of 32 tiles
     double f0, df;

@@ -155,6 +155,15 @@ struct Chain {
     double cval[CACHE_MAX];
 };
 
+// Lane i's coordinate of the candidate x + t e (lanes >= d: 0.5, inside the
+// box); periodic coordinates wrap into [0, 1).
+__device__ __forceinline__ double line_y(const Model &M, const Chain &c, double t, int lane, int d) {
+    if (lane >= d) return 0.5;
+    double y = __dadd_rn(c.x, __dmul_rn(t, c.e));
+    if ((M.periodic >> lane) & 1u) y = __dsub_rn(y, floor(y));
+    return y;
+}
+
 __device__ __forceinline__ bool warp_inbox(double y, int lane, int d) {
     return __all_sync(0xffffffffu, lane >= d || (y >= 0.0 && y <= 1.0));
 }
@@ -238,7 +247,7 @@ static __device__ void chain_run(const Model &M, const StepArgs &A, Chain &c, in
                 continue;
             }
             const double t = left ? c.a : c.b;
-            const double y = (lane < d) ? __dadd_rn(c.x, __dmul_rn(t, c.e)) : 0.5;
+            const double y = line_y(M, c, t, lane, d);
             if (!warp_inbox(y, lane, d)) {
                 end_side(c, left);
                 continue;
@@ -261,7 +270,7 @@ static __device__ void chain_run(const Model &M, const StepArgs &A, Chain &c, in
             continue;
         }
         const double t = shrink_t(A, c.a, c.b, c.nsh, c.s, chain, iter);
-        const double y = (lane < d) ? __dadd_rn(c.x, __dmul_rn(t, c.e)) : 0.5;
+        const double y = line_y(M, c, t, lane, d);
         if (warp_inbox(y, lane, d)) {
             const int ci = cache_find(c, KIND_SH, c.nsh);
             if (ci < 0) return;
@@ -305,7 +314,7 @@ __device__ int chain_plan(const Model &M, const StepArgs &A, const Chain &c, int
             double t = left ? c.a : c.b;
             const int n0 = left ? c.nl : c.nr;
             for (int n = n0; n < n0 + S && n < A.max_stepout && ns < limit; n++) {
-                const double y = (lane < d) ? __dadd_rn(c.x, __dmul_rn(t, c.e)) : 0.5;
+                const double y = line_y(M, c, t, lane, d);
                 if (!warp_inbox(y, lane, d)) break;
                 if (cache_find(c, left ? KIND_L : KIND_R, n) < 0) {
                     if (lane < d) ysh[ns][lane] = y;
@@ -320,7 +329,7 @@ __device__ int chain_plan(const Model &M, const StepArgs &A, const Chain &c, int
         double a = c.a, b = c.b;
         for (int n = c.nsh; n < c.nsh + S && n < A.max_shrink && ns < cap; n++) {
             const double t = shrink_t(A, a, b, n, c.s, chain, iter);
-            const double y = (lane < d) ? __dadd_rn(c.x, __dmul_rn(t, c.e)) : 0.5;
+            const double y = line_y(M, c, t, lane, d);
             if (warp_inbox(y, lane, d) && cache_find(c, KIND_SH, n) < 0) {
                 if (lane < d) ysh[ns][lane] = y;
                 pk[ns] = KIND_SH;
@@ -333,7 +342,7 @@ __device__ int chain_plan(const Model &M, const StepArgs &A, const Chain &c, int
     return ns;
 }
 
-template <int PREC, int NDET, int S>
+template <int PREC, int NDET, int S, int W = S>
 __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, const int chain) {
     __shared__ Coef coef[S];
     __shared__ CoefMixed cm[S];
@@ -341,7 +350,7 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
     __shared__ double lval[S];
     __shared__ int nslot, tailmode;
     __shared__ int jc[S];
-    __shared__ double part[S][S][NDET][2];
+    __shared__ double part[W][S][NDET][2];
     if (chain >= A.k) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, d = M.dim;
     const uint32_t iter = (uint32_t)A.state->iter;
@@ -398,7 +407,7 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
             __syncthreads();
         } else if (S >= 2) {
             const int grp = warp >> 1;
-            if (4 * grp < ns && 2 * grp + 1 < S) {
+            if (4 * grp < ns && 2 * grp + 1 < W) {
                 const int cnt = ns - 4 * grp < 4 ? ns - 4 * grp : 4;
                 point_coef_group(M, T, ysh[4 * grp], MAXD, &coef[4 * grp], cnt, PREC == 0 ? 32 : 0,
                                  1 + (warp & 1));
@@ -434,7 +443,7 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
             if (M.tlg) {
                 for (int c0 = 0; c0 < ns; c0 += 2) {
                     float zh[2][NDET][2], zl[2][NDET][2];
-                    tile_bins<NDET, 2>(T, M.tlg, M.np, cm + c0, jc + c0, ns - c0 < 2 ? ns - c0 : 2, warp, S, zh,
+                    tile_bins<NDET, 2>(T, M.tlg, M.np, cm + c0, jc + c0, ns - c0 < 2 ? ns - c0 : 2, warp, W, zh,
                                        zl);
 #pragma unroll
                     for (int sc = 0; sc < 2; sc++)
@@ -450,7 +459,7 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
                 }
             } else {
                 float zrh[S][NDET], zrl[S][NDET], zih[S][NDET], zil[S][NDET];
-                bins_mixed_multi<NDET, S>(T, M.N, cm, jc, ns, threadIdx.x, S * 32, zrh, zrl, zih, zil);
+                bins_mixed_multi<NDET, S>(T, M.N, cm, jc, ns, threadIdx.x, W * 32, zrh, zrl, zih, zil);
 #pragma unroll
                 for (int sc = 0; sc < S; sc++)
 #pragma unroll
@@ -470,7 +479,7 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
                 const int sc = lane / NDET, dd = lane % NDET;
                 if (sc < ns && lane < S * NDET) {
                     double ZR = 0.0, ZI = 0.0;
-                    for (int w2 = 0; w2 < S; w2++) { ZR += part[w2][sc][dd][0]; ZI += part[w2][sc][dd][1]; }
+                    for (int w2 = 0; w2 < W; w2++) { ZR += part[w2][sc][dd][0]; ZI += part[w2][sc][dd][1]; }
                     v = coef[sc].gre[dd] * ZR - coef[sc].gim[dd] * ZI;
                 }
                 for (int sc2 = 0; sc2 < ns; sc2++) {
@@ -487,7 +496,7 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
             // duplicated per-warp start values would cost more FP64 issue than
             // the shorter loop saves.
             int lg = 0;
-            while ((ns << (lg + 1)) <= S) lg++;
+            while ((ns << (lg + 1)) <= W) lg++;
             const int wpc = 1 << lg, cand = warp >> lg, sub = warp & (wpc - 1);
             if (cand < ns) {
                 double zr[NDET], zi[NDET];
@@ -585,14 +594,25 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
 // 9.8 ms, c1 mixed 4.7 -> 3.4 ms, c4 mixed 631 -> 550 ms per slice update, in
 // spite of ~100 bytes of spills in the mixed tile loop.
 #define SLICE_MIN_BLOCKS(PREC, S) (16 / (S))
+#define SLICE_WIDE 1
 
-template <int PREC, int NDET, int S>
-__global__ void __launch_bounds__(S * 32, SLICE_MIN_BLOCKS(PREC, S)) k_slice(Model M, Tables T, StepArgs A) {
-    slice_body<PREC, NDET, S>(M, T, A, blockIdx.x);
+template <int PREC, int NDET, int S, int W = S>
+__global__ void __launch_bounds__(W * 32, SLICE_MIN_BLOCKS(PREC, W)) k_slice(Model M, Tables T, StepArgs A) {
+    slice_body<PREC, NDET, S, W>(M, T, A, blockIdx.x);
 }
 
 template <int PREC, int NDET>
 cudaError_t slice_launch(const Model &M, const Tables &T, int slots, const StepArgs &A, cudaStream_t s) {
+    // on grids of 262,144 bins or more the tiled mixed form with cooperative
+    // bins takes 8 warps for 4 slots: as many warps per SM as 4-warp CTAs, twice
+    // as many per chain, so the update's last chains finish sooner (GB300,
+    // 519,169 bins: 536 -> 467 ms per slice update; on 64,897 bins, where an
+    // evaluation has a few tile groups, 15.2 -> 17.5 ms, hence the threshold)
+    if (PREC == 1 && slots == 4 && SLICE_WIDE && M.model == M_GW && M.coop && M.tlg && !M.rb &&
+        M.N >= 262144) {
+        k_slice<PREC, NDET, 4, 8><<<A.k, 256, 0, s>>>(M, T, A);
+        return cudaGetLastError();
+    }
     switch (slots) {
         case 1: k_slice<PREC, NDET, 1><<<A.k, 32, 0, s>>>(M, T, A); break;
         case 2: k_slice<PREC, NDET, 2><<<A.k, 64, 0, s>>>(M, T, A); break;

@@ -196,6 +196,26 @@ def test_ns_iterations_match_oracle(gw, name, n_live, k, iters, slots):
     sp.close()
 
 
+@pytest.mark.parametrize("slots", [1, 2])
+def test_periodic_iterations_match_oracle(gw, slots):
+    """phi_c, psi and RA wrapping on the slice line: GPU and oracle follow the
+    same trajectories (a fresh problem, so no other test sees the mask)."""
+    w = gi.workload("c1")
+    pb, th = oracle.make_problem(w)
+    pb.set_periodic((gi.P_PHIC, gi.P_PSI, gi.P_RA))
+    n_live, k = 120, 60
+    st = ons.initial_state(pb, n_live, w.seed_sampler)
+    with sampler_from(gw, pb, 0, n_live=n_live, k=k, steps_per_dim=w.steps_per_dim, seed=w.seed_sampler,
+                      slots=slots, periodic=(gi.P_PHIC, gi.P_PSI, gi.P_RA)) as sp:
+        for it in range(2):
+            ons.iterate(pb, st, k, w.steps_per_dim * pb.dim, w.seed_sampler)
+            sp.step(k)
+            gu, gl = sp.live()
+            assert np.max(np.abs(gu - st.live_u)) < 1e-9, it
+            assert np.max(np.abs(gl - st.live_logl) / np.maximum(1, np.abs(st.live_logl))) < 1e-8
+            assert sp.stats()["evals"] == st.evals
+
+
 def test_ns_step_host_dead_points(gw):
     w, pb, sp, st = _ns_pair(gw, "c0", 100, 50)
     k, d = 50, pb.dim
@@ -396,6 +416,30 @@ def test_mixed_large_grid_cooperative_bins(gw, slots):
     with sampler_from(gw, pb, 1, n_live=60, k=30, steps_per_dim=2, seed=5, slots=slots) as sp:
         sp.step()
         u, l = sp.live()
+    want = pb.loglike(u)
+    assert np.max(np.abs(l - want)) < MIXED_ATOL
+
+
+@pytest.mark.parametrize("name,over,tile", [("c1", {}, 0), ("c1", {"N": 8000, "df": 0.03125}, 16),
+                                            ("c2", {}, 16), ("c4", {}, 64), ("c1", {"N": 33, "df": 4.0}, 0)])
+def test_mixed_form_choice(gw, name, over, tile):
+    """The tiled form is taken where the Taylor remainder bound allows (the
+    longest such tile), the per-bin form elsewhere."""
+    w, pb, th = problem(name, **over)
+    with sampler_from(gw, pb, 1, n_live=8) as sp:
+        assert sp.stats()["mixed_tile"] == tile
+
+
+def test_mixed_wide_ctas_on_the_largest_grid(gw):
+    """The 519,169-bin grid runs the mixed slice update with 8-warp CTAs
+    (64-bin tiles shared out by all warps): live points after one iteration
+    agree with the oracle per point."""
+    w, pb, th = problem("c4")
+    with sampler_from(gw, pb, 1, n_live=24, k=12, steps_per_dim=1, seed=11) as sp:
+        assert sp.stats()["mixed_tile"] == 64
+        sp.step()
+        u, l = sp.live()
+        assert sp.stats()["status"] == 0
     want = pb.loglike(u)
     assert np.max(np.abs(l - want)) < MIXED_ATOL
 

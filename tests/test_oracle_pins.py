@@ -328,6 +328,56 @@ def test_chains_without_constraint_are_uniform():
     assert caps[0] == 0
 
 
+def test_periodic_coordinates_wrap_on_the_slice_line():
+    """All coordinates periodic and L* = -inf: no candidate ever leaves the
+    (wrapped) box, so stepping out runs to its cap on both sides and every
+    slice step costs exactly 2 * max_stepout + 1 evaluations; the chains
+    still sample the uniform distribution on the torus."""
+    d, k, steps, cap = 3, 1500, 4, 8
+    pb = oracle.toy_problem(d)
+    assert pb.set_periodic(range(d)) == 0b111
+    surv = oracle.initial_points(1, 500, d)
+    surv_l = pb.loglike(surv)
+    chol = np.ascontiguousarray(np.linalg.cholesky(np.cov(surv.T)))
+    new_u, new_l = np.zeros((k, d)), np.zeros(k)
+    caps = np.zeros(1, dtype=np.int32)
+    ev = oracle.lib().or_evolve(pb.c, 4, 7, 0, k, oracle._ptr(surv), oracle._ptr(surv_l), 500,
+                                oracle._ptr(chol), -np.inf, steps, cap, 64,
+                                oracle._ptr(new_u), oracle._ptr(new_l), oracle._ptr(caps))
+    assert ev == k * steps * (2 * cap + 1)
+    assert np.all((new_u >= 0.0) & (new_u <= 1.0))
+    for i in range(d):
+        assert stats.kstest(new_u[:, i], "uniform").pvalue > 1e-3
+    # without wrapping the box stops stepping out early
+    pb.set_periodic(())
+    ev2 = oracle.lib().or_evolve(pb.c, 4, 7, 0, k, oracle._ptr(surv), oracle._ptr(surv_l), 500,
+                                 oracle._ptr(chol), -np.inf, steps, cap, 64,
+                                 oracle._ptr(new_u), oracle._ptr(new_l), oracle._ptr(caps))
+    assert ev2 < ev
+
+
+def test_gw_likelihood_is_periodic_in_the_wrapped_parameters():
+    """phi_c (period 2 pi), psi (period pi: F+ and Fx are unchanged under
+    psi -> psi + pi) and RA (period 2 pi) with their full-period uniform
+    priors: log L takes the same value on opposite faces of the unit cube, which
+    is what makes wrapping these coordinates exact."""
+    w = gi.workload("c1", N=513)
+    pb, th = oracle.make_problem(w)
+    order = [p for p in range(gi.NPARAM) if pb.kind[p] != gi.PRIOR_FIXED]
+    u = gi.unit_cube(31, 12, pb.dim)
+    for p in (gi.P_PHIC, gi.P_PSI, gi.P_RA):
+        i = order.index(p)
+        a, b = u.copy(), u.copy()
+        a[:, i], b[:, i] = 0.0, 1.0
+        la, lb = pb.loglike(a), pb.loglike(b)
+        assert np.max(np.abs(la - lb) / np.maximum(1.0, np.abs(la))) < 1e-9, p
+    # and not in a non-periodic one (the chirp mass)
+    i = order.index(gi.P_MC)
+    a, b = u.copy(), u.copy()
+    a[:, i], b[:, i] = 0.0, 1.0
+    assert np.max(np.abs(pb.loglike(a) - pb.loglike(b))) > 1.0
+
+
 def test_chains_sample_the_constrained_prior():
     """Toy Gaussian with L > L*: the constrained prior is uniform in the
     ellipsoid x^T P x < r*^2, so (x^T P x / r*^2)^(d/2) ~ U(0, 1)."""
