@@ -637,6 +637,63 @@ def run_scaling_study(args):
               flush=True)
 
 
+def run_calibration(args):
+    """Evidence calibration (paper Sec. 4 leaves its validation open): on the
+    c1 workload, log Z over sampler seeds on the same data against the
+    replicate error dlogZ, for 5, 10 and 20 slice steps per dimension; and the
+    log Bayes factor of noise-only data against that of the SNR-20 injection."""
+    import torch
+    import paper_2509_24949_gb300 as g
+    from paper_2509_24949_gb300 import _build
+    if not _build.up_to_date():
+        _build.build()
+    prec = g.NS_MIXED if args.precision == "mixed" else g.NS_FP64
+    stream = torch.cuda.Stream()
+    seeds = 12
+    for spd in (5, 10, 20):
+        z, dz, secs = [], [], []
+        for i in range(seeds):
+            w = gi.workload("c1")
+            w.steps_per_dim = spd
+            w.seed_sampler += 1000 * (i + 1)
+            sp, th = g.make_analysis(w, precision=prec, stream=stream.cuda_stream)
+            t0 = time.perf_counter()
+            sp.run()
+            r = sp.result(samples=False)
+            secs.append(time.perf_counter() - t0)
+            sp.close()
+            z.append(r["logZ"])
+            dz.append(r["dlogZ"])
+        z = np.array(z)
+        print(json.dumps({"study": "log Z scatter over sampler seeds vs dlogZ", "workload": "c1",
+                          "precision": args.precision, "steps_per_dim": spd, "seeds": seeds,
+                          "mean_logZ": float(z.mean()), "sd_logZ": float(z.std(ddof=1)),
+                          "mean_dlogZ": float(np.mean(dz)), "ratio_sd_to_dlogZ": float(z.std(ddof=1) / np.mean(dz)),
+                          "mean_seconds": float(np.mean(secs))}), flush=True)
+    # noise only: the same detectors and noise, no signal
+    for label, snr_scale in (("noise only", 0.0), ("injection SNR 20", 1.0)):
+        w = gi.workload("c1")
+        probe, th = g.make_analysis(w, precision=g.NS_FP64, n_live=2, k=1, stream=stream.cuda_stream)
+        data = snr_scale * probe.waveform(th)
+        probe.close()
+        data = data + gi.noise(w.seed_noise, np.tile(gi.psd_analytic(w.freqs()), (w.n_det, 1)), w.df)
+        sp = g.sampler_for_workload(w, data=data, precision=prec, stream=stream.cuda_stream)
+        sp.run()
+        r = sp.result(samples=False)
+        sp.close()
+        print(json.dumps({"study": "log Bayes factor against noise", "workload": "c1", "data": label,
+                          "precision": args.precision, "logZ": r["logZ"], "dlogZ": r["dlogZ"],
+                          "rho2_over_2": float(probe_snr2(g, w, th, stream) / 2) if snr_scale else 0.0}),
+              flush=True)
+
+
+def probe_snr2(g, w, th, stream):
+    sp = g.sampler_for_workload(w, data=None, precision=g.NS_FP64, n_live=2, k=1, stream=stream.cuda_stream)
+    v = sp.snr2(th)
+    sp.close()
+    return v
+
+
 def run_profile_case(args):
     """A few iterations of one workload and form, untimed, for profiler captures
     of its kernels (e.g. ncu -k regex:k_slice -s <warm-up launches> -c 1)."""
@@ -679,6 +736,8 @@ def main():
     ap.add_argument("--profile-case", default=None,
                     help="workload (c0..c4): run --steps untimed iterations for a profiler capture")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--calibration", action="store_true",
+                    help="log Z scatter over seeds vs dlogZ (5, 10, 20 steps per dim) and noise-only log BF (c1)")
     ap.add_argument("--scaling-study", action="store_true",
                     help="whole-run time against n_live (k = n/2) and against k at n = 1000 (c1)")
     ap.add_argument("--n-live", type=int, default=0)
@@ -694,6 +753,9 @@ def main():
         return
     if args.scaling_study:
         run_scaling_study(args)
+        return
+    if args.calibration:
+        run_calibration(args)
         return
     if args.impl == "reference":
         run_reference(args)
