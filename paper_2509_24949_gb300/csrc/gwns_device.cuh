@@ -745,11 +745,6 @@ __device__ __forceinline__ double warp_max(double v) {
 // accumulators. The only per-bin table is the weighted data.
 constexpr int TK = 6;
 
-// Prefetch of the cache line holding *p into L1 (no register result).
-__device__ __forceinline__ void prefetch_l1(const void *p) {
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
-}
-
 // Position of bin j in the pair-tile order of the weighted data: at step i of
 // a tile, lanes read consecutive float4s (bins i, i + 1 of their tiles).
 __device__ __forceinline__ int tile_pos2(int j, int lg) {
@@ -838,26 +833,7 @@ __device__ __forceinline__ void tile_bins(const Tables &T, int lg, int np, const
 #pragma unroll
             for (int d = 0; d < NDET; d++) pr[c][d] = pim[c][d] = 0.f;
         const size_t gb = (size_t)g << (lg + 5);
-        // the weighted data of the chunk two steps ahead are prefetched into L1,
-        // so that each chunk's loads do not wait for L2
-#pragma unroll
-        for (int q0 = 0; q0 < 8; q0 += 4)
-            if (q0 < nmax)
-#pragma unroll
-                for (int d = 0; d < NDET; d++) {
-                    const size_t base = ((size_t)d * np + gb) >> 1;
-                    prefetch_l1(wt4 + base + (q0 << 4) + lane);
-                    prefetch_l1(wt4 + base + (q0 << 4) + 32 + lane);
-                }
         for (int q = 0; q < nmax; q += 4) {
-            if (q + 8 < nmax) {
-#pragma unroll
-                for (int d = 0; d < NDET; d++) {
-                    const size_t base = ((size_t)d * np + gb) >> 1;
-                    prefetch_l1(wt4 + base + ((q + 8) << 4) + lane);
-                    prefetch_l1(wt4 + base + ((q + 8) << 4) + 32 + lane);
-                }
-            }
             float4 w[NDET][2];
 #pragma unroll
             for (int d = 0; d < NDET; d++) {
