@@ -57,8 +57,14 @@ def initial_state(problem, n_live: int, seed: int, nthreads: Optional[int] = Non
 def survivor_cholesky(surv_u: np.ndarray) -> np.ndarray:
     """Cholesky factor of the survivors' covariance (unbiased, 1/(m-1)),
     jittered by 1e-12 tr(Sigma)/d on the diagonal; diag(sqrt(Sigma_ii)) if the
-    factorisation fails."""
+    factorisation fails. A single survivor (k = n - 1) has no sample
+    covariance: the unit cube's prior covariance I/12 stands in (reading; the
+    paper deletes half the population)."""
     m, d = surv_u.shape
+    if m < 2:
+        sigma = np.eye(d) / 12.0
+        sigma = sigma + 1e-12 * np.trace(sigma) / d * np.eye(d)
+        return np.linalg.cholesky(sigma)
     mu = surv_u.mean(axis=0)
     xc = surv_u - mu
     sigma = xc.T @ xc / (m - 1)

@@ -419,8 +419,11 @@ __device__ void cov_chol_body(const Model &M, const StepArgs &A) {
         __syncthreads();
     }
     if ((int)threadIdx.x < npair) {
-        cov[pi * d + pj] = acc / (m - 1);
-        cov[pj * d + pi] = acc / (m - 1);
+        // a single survivor (k = n - 1) has no sample covariance: the unit
+        // cube's prior covariance I/12 stands in
+        const double v = m >= 2 ? acc / (m - 1) : (pi == pj ? 1.0 / 12.0 : 0.0);
+        cov[pi * d + pj] = v;
+        cov[pj * d + pi] = v;
     }
     if (threadIdx.x == 0 && A.active) *A.active = A.k;     // chains of the coming slice update
     __syncthreads();

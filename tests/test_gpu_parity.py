@@ -297,6 +297,31 @@ def test_errors(gw):
         assert e.value.code == -3
 
 
+@pytest.mark.parametrize("n_live,k", [(2, 1), (40, 39), (4096, 2048)])
+def test_population_extremes_match_oracle(gw, n_live, k):
+    """The smallest population (2 live points, 1 deleted), one survivor per
+    iteration (k = n - 1) and the largest population the one-CTA sort takes
+    (4096): iterations match the oracle's."""
+    w, pb, sp, st = _ns_pair(gw, "c0", n_live, k)
+    with sp:
+        for it in range(2):
+            ons.iterate(pb, st, k, w.steps_per_dim * pb.dim, w.seed_sampler)
+            sp.step(k)
+            gu, gl = sp.live()
+            assert np.max(np.abs(gu - st.live_u)) < 1e-9, it
+            assert np.max(np.abs(gl - st.live_logl) / np.maximum(1, np.abs(st.live_logl))) < 1e-8
+            s = sp.stats()
+            assert s["logZ"] == pytest.approx(st.logZ, rel=1e-9, abs=1e-9)
+            assert s["evals"] == st.evals and s["status"] == 0
+
+
+def test_population_above_the_limit_is_refused(gw):
+    w, pb, th = problem("c0")
+    with pytest.raises(gw.GWNSError) as e:
+        sampler_from(gw, pb, 0, n_live=4097)
+    assert e.value.code == -1
+
+
 # ---------------------------------------------------------- relative binning
 @pytest.mark.parametrize("precision", [0, 1])
 def test_relative_binning_parity(gw, precision):

@@ -378,6 +378,19 @@ def test_gw_likelihood_is_periodic_in_the_wrapped_parameters():
     assert np.max(np.abs(pb.loglike(a) - pb.loglike(b))) > 1.0
 
 
+def test_survivor_covariance():
+    """L L^T is numpy's unbiased sample covariance (up to the 1e-12 tr/d
+    jitter); a single survivor falls back to the unit cube's covariance I/12."""
+    rng = np.random.default_rng(5)
+    surv = rng.uniform(size=(37, 5))
+    L = ons.survivor_cholesky(surv)
+    want = np.cov(surv.T)
+    assert np.allclose(L @ L.T, want + 1e-12 * np.trace(want) / 5 * np.eye(5), rtol=1e-12, atol=1e-15)
+    assert np.allclose(np.tril(L), L)
+    L1 = ons.survivor_cholesky(surv[:1])
+    assert np.allclose(L1 @ L1.T, np.eye(5) / 12.0, rtol=1e-10)
+
+
 def test_chains_sample_the_constrained_prior():
     """Toy Gaussian with L > L*: the constrained prior is uniform in the
     ellipsoid x^T P x < r*^2, so (x^T P x / r*^2)^(d/2) ~ U(0, 1)."""
