@@ -694,6 +694,41 @@ def probe_snr2(g, w, th, stream):
     return v
 
 
+def run_kernel_study(args):
+    """Slice sampling against the random-walk (acceptance-walk) inner kernel on
+    the c1 workload: time to log Z, evaluations and log Z over sampler seeds."""
+    import torch
+    import paper_2509_24949_gb300 as g
+    from paper_2509_24949_gb300 import _build
+    if not _build.up_to_date():
+        _build.build()
+    prec = g.NS_MIXED if args.precision == "mixed" else g.NS_FP64
+    stream = torch.cuda.Stream()
+    seeds = 8
+    for kname, kern in (("slice", g.NS_KERNEL_SLICE), ("walk", g.NS_KERNEL_WALK)):
+        z, dz, secs, evs, its = [], [], [], [], []
+        for i in range(seeds):
+            w = gi.workload("c1")
+            w.seed_sampler += 1000 * (i + 1)
+            sp, th = g.make_analysis(w, precision=prec, stream=stream.cuda_stream, kernel=kern)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            it = sp.run()
+            r = sp.result(samples=False)
+            secs.append(time.perf_counter() - t0)
+            evs.append(sp.stats()["evals"])
+            its.append(it)
+            sp.close()
+            z.append(r["logZ"])
+            dz.append(r["dlogZ"])
+        z = np.array(z)
+        print(json.dumps({"study": "inner kernel", "workload": "c1", "precision": args.precision,
+                          "kernel": kname, "seeds": seeds, "mean_seconds": float(np.mean(secs)),
+                          "mean_iterations": float(np.mean(its)), "mean_evals": float(np.mean(evs)),
+                          "evals_per_s": float(np.sum(evs) / np.sum(secs)), "mean_logZ": float(z.mean()),
+                          "sd_logZ": float(z.std(ddof=1)), "mean_dlogZ": float(np.mean(dz))}), flush=True)
+
+
 def run_profile_case(args):
     """A few iterations of one workload and form, untimed, for profiler captures
     of its kernels (e.g. ncu -k regex:k_slice -s <warm-up launches> -c 1)."""
@@ -736,6 +771,8 @@ def main():
     ap.add_argument("--profile-case", default=None,
                     help="workload (c0..c4): run --steps untimed iterations for a profiler capture")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--kernel-study", action="store_true",
+                    help="slice sampling vs the random-walk inner kernel on c1 (time, evaluations, log Z)")
     ap.add_argument("--calibration", action="store_true",
                     help="log Z scatter over seeds vs dlogZ (5, 10, 20 steps per dim) and noise-only log BF (c1)")
     ap.add_argument("--scaling-study", action="store_true",
@@ -756,6 +793,9 @@ def main():
         return
     if args.calibration:
         run_calibration(args)
+        return
+    if args.kernel_study:
+        run_kernel_study(args)
         return
     if args.impl == "reference":
         run_reference(args)

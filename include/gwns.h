@@ -57,6 +57,9 @@ enum {
 };
 
 enum { NS_PRIOR_FIXED = 0, NS_PRIOR_UNIFORM = 1, NS_PRIOR_VOLUME = 2 };
+
+/* Inner kernels of the update (ns_options.kernel). */
+enum { NS_KERNEL_SLICE = 0, NS_KERNEL_WALK = 1 };
 enum { NS_FP64 = 0, NS_MIXED = 1 };
 enum { NS_MODEL_GW = 0, NS_MODEL_TOY = 1 };
 
@@ -132,6 +135,11 @@ typedef struct {
     double dlogz_stop;   /* stop when log(Z + X Lmax) - log Z < this [0.1] */
     uint64_t seed;       /* Philox key */
     void *stream;        /* cudaStream_t to run on [NULL: library-owned stream] */
+    int kernel;          /* inner kernel of the update: NS_KERNEL_SLICE (slice sampling along
+                            hit-and-run directions, paper Sec. 2) or NS_KERNEL_WALK (constrained
+                            random walk of adaptive length, the acceptance-walk variant the
+                            paper compares against, Sec. 3) [NS_KERNEL_SLICE] */
+    double walk_scale;   /* NS_KERNEL_WALK: proposal y = x + walk_scale L z [2.38/sqrt(d)] */
     unsigned periodic;   /* bit p set (p = NS_MC..NS_SINDEC): parameter p is periodic over
                             its prior range (phi_c, psi, RA with their full-period uniform
                             priors): its unit-cube coordinate wraps mod 1 on the slice line

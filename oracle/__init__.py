@@ -101,6 +101,12 @@ def lib():
                                     dp, dp, ctypes.c_int, dp, ctypes.c_double, ctypes.c_int,
                                     ctypes.c_int, ctypes.c_int, dp, dp, dp]
             L.or_evolve.restype = ctypes.c_longlong
+            L.or_evolve_walk.argtypes = [P, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int,
+                                         dp, dp, ctypes.c_int, dp, ctypes.c_double, ctypes.c_int,
+                                         ctypes.c_double, dp, dp, dp]
+            L.or_evolve_walk.restype = ctypes.c_longlong
+            L.or_walk_next.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_longlong]
+            L.or_walk_next.restype = ctypes.c_int
             L.or_max_threads.argtypes = []; L.or_max_threads.restype = ctypes.c_int
             L.or_rb_edges.argtypes = [P, ctypes.c_int, dp]; L.or_rb_edges.restype = ctypes.c_int
             L.or_rb_summary.argtypes = [P, dp, dp, ctypes.c_int] + [dp] * 6

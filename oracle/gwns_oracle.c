@@ -505,6 +505,88 @@ static void evolve_chain(const or_problem *pb, uint64_t seed, uint32_t iter, int
     out_logl[chain] = lx;
 }
 
+/* Constrained random walk (the acceptance-walk alternative to slice sampling
+ * as an inner kernel): from a uniformly chosen survivor, `walk` proposals
+ * y = x + scale L z (z ~ N(0, I) from the draws of proposal p, L the
+ * Cholesky factor of the survivors' covariance) are accepted when inside the
+ * prior box (periodic coordinates wrapped) and above L*, otherwise the walk
+ * stays. A uniform prior restricted to L > L* is the walk's stationary law
+ * (symmetric proposal, rejection outside the constraint) for any fixed walk
+ * length; the length adapts between iterations only (or_walk_next). Adds the
+ * accepted moves to *accepted. */
+static void evolve_walk(const or_problem *pb, uint64_t seed, uint32_t iter, int chain, int d,
+                        const double *surv_u, const double *surv_logl, int m, const double *chol,
+                        double lstar, int walk, double scale, double *out_u,
+                        double *out_logl, long long *evals, long long *accepted)
+{
+    double x[OR_MAXD], y[OR_MAXD], z[OR_MAXD];
+    uint32_t w[4];
+    draw(seed, 0u, STEP_START, (uint32_t)chain, iter, w);
+    int idx = (int)(or_u01(w[0], w[1]) * m);
+    if (idx >= m) idx = m - 1;
+    for (int i = 0; i < d; i++) x[i] = surv_u[(size_t)idx * d + i];
+    double lx = surv_logl[idx], ly;
+    long long acc_moves = 0;
+    for (int p = 0; p < walk; p++) {
+        for (int q = 0; 2 * q < d; q++) {
+            draw(seed, (uint32_t)q, (uint32_t)p, (uint32_t)chain, iter, w);
+            double u1 = or_u01(w[0], w[1]), u2 = or_u01(w[2], w[3]);
+            double r = sqrt(-2.0 * log(u1));
+            z[2 * q] = r * cos(2.0 * OR_PI * u2);
+            if (2 * q + 1 < d) z[2 * q + 1] = r * sin(2.0 * OR_PI * u2);
+        }
+        for (int i = 0; i < d; i++) {
+            double acc = 0.0;
+            for (int j = 0; j <= i; j++) acc += chol[i * d + j] * z[j];
+            y[i] = x[i] + acc * scale;
+            if ((pb->periodic >> i) & 1u) y[i] -= floor(y[i]);
+        }
+        if (in_slice(pb, d, y, lstar, &ly, evals)) {
+            for (int i = 0; i < d; i++) x[i] = y[i];
+            lx = ly;
+            acc_moves++;
+        }
+    }
+    *accepted += acc_moves;
+    for (int i = 0; i < d; i++) out_u[(size_t)chain * d + i] = x[i];
+    out_logl[chain] = lx;
+}
+
+/* The k walks of one iteration; *accepted receives their accepted moves. */
+long long or_evolve_walk(const or_problem *pb, int nthreads, uint64_t seed, uint32_t iter, int k,
+                         const double *surv_u, const double *surv_logl, int m, const double *chol,
+                         double lstar, int walk, double scale, double *out_u, double *out_logl,
+                         long long *accepted)
+{
+    int d = or_dim(pb);
+    long long total = 0, acc = 0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : total, acc) num_threads(nthreads > 0 ? nthreads : 1)
+#endif
+    for (int c = 0; c < k; c++) {
+        long long ev = 0, a = 0;
+        evolve_walk(pb, seed, iter, c, d, surv_u, surv_logl, m, chol, lstar, walk, scale, out_u,
+                    out_logl, &ev, &a);
+        total += ev;
+        acc += a;
+    }
+    *accepted = acc;
+    return total;
+}
+
+/* Walk length of the next iteration, as in bilby's acceptance walk: scaled so
+ * that a walk would make `target` accepted moves at this iteration's
+ * acceptance (accepted moves over k walks of length walk), kept within
+ * [target, 64 target]. */
+int or_walk_next(int walk, int target, int k, long long accepted)
+{
+    if (accepted <= 0) return 64 * target;
+    double t = ceil(((double)walk * (double)target) * (double)k / (double)accepted);
+    if (t < (double)target) t = (double)target;
+    if (t > 64.0 * (double)target) t = 64.0 * (double)target;
+    return (int)t;
+}
+
 /* Evolve the k chains of one iteration (chains are independent; OpenMP over
  * chains does not change any result). Returns the total number of likelihood
  * evaluations; caps receives the number of steps that hit the shrink cap. */

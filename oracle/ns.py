@@ -43,6 +43,7 @@ class NSState:
     it: int = 0
     evals: int = 0
     caps: int = 0
+    walk_len: int = 0       # random-walk kernel: proposals per walk this iteration (0: not set yet)
     dead_u: List[np.ndarray] = dataclasses.field(default_factory=list)
     dead_logl: List[np.ndarray] = dataclasses.field(default_factory=list)
     dead_logw: List[np.ndarray] = dataclasses.field(default_factory=list)
@@ -75,8 +76,15 @@ def survivor_cholesky(surv_u: np.ndarray) -> np.ndarray:
         return np.diag(np.sqrt(np.maximum(np.diag(sigma), 0.0)))
 
 
+def walk_scale_default(d: int) -> float:
+    """Random-walk proposal scale on top of the survivors' Cholesky factor:
+    2.38 / sqrt(d) (Roberts, Gelman and Gilks 1997)."""
+    return 2.38 / math.sqrt(d)
+
+
 def iterate(problem, st: NSState, k: int, steps: int, seed: int, *, max_stepout: int = 64,
-            max_shrink: int = 64, nthreads: Optional[int] = None) -> dict:
+            max_shrink: int = 64, nthreads: Optional[int] = None, kernel: str = "slice",
+            walk_scale: Optional[float] = None) -> dict:
     """One nested-sampling iteration in place on st. Returns its details."""
     n, d = st.live_u.shape
     order = np.argsort(st.live_logl, kind="stable")       # ascending, ties by index
@@ -101,9 +109,21 @@ def iterate(problem, st: NSState, k: int, steps: int, seed: int, *, max_stepout:
     new_logl = np.zeros(k)
     caps = np.zeros(1, dtype=np.int32)
     nt = nthreads if nthreads else lib().or_max_threads()
-    ev = lib().or_evolve(problem.c, nt, seed, st.it, k, _ptr(surv_u), _ptr(surv_logl),
-                         n - k, _ptr(chol), lstar, steps, max_stepout, max_shrink,
-                         _ptr(new_u), _ptr(new_logl), _ptr(caps))
+    if kernel == "walk":
+        # walks of fixed length within the iteration (first: 2 x the target of
+        # `steps` accepted moves), rescaled between iterations
+        scale = walk_scale if walk_scale else walk_scale_default(d)
+        if st.walk_len == 0:
+            st.walk_len = 2 * steps
+        acc = np.zeros(1, dtype=np.int64)
+        ev = lib().or_evolve_walk(problem.c, nt, seed, st.it, k, _ptr(surv_u), _ptr(surv_logl),
+                                  n - k, _ptr(chol), lstar, st.walk_len, scale,
+                                  _ptr(new_u), _ptr(new_logl), _ptr(acc))
+        st.walk_len = int(lib().or_walk_next(st.walk_len, steps, k, int(acc[0])))
+    else:
+        ev = lib().or_evolve(problem.c, nt, seed, st.it, k, _ptr(surv_u), _ptr(surv_logl),
+                             n - k, _ptr(chol), lstar, steps, max_stepout, max_shrink,
+                             _ptr(new_u), _ptr(new_logl), _ptr(caps))
     st.live_u[dead] = new_u
     st.live_logl[dead] = new_logl
     st.evals += int(ev)
@@ -157,12 +177,13 @@ def finalize(st: NSState, seed: int, replicates: int = 200) -> dict:
 
 def run(problem, *, n_live: int, k: int, steps: int, seed: int, dlogz: float = 0.1,
         max_iter: int = 100000, max_stepout: int = 64, max_shrink: int = 64,
-        nthreads: Optional[int] = None, replicates: int = 200) -> dict:
+        nthreads: Optional[int] = None, replicates: int = 200, kernel: str = "slice",
+        walk_scale: Optional[float] = None) -> dict:
     """Full nested-sampling run; returns the finalize() dict plus counters."""
     st = initial_state(problem, n_live, seed, nthreads)
     while st.it < max_iter:
         iterate(problem, st, k, steps, seed, max_stepout=max_stepout, max_shrink=max_shrink,
-                nthreads=nthreads)
+                nthreads=nthreads, kernel=kernel, walk_scale=walk_scale)
         if remaining_fraction(st) < dlogz:
             break
     res = finalize(st, seed, replicates)

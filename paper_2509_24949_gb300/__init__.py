@@ -21,6 +21,7 @@ _LIB = None
 NS_OK = 0
 NS_FP64, NS_MIXED = 0, 1
 NS_MODEL_GW, NS_MODEL_TOY = 0, 1
+NS_KERNEL_SLICE, NS_KERNEL_WALK = 0, 1
 NPARAM = 11
 NS_MAX_DET = 4
 NOALLOC_MAX_POINTS = 4096
@@ -59,7 +60,8 @@ class _Options(ctypes.Structure):
                 ("model", ctypes.c_int), ("toy_dim", ctypes.c_int),
                 ("warps_per_point", ctypes.c_int), ("slots", ctypes.c_int),
                 ("dlogz_stop", ctypes.c_double),
-                ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p), ("periodic", ctypes.c_uint)]
+                ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p), ("kernel", ctypes.c_int),
+                ("walk_scale", ctypes.c_double), ("periodic", ctypes.c_uint)]
 
 
 class _Samples(ctypes.Structure):
@@ -172,7 +174,7 @@ class Sampler:
                  pos=None, xarm=None, yarm=None, ideal=False, n_live=100, k=0, steps_per_dim=5,
                  precision=NS_FP64, no_cutoff=False, max_stepout=0, max_shrink=0,
                  model=NS_MODEL_GW, toy_dim=0, warps_per_point=0, slots=0, dlogz_stop=0.1, seed=0,
-                 stream=None, coarse_bins=0, theta_fid=None, periodic=()):
+                 stream=None, coarse_bins=0, theta_fid=None, periodic=(), kernel=0, walk_scale=0.0):
         """periodic: parameter indices (NS_* order; toy model: unit-cube
         coordinates) whose coordinates wrap mod 1 on the slice line."""
         L = lib()
@@ -212,7 +214,8 @@ class Sampler:
             self.n_det, self.N = 0, 0
         opt = _Options(n_live, k, steps_per_dim, precision, int(bool(no_cutoff)), max_stepout,
                        max_shrink, model, toy_dim, warps_per_point, slots, dlogz_stop, seed,
-                       None if stream is None else int(stream), sum(1 << int(p) for p in set(periodic)))
+                       None if stream is None else int(stream), int(kernel), float(walk_scale),
+                       sum(1 << int(p) for p in set(periodic)))
         ctx = ctypes.c_void_p()
         _check(L.ns_init(ctypes.byref(ctx), ctypes.byref(pr), ctypes.byref(dt), ctypes.byref(ps),
                          ctypes.byref(gr), ctypes.byref(opt)), "ns_init")

@@ -237,6 +237,8 @@ StepArgs step_args(ns_ctx *c, int k) {
     A.depth = choose_slots(c);
     A.tail = c->n_sm;
     A.tail_coop = c->n_sm;
+    A.kernel = c->kernel;
+    A.walk_scale = c->walk_scale;
     return A;
 }
 
@@ -414,6 +416,8 @@ int ns_init(ns_ctx **out, const ns_prior *prior, const ns_data *data, const ns_p
     c->slots = o->slots;
     c->dlogz = o->dlogz_stop > 0.0 ? o->dlogz_stop : 0.1;
     c->seed = o->seed;
+    if (o->kernel != NS_KERNEL_SLICE && o->kernel != NS_KERNEL_WALK) { delete c; return NS_ERR_INVALID_ARG; }
+    c->kernel = o->kernel;
     if (o->stream) {
         c->stream = (cudaStream_t)o->stream;
     } else {
@@ -482,6 +486,7 @@ int ns_init(ns_ctx **out, const ns_prior *prior, const ns_data *data, const ns_p
     }
     c->d = M.dim;
     c->steps = (o->steps_per_dim ? o->steps_per_dim : 5) * M.dim;
+    c->walk_scale = o->walk_scale > 0.0 ? o->walk_scale : 2.38 / std::sqrt((double)M.dim);
     const size_t N = M.N, nd = M.n_det, nn = nd * N;
     if ((rc = dalloc(&c->d_re, nn)) || (rc = dalloc(&c->d_im, nn)) || (rc = dalloc(&c->d_psd, nn)) ||
         (rc = dalloc(&c->basis64, NB * N)) || (rc = dalloc(&c->f64, N)) || (rc = dalloc(&c->prefix, nn)) ||
@@ -538,6 +543,8 @@ int ns_init(ns_ctx **out, const ns_prior *prior, const ns_data *data, const ns_p
     s0.logX = 0.0;
     s0.lstar = -INFINITY;
     s0.evals = (unsigned long long)c->n;
+    s0.walk_len = 2 * c->steps;     // random walk: first length twice the target of accepted moves
+    s0.walk_acc = 0;
     *c->h_state = s0;
     e = cudaMemcpyAsync(c->state, c->h_state, sizeof(RunState), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = launch_init_live(M, c->seed, c->n, c->live_u, c->stream);

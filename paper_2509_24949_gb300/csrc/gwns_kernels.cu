@@ -482,6 +482,18 @@ __device__ void finish_body(const StepArgs &A) {
         st->remaining = tot - lz;
         st->done = (st->remaining < A.dlogz_stop) ? 1 : 0;
         st->iter += 1;
+        if (A.kernel == 1) {
+            // next walk length: A.steps accepted moves per walk at this
+            // iteration's acceptance, within [A.steps, 64 A.steps]
+            const unsigned long long acc = st->walk_acc;
+            double t = 64.0 * A.steps;
+            if (acc > 0) {
+                t = ceil(((double)st->walk_len * (double)A.steps) * (double)A.k / (double)acc);
+                t = fmin(fmax(t, (double)A.steps), 64.0 * A.steps);
+            }
+            st->walk_len = (int)t;
+            st->walk_acc = 0;
+        }
     }
 }
 

@@ -23,6 +23,9 @@ struct RunState {
     long long iter;
     int done;
     int status;
+    int walk_len;                    // random-walk kernel: proposals per walk this iteration
+    int pad_;
+    unsigned long long walk_acc;     // random-walk kernel: accepted moves of this iteration's walks
 };
 
 struct StepArgs {
@@ -42,6 +45,8 @@ struct StepArgs {
     int depth;            // candidates planned per round while many chains run
     int tail;             // below this many running chains, plan as many as there are warps
     int tail_coop;        // FP64, below this many: base depth, spare warps share the candidates' bins
+    int kernel;           // 0 slice sampling, 1 random walk
+    double walk_scale;    // random walk: y = x + walk_scale L z
 };
 
 // One analysis' iteration arguments, for the multi-analysis launches.

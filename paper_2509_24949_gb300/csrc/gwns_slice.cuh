@@ -139,8 +139,8 @@ cudaError_t eval_launch(const Model &M, const Tables &T, int warps, const double
 // Evaluations the sequential order never reaches are discarded. The trajectory,
 // the evaluation count and every draw are those of the sequential algorithm;
 // the slots only shorten the chain's critical path.
-enum { PH_NEWSTEP = 0, PH_OUT = 1, PH_SHRINK = 2, PH_DONE = 3 };
-enum { KIND_L = 0, KIND_R = 1, KIND_SH = 2 };
+enum { PH_NEWSTEP = 0, PH_OUT = 1, PH_SHRINK = 2, PH_DONE = 3, PH_WALK = 4 };
+enum { KIND_L = 0, KIND_R = 1, KIND_SH = 2, KIND_W = 3 };
 constexpr int CACHE_MAX = 16;
 
 struct Chain {
@@ -342,6 +342,86 @@ __device__ int chain_plan(const Model &M, const StepArgs &A, const Chain &c, int
     return ns;
 }
 
+// ------------------------------------------------------------ random walk
+// The random-walk inner kernel (acceptance walk): from the chain's start point,
+// walk_len proposals y = x + scale L z_p, z_p ~ N(0, I) from the draws of
+// proposal p (the slice directions' slots with p in place of the step); a
+// proposal inside the prior box (periodic coordinates wrapped) and above L*
+// is accepted. The walk length is fixed within an iteration and rescaled
+// between iterations (k_finish). Speculation: the proposals after the current
+// one are evaluated from the current point, as if it were rejected; an
+// acceptance discards them. c.s counts accepted moves, c.nsh the proposal.
+__device__ __forceinline__ double walk_disp(const StepArgs &A, const Chain &c, int chain, uint32_t iter, int p,
+                                            int lane, int d) {
+    double z = 0.0;
+    if (lane < d) {
+        const uint4 w = draw(A.seed, (uint32_t)(lane >> 1), (uint32_t)p, (uint32_t)chain, iter);
+        const double u1 = u01(w.x, w.y), u2 = u01(w.z, w.w);
+        const double r = sqrt(-2.0 * log(u1));
+        double sn, cs;
+        sincos(TWO_PI_D * u2, &sn, &cs);
+        z = (lane & 1) ? r * sn : r * cs;
+    }
+    double acc = 0.0;
+    for (int j = 0; j < d; j++) {
+        const double zj = __shfl_sync(0xffffffffu, z, j);
+        if (j <= lane) acc = __dadd_rn(acc, __dmul_rn(c.lrow[j], zj));
+    }
+    return __dmul_rn(acc, A.walk_scale);
+}
+
+__device__ __forceinline__ double walk_y(const Model &M, const Chain &c, double disp, int lane, int d) {
+    if (lane >= d) return 0.5;
+    double y = __dadd_rn(c.x, disp);
+    if ((M.periodic >> lane) & 1u) y = __dsub_rn(y, floor(y));
+    return y;
+}
+
+static __device__ void walk_run(const Model &M, const StepArgs &A, Chain &c, int chain, uint32_t iter,
+                                double lstar, int walk_len) {
+    const int lane = threadIdx.x & 31, d = M.dim;
+    for (int guard = 0; guard < (1 << 22); guard++) {
+        if (c.phase == PH_DONE) return;
+        if (c.nsh >= walk_len) { c.phase = PH_DONE; return; }
+        const double y = walk_y(M, c, walk_disp(A, c, chain, iter, c.nsh, lane, d), lane, d);
+        if (!warp_inbox(y, lane, d)) { c.nsh++; continue; }
+        const int ci = cache_find(c, KIND_W, c.nsh);
+        if (ci < 0) return;
+        const double val = c.cval[ci];
+        c.evals++;
+        c.bins += (unsigned long long)c.cbins[ci];
+        cache_drop(c, ci);
+        if (val > lstar) {
+            c.x = y;
+            c.lx = val;
+            c.s++;
+            cache_purge(c, KIND_W);
+        }
+        c.nsh++;
+    }
+    c.phase = PH_DONE;
+}
+
+template <int S>
+__device__ int walk_plan(const Model &M, const StepArgs &A, const Chain &c, int chain, uint32_t iter,
+                         double (*ysh)[MAXD], int *pk, int *pidx, int depth, int walk_len) {
+    const int lane = threadIdx.x & 31, d = M.dim;
+    const int room = CACHE_MAX - c.ncache;
+    const int lim = depth < S ? depth : S;
+    const int cap = lim < room ? lim : room;
+    int ns = 0;
+    for (int p = c.nsh; p < c.nsh + S && p < walk_len && ns < cap; p++) {
+        const double y = walk_y(M, c, walk_disp(A, c, chain, iter, p, lane, d), lane, d);
+        if (warp_inbox(y, lane, d) && cache_find(c, KIND_W, p) < 0) {
+            if (lane < d) ysh[ns][lane] = y;
+            pk[ns] = KIND_W;
+            pidx[ns] = p;
+            ns++;
+        }
+    }
+    return ns;
+}
+
 template <int PREC, int NDET, int S, int W = S>
 __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, const int chain) {
     __shared__ Coef coef[S];
@@ -355,6 +435,7 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, d = M.dim;
     const uint32_t iter = (uint32_t)A.state->iter;
     const double lstar = A.state->lstar;
+    const int walk_len = A.state->walk_len;
     Chain c;
     int pk[S], pidx[S];
     if (warp == 0) {
@@ -367,12 +448,14 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
         c.lx = A.live_logl[src];
         for (int j = 0; j < MAXD; j++) c.lrow[j] = (lane < d && j < d) ? A.chol[lane * d + j] : 0.0;
         c.e = 0.0; c.a = 0.0; c.b = 0.0;
-        c.s = 0; c.phase = PH_NEWSTEP; c.nl = c.nr = c.nsh = 0; c.caps = 0; c.evals = 0; c.bins = 0;
+        c.s = 0; c.phase = A.kernel == 1 ? PH_WALK : PH_NEWSTEP; c.nl = c.nr = c.nsh = 0; c.caps = 0;
+        c.evals = 0; c.bins = 0;
         c.left_done = c.right_done = 0; c.ncache = 0;
     }
     for (;;) {
         if (warp == 0) {
-            chain_run(M, A, c, chain, iter, lstar);
+            if (A.kernel == 1) walk_run(M, A, c, chain, iter, lstar, walk_len);
+            else chain_run(M, A, c, chain, iter, lstar);
             // plan the base depth while many chains run; the stragglers of the
             // update (fewer running chains than the tail threshold) use every warp
             // FP64 among the very last chains keeps the base depth and gives the
@@ -386,7 +469,9 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
                     tail = 2;
                 }
             }
-            int ns = (c.phase == PH_DONE) ? 0 : chain_plan<S>(M, A, c, chain, iter, ysh, pk, pidx, depth);
+            int ns = (c.phase == PH_DONE) ? 0
+                   : A.kernel == 1 ? walk_plan<S>(M, A, c, chain, iter, ysh, pk, pidx, depth, walk_len)
+                                   : chain_plan<S>(M, A, c, chain, iter, ysh, pk, pidx, depth);
             if (ns == 0 && c.phase != PH_DONE) {
                 // cannot happen with the bounds above; end the chain at its
                 // current (in-slice) point and flag the run state
@@ -585,6 +670,7 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
             atomicAdd(&A.state->evals, (unsigned long long)c.evals);
             atomicAdd(&A.state->caps, (unsigned long long)c.caps);
             atomicAdd(&A.state->point_bins, c.bins);
+            if (A.kernel == 1) atomicAdd(&A.state->walk_acc, (unsigned long long)c.s);
         }
     }
 }

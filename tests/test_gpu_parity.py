@@ -242,6 +242,41 @@ def test_toy_evidence_gpu(gw):
     assert hits >= 5
 
 
+@pytest.mark.parametrize("slots", [1, 2, 4])
+@pytest.mark.parametrize("name,n_live,k,iters", [("c0", 200, 100, 3), ("c1", 120, 60, 2)])
+def test_walk_iterations_match_oracle(gw, name, n_live, k, iters, slots):
+    """The random-walk inner kernel: same proposals, same accepted moves, same
+    walk-length adaptation on both sides."""
+    w, pb, th = problem(name)
+    st = ons.initial_state(pb, n_live, w.seed_sampler)
+    with sampler_from(gw, pb, 0, n_live=n_live, k=k, steps_per_dim=w.steps_per_dim, seed=w.seed_sampler,
+                      slots=slots, kernel=gw.NS_KERNEL_WALK) as sp:
+        for it in range(iters):
+            ons.iterate(pb, st, k, w.steps_per_dim * pb.dim, w.seed_sampler, kernel="walk")
+            sp.step(k)
+            gu, gl = sp.live()
+            s = sp.stats()
+            assert np.max(np.abs(gu - st.live_u)) < 1e-9, it
+            assert np.max(np.abs(gl - st.live_logl) / np.maximum(1, np.abs(st.live_logl))) < 1e-8
+            assert s["evals"] == st.evals and s["status"] == 0
+            assert s["logZ"] == pytest.approx(st.logZ, rel=1e-9, abs=1e-9)
+
+
+def test_walk_toy_run_matches_oracle_run(gw):
+    """Whole toy run with the random walk: same iterations and evidence as the
+    oracle's, and log Z within 3 dlogZ of the analytic -d ln 20."""
+    d = 4
+    pb = oracle.toy_problem(d)
+    ref = ons.run(pb, n_live=100, k=50, steps=5 * d, seed=43, kernel="walk")
+    with gw.Sampler(model=gw.NS_MODEL_TOY, toy_dim=d, n_live=100, k=50, steps_per_dim=5, seed=43,
+                    kernel=gw.NS_KERNEL_WALK) as sp:
+        it = sp.run()
+        r = sp.result()
+    assert it == ref["iterations"]
+    assert r["logZ"] == pytest.approx(ref["logZ"], rel=1e-10, abs=1e-10)
+    assert abs(r["logZ"] + d * math.log(20.0)) < 3 * r["dlogZ"] + 0.05
+
+
 def test_toy_run_matches_oracle_run(gw):
     """Whole toy run: same seed, same draws, same evidence and replicates."""
     d = 4

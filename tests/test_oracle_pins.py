@@ -378,6 +378,64 @@ def test_gw_likelihood_is_periodic_in_the_wrapped_parameters():
     assert np.max(np.abs(pb.loglike(a) - pb.loglike(b))) > 1.0
 
 
+def _walk(pb, surv, lstar, k, walk, seed=3, scale=None):
+    d = pb.dim
+    surv_l = pb.loglike(surv)
+    chol = np.ascontiguousarray(np.linalg.cholesky(np.cov(surv.T)))
+    new_u, new_l = np.zeros((k, d)), np.zeros(k)
+    acc = np.zeros(1, dtype=np.int64)
+    ev = oracle.lib().or_evolve_walk(pb.c, 4, seed, 0, k, oracle._ptr(surv), oracle._ptr(surv_l), len(surv),
+                                     oracle._ptr(chol), lstar, walk, scale or ons.walk_scale_default(d),
+                                     oracle._ptr(new_u), oracle._ptr(new_l), oracle._ptr(acc))
+    return new_u, new_l, ev, int(acc[0])
+
+
+def test_random_walk_without_constraint_is_uniform():
+    """L* = -inf: the walk is a Metropolis chain for the uniform prior (symmetric
+    proposals, rejection outside the box), so it stays uniform; every in-box
+    proposal is evaluated and accepted, so evaluations = accepted moves."""
+    d, k, walk = 3, 2000, 6
+    pb = oracle.toy_problem(d)
+    surv = oracle.initial_points(1, 500, d)
+    u, l, ev, acc = _walk(pb, surv, -np.inf, k, walk)
+    for i in range(d):
+        assert stats.kstest(u[:, i], "uniform").pvalue > 1e-3
+    assert ev == acc and 0 < acc < k * walk
+
+
+def test_walk_length_rule():
+    """Between iterations the walk length is rescaled towards the target of
+    accepted moves per walk: walk * target * k / accepted, rounded up and kept
+    within [target, 64 target]."""
+    L = oracle.lib()
+    assert L.or_walk_next(110, 55, 500, 500 * 55) == 110          # on target
+    assert L.or_walk_next(110, 55, 500, 500 * 55 // 2) == 220     # half the moves: twice the length
+    assert L.or_walk_next(110, 55, 500, 10 ** 9) == 55            # floor
+    assert L.or_walk_next(110, 55, 500, 1) == 64 * 55             # ceiling
+    assert L.or_walk_next(110, 55, 500, 0) == 64 * 55
+    assert L.or_walk_next(100, 55, 3, 7) == math.ceil(100 * 55 * 3 / 7)
+
+
+def test_random_walk_samples_the_constrained_prior():
+    """Toy Gaussian with L > L*: the walk leaves the uniform law on the
+    ellipsoid x^T P x < r*^2 invariant, so (x^T P x / r*^2)^(d/2) ~ U(0, 1)."""
+    d = 4
+    pb = oracle.toy_problem(d)
+    prec = np.linalg.inv(gi.toy_covariance(d, gi.TOY_RHO))
+    r2 = 9.0
+    lstar = -0.5 * r2 + pb.toy_lognorm
+    # survivors: uniform in the ellipsoid (rejection from the prior box)
+    u = oracle.initial_points(2, 200000, d)
+    x = gi.TOY_BOX[0] + (gi.TOY_BOX[1] - gi.TOY_BOX[0]) * u
+    q = np.einsum("ni,ij,nj->n", x, prec, x)
+    surv = np.ascontiguousarray(u[q < r2][:400])
+    new_u, new_l, ev, acc = _walk(pb, surv, lstar, 3000, 6 * d)
+    x = gi.TOY_BOX[0] + (gi.TOY_BOX[1] - gi.TOY_BOX[0]) * new_u
+    q = np.einsum("ni,ij,nj->n", x, prec, x)
+    assert np.all(q < r2) and np.all(new_l > lstar)
+    assert stats.kstest((q / r2) ** (d / 2), "uniform").pvalue > 1e-3
+
+
 def test_survivor_covariance():
     """L L^T is numpy's unbiased sample covariance (up to the 1e-12 tr/d
     jitter); a single survivor falls back to the unit cube's covariance I/12."""
