@@ -52,7 +52,11 @@ K_SLICE_FP64_C1_DRAM_BYTES = 340992   # re-captured after the kernel changes
 
 
 def fp64_flops_per_point_bin(n_det: int) -> float:
-    return 2.0 * (8 + 32 + 12 * n_det)
+    """Algorithmic FP64 work of one point-bin, in flops (2 per FMA-equivalent):
+    the phase as 8 basis FMAs, one sine/cosine pair (32 FMA-equivalents,
+    measured by instruction count), and per detector the complex product with
+    the weighted data and one Horner step of the detector rotation (8)."""
+    return 2.0 * (8 + 32 + 8 * n_det)
 
 
 def world():

@@ -499,56 +499,31 @@ __device__ __forceinline__ void bins_fp64(const Tables &T, int N, double f0, dou
 #pragma unroll
     for (int m = 0; m < NB; m++) a[m] = c.a[m];
     const double c0 = c.c0;
-    double rr[NDET], ri[NDET], pr[NDET], pi_[NDET];
+    // the thread's bins j_n = tid + n stride, n = 0 .. nb-1; the detector factor
+    // exp(2 pi i f_j tau_d) = R_d rho_d^n with R_d at j_0 and rho_d the rotation
+    // over one stride, so Z_d = R_d sum_n (w_dj exp(i Psi_j)) rho_d^n, evaluated
+    // by Horner's rule from the last bin down: per bin and detector a complex
+    // product and a Horner step (8 FP64) instead of advancing, applying and
+    // accumulating a running phasor (12)
+    const int nb = tid <= c.jcut ? (c.jcut - tid) / stride + 1 : 0;
+    double pr[NDET], pi_[NDET], hr[NDET], hi[NDET];
 #pragma unroll
     for (int d = 0; d < NDET; d++) {
-        zr[d] = 0.0; zi[d] = 0.0;
-        if (tid <= c.jcut) {
-            sincos_bf(TWO_PI_D * (f0 + tid * df) * c.tau[d], ri[d], rr[d]);
-            if (PRE_ROT) {
-                pr[d] = c.rot_re[d];
-                pi_[d] = c.rot_im[d];
-                for (int q = 0; q < rot_sq; q++) {
-                    const double re = pr[d] * pr[d] - pi_[d] * pi_[d];
-                    pi_[d] = 2.0 * pr[d] * pi_[d];
-                    pr[d] = re;
-                }
-            } else {
-                sincos(TWO_PI_D * (stride * df) * c.tau[d], &pi_[d], &pr[d]);
+        hr[d] = 0.0; hi[d] = 0.0;
+        if (PRE_ROT) {
+            pr[d] = c.rot_re[d];
+            pi_[d] = c.rot_im[d];
+            for (int q = 0; q < rot_sq; q++) {
+                const double re = pr[d] * pr[d] - pi_[d] * pi_[d];
+                pi_[d] = 2.0 * pr[d] * pi_[d];
+                pr[d] = re;
             }
+        } else if (nb > 0) {
+            sincos_bf(TWO_PI_D * (stride * df) * c.tau[d], pi_[d], pr[d]);
         }
     }
-    int j = tid;
-    // two bins per step (j and j + stride): independent phase and sincos chains
-    for (; j + stride <= c.jcut; j += 2 * stride) {
-        const int j2 = j + stride;
-        double psi = c0, psi2 = c0;
-#pragma unroll
-        for (int m = 0; m < NB; m++) {
-            psi = fma(a[m], __ldg(T.basis64 + (size_t)m * N + j), psi);
-            psi2 = fma(a[m], __ldg(T.basis64 + (size_t)m * N + j2), psi2);
-        }
-        double s, co, s2, co2;
-        sincos_bf(psi, s, co);
-        sincos_bf(psi2, s2, co2);
-#pragma unroll
-        for (int d = 0; d < NDET; d++) {
-            // rotation of the second bin, then both contributions
-            const double r2r = rr[d] * pr[d] - ri[d] * pi_[d];
-            const double r2i = rr[d] * pi_[d] + ri[d] * pr[d];
-            const double er = co * rr[d] - s * ri[d], ei = co * ri[d] + s * rr[d];
-            const double er2 = co2 * r2r - s2 * r2i, ei2 = co2 * r2i + s2 * r2r;
-            const double2 w = __ldg(T.w64 + (size_t)d * N + j);
-            const double2 w2 = __ldg(T.w64 + (size_t)d * N + j2);
-            zr[d] = fma(w.x, er, fma(-w.y, ei, zr[d]));
-            zi[d] = fma(w.x, ei, fma(w.y, er, zi[d]));
-            zr[d] = fma(w2.x, er2, fma(-w2.y, ei2, zr[d]));
-            zi[d] = fma(w2.x, ei2, fma(w2.y, er2, zi[d]));
-            rr[d] = r2r * pr[d] - r2i * pi_[d];
-            ri[d] = r2r * pi_[d] + r2i * pr[d];
-        }
-    }
-    if (j <= c.jcut) {
+    for (int n = nb - 1; n >= 0; n--) {
+        const int j = tid + n * stride;
         double psi = c0;
 #pragma unroll
         for (int m = 0; m < NB; m++) psi = fma(a[m], __ldg(T.basis64 + (size_t)m * N + j), psi);
@@ -556,11 +531,22 @@ __device__ __forceinline__ void bins_fp64(const Tables &T, int N, double f0, dou
         sincos_bf(psi, s, co);
 #pragma unroll
         for (int d = 0; d < NDET; d++) {
-            const double er = co * rr[d] - s * ri[d];
-            const double ei = co * ri[d] + s * rr[d];
             const double2 w = __ldg(T.w64 + (size_t)d * N + j);
-            zr[d] = fma(w.x, er, fma(-w.y, ei, zr[d]));
-            zi[d] = fma(w.x, ei, fma(w.y, er, zi[d]));
+            const double cr = fma(w.x, co, -w.y * s), ci = fma(w.x, s, w.y * co);
+            const double h2r = fma(hr[d], pr[d], fma(-hi[d], pi_[d], cr));
+            const double h2i = fma(hr[d], pi_[d], fma(hi[d], pr[d], ci));
+            hr[d] = h2r;
+            hi[d] = h2i;
+        }
+    }
+#pragma unroll
+    for (int d = 0; d < NDET; d++) {
+        zr[d] = 0.0; zi[d] = 0.0;
+        if (nb > 0) {
+            double rs, rc;
+            sincos_bf(TWO_PI_D * (f0 + tid * df) * c.tau[d], rs, rc);
+            zr[d] = rc * hr[d] - rs * hi[d];
+            zi[d] = rc * hi[d] + rs * hr[d];
         }
     }
 }

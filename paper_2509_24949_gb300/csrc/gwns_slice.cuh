@@ -200,34 +200,43 @@ __device__ __forceinline__ double shrink_t(const StepArgs &A, double a, double b
     return __dadd_rn(a, __dmul_rn(__dsub_rn(b, a), u01(w.x, w.y)));
 }
 
+// Hit-and-run direction of slice step s: lane i < d gets coordinate i of
+// L z / |z|, z ~ N(0, I) by Box-Muller (two normals per draw); lrow is the
+// lane's row of the Cholesky factor L.
+__device__ __forceinline__ double slice_direction(const StepArgs &A, const double *lrow, int chain, uint32_t iter,
+                                                  int s, int lane, int d) {
+    double z = 0.0;
+    if (lane < d) {
+        const uint4 w = draw(A.seed, (uint32_t)(lane >> 1), (uint32_t)s, (uint32_t)chain, iter);
+        const double u1 = u01(w.x, w.y), u2 = u01(w.z, w.w);
+        const double r = sqrt(-2.0 * log(u1));
+        double sn, cs;
+        sincos(TWO_PI_D * u2, &sn, &cs);
+        z = (lane & 1) ? r * sn : r * cs;
+    }
+    const double nz = sqrt(warp_sum(z * z));
+    double acc = 0.0;
+    for (int j = 0; j < d; j++) {
+        const double zj = __shfl_sync(0xffffffffu, z, j);
+        if (j <= lane) acc = __dadd_rn(acc, __dmul_rn(lrow[j], zj));
+    }
+    return (lane < d) ? acc / nz : 0.0;
+}
+
 // Apply every transition that needs no new evaluation: new steps (direction and
 // bracket draws), cap and prior-box outcomes, and results already in the cache.
 // Returns when the next transition needs an evaluation not in the cache, or the
 // chain is done.
 static __device__ void chain_run(const Model &M, const StepArgs &A, Chain &c, int chain, uint32_t iter,
-                          double lstar) {
+                                 double lstar, const double *e_pre, int e_pre_step) {
     const int lane = threadIdx.x & 31, d = M.dim;
     for (int guard = 0; guard < (1 << 22); guard++) {
         if (c.phase == PH_DONE) return;
         if (c.phase == PH_NEWSTEP) {
             if (c.s >= A.steps) { c.phase = PH_DONE; return; }
-            // direction e = L z / |z|, z ~ N(0, I) by Box-Muller, two normals per draw
-            double z = 0.0;
-            if (lane < d) {
-                const uint4 w = draw(A.seed, (uint32_t)(lane >> 1), (uint32_t)c.s, (uint32_t)chain, iter);
-                const double u1 = u01(w.x, w.y), u2 = u01(w.z, w.w);
-                const double r = sqrt(-2.0 * log(u1));
-                double sn, cs;
-                sincos(TWO_PI_D * u2, &sn, &cs);
-                z = (lane & 1) ? r * sn : r * cs;
-            }
-            const double nz = sqrt(warp_sum(z * z));
-            double acc = 0.0;
-            for (int j = 0; j < d; j++) {
-                const double zj = __shfl_sync(0xffffffffu, z, j);
-                if (j <= lane) acc = __dadd_rn(acc, __dmul_rn(c.lrow[j], zj));
-            }
-            c.e = (lane < d) ? acc / nz : 0.0;
+            // direction (computed ahead by a spare warp when it could be)
+            if (e_pre_step == c.s) c.e = (lane < d) ? e_pre[lane] : 0.0;
+            else c.e = slice_direction(A, c.lrow, chain, iter, c.s, lane, d);
             const uint4 w = draw(A.seed, SLOT_OFFSET, (uint32_t)c.s, (uint32_t)chain, iter);
             const double r = u01(w.x, w.y);
             c.a = -r;
@@ -429,6 +438,8 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
     __shared__ double ysh[S][MAXD];
     __shared__ double lval[S];
     __shared__ int nslot, tailmode;
+    __shared__ double e_next[MAXD];         // direction of slice step e_next_step, computed ahead
+    __shared__ int e_next_step, cur_step;
     __shared__ int jc[S];
     __shared__ double part[W][S][NDET][2];
     if (chain >= A.k) return;
@@ -451,11 +462,12 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
         c.s = 0; c.phase = A.kernel == 1 ? PH_WALK : PH_NEWSTEP; c.nl = c.nr = c.nsh = 0; c.caps = 0;
         c.evals = 0; c.bins = 0;
         c.left_done = c.right_done = 0; c.ncache = 0;
+        if (lane == 0) e_next_step = -1;
     }
     for (;;) {
         if (warp == 0) {
             if (A.kernel == 1) walk_run(M, A, c, chain, iter, lstar, walk_len);
-            else chain_run(M, A, c, chain, iter, lstar);
+            else chain_run(M, A, c, chain, iter, lstar, e_next, e_next_step);
             // plan the base depth while many chains run; the stragglers of the
             // update (fewer running chains than the tail threshold) use every warp
             // FP64 among the very last chains keeps the base depth and gives the
@@ -478,7 +490,7 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
                 c.phase = PH_DONE;
                 if (lane == 0) atomicOr(&A.state->status, 1);
             }
-            if (lane == 0) { nslot = ns; tailmode = tail; }
+            if (lane == 0) { nslot = ns; tailmode = tail; cur_step = c.s; }
         }
         __syncthreads();
         const int ns = nslot;
@@ -496,6 +508,17 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
                 const int cnt = ns - 4 * grp < 4 ? ns - 4 * grp : 4;
                 point_coef_group(M, T, ysh[4 * grp], MAXD, &coef[4 * grp], cnt, PREC == 0 ? 32 : 0,
                                  1 + (warp & 1));
+            } else if (warp == W - 1 && A.kernel == 0) {
+                // a warp without coefficients computes the next slice step's direction
+                const int s1 = cur_step + 1;
+                if (s1 < A.steps && e_next_step != s1) {
+                    double lrow[MAXD];
+                    for (int j = 0; j < MAXD; j++) lrow[j] = (lane < d && j < d) ? A.chol[lane * d + j] : 0.0;
+                    const double e1 = slice_direction(A, lrow, chain, iter, s1, lane, d);
+                    if (lane < d) e_next[lane] = e1;
+                    __syncwarp();
+                    if (lane == 0) e_next_step = s1;
+                }
             }
             __syncthreads();
             if (warp == 0) point_coef_join(M, T, coef, ns);
