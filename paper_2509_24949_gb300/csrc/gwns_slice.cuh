@@ -153,6 +153,7 @@ struct Chain {
     int ncache;
     int ckind[CACHE_MAX], cidx[CACHE_MAX], cbins[CACHE_MAX];
     double cval[CACHE_MAX];
+    double cy[CACHE_MAX];      // random walk: the evaluated proposal (lane's coordinate)
 };
 
 // Lane i's coordinate of the candidate x + t e (lanes >= d: 0.5, inside the
@@ -180,6 +181,7 @@ __device__ __forceinline__ void cache_drop(Chain &c, int i) {
     c.cidx[i] = c.cidx[c.ncache];
     c.cval[i] = c.cval[c.ncache];
     c.cbins[i] = c.cbins[c.ncache];
+    c.cy[i] = c.cy[c.ncache];
 }
 
 // Drop every cached result of one stepping-out side (once that side has ended,
@@ -392,10 +394,18 @@ static __device__ void walk_run(const Model &M, const StepArgs &A, Chain &c, int
     for (int guard = 0; guard < (1 << 22); guard++) {
         if (c.phase == PH_DONE) return;
         if (c.nsh >= walk_len) { c.phase = PH_DONE; return; }
-        const double y = walk_y(M, c, walk_disp(A, c, chain, iter, c.nsh, lane, d), lane, d);
-        if (!warp_inbox(y, lane, d)) { c.nsh++; continue; }
+        // an evaluated proposal comes with its point (planned from the current
+        // point: the cache is emptied at every acceptance); otherwise compute
+        // it, skip it outside the box, or wait for its evaluation
         const int ci = cache_find(c, KIND_W, c.nsh);
-        if (ci < 0) return;
+        double y;
+        if (ci >= 0) {
+            y = (lane < d) ? c.cy[ci] : 0.5;
+        } else {
+            y = walk_y(M, c, walk_disp(A, c, chain, iter, c.nsh, lane, d), lane, d);
+            if (!warp_inbox(y, lane, d)) { c.nsh++; continue; }
+            return;
+        }
         const double val = c.cval[ci];
         c.evals++;
         c.bins += (unsigned long long)c.cbins[ci];
@@ -420,8 +430,9 @@ __device__ int walk_plan(const Model &M, const StepArgs &A, const Chain &c, int 
     const int cap = lim < room ? lim : room;
     int ns = 0;
     for (int p = c.nsh; p < c.nsh + S && p < walk_len && ns < cap; p++) {
+        if (cache_find(c, KIND_W, p) >= 0) continue;
         const double y = walk_y(M, c, walk_disp(A, c, chain, iter, p, lane, d), lane, d);
-        if (warp_inbox(y, lane, d) && cache_find(c, KIND_W, p) < 0) {
+        if (warp_inbox(y, lane, d)) {
             if (lane < d) ysh[ns][lane] = y;
             pk[ns] = KIND_W;
             pidx[ns] = p;
@@ -679,6 +690,7 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
                 c.cidx[c.ncache] = pidx[sl];
                 c.cval[c.ncache] = lval[sl];
                 c.cbins[c.ncache] = coef[sl].jcut + 1;
+                c.cy[c.ncache] = (lane < d) ? ysh[sl][lane] : 0.5;
                 c.ncache++;
             }
         }
