@@ -216,6 +216,23 @@ def test_periodic_iterations_match_oracle(gw, slots):
             assert sp.stats()["evals"] == st.evals
 
 
+def test_bench_configuration_iteration_matches_oracle(gw):
+    """The benchmarked configuration itself (3 detectors, 4017 bins, 1000 live
+    points, 500 chains of 55 steps, FP64, the default slot rule and launch):
+    the live set after one iteration matches the oracle's."""
+    w, pb, th = problem("c1")
+    st = ons.initial_state(pb, w.n_live, w.seed_sampler)
+    with sampler_from(gw, pb, 0, n_live=w.n_live, k=w.k, steps_per_dim=w.steps_per_dim,
+                      seed=w.seed_sampler) as sp:
+        ons.iterate(pb, st, w.k, w.steps_per_dim * pb.dim, w.seed_sampler)
+        sp.step()
+        gu, gl = sp.live()
+        s = sp.stats()
+    assert np.max(np.abs(gu - st.live_u)) < 1e-9
+    assert np.max(np.abs(gl - st.live_logl) / np.maximum(1, np.abs(st.live_logl))) < 1e-8
+    assert s["evals"] == st.evals and s["status"] == 0
+
+
 def test_ns_step_host_dead_points(gw):
     w, pb, sp, st = _ns_pair(gw, "c0", 100, 50)
     k, d = 50, pb.dim
