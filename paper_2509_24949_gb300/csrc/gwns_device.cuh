@@ -169,22 +169,9 @@ __device__ __forceinline__ void prior_transform(const Model &M, const double *u,
 }
 
 // --------------------------------------------------------- point coefficients
-// Last grid index with f0 + j df <= fisco, in [-1, N-1]; the comparison uses the
-// same rounded frequency f0 + j*df as the tables.
-__device__ __forceinline__ int cutoff_index(const Model &M, double fisco) {
-    if (!M.cutoff) return M.N - 1;
-    double jf = floor((fisco - M.f0) / M.df);
-    if (jf < -1.0) return -1;
-    if (jf > (double)(M.N - 1)) return M.N - 1;
-    int j = (int)jf;
-    while (j + 1 <= M.N - 1 && __dadd_rn(M.f0, __dmul_rn((double)(j + 1), M.df)) <= fisco) j++;
-    while (j >= 0 && __dadd_rn(M.f0, __dmul_rn((double)j, M.df)) > fisco) j--;
-    return j;
-}
-
-// The same index from the grid's frequency table (f64[j] holds exactly the
-// rounded f0 + j*df compared above): a first guess by one multiplication, then
-// at most a step either way against the table.
+// Last grid index with f_j <= fisco, in [-1, N-1], from the grid's frequency
+// table (f64[j] holds the rounded f0 + j*df the tables use): a first guess by
+// one multiplication, then at most a few steps either way against the table.
 __device__ __forceinline__ int cutoff_index_tab(const Model &M, const double *f64, double fisco) {
     if (!M.cutoff) return M.N - 1;
     const double jf = floor((fisco - M.f0) * M.inv_df);

@@ -715,7 +715,6 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
 // 9.8 ms, c1 mixed 4.7 -> 3.4 ms, c4 mixed 631 -> 550 ms per slice update, in
 // spite of ~100 bytes of spills in the mixed tile loop.
 #define SLICE_MIN_BLOCKS(PREC, S) (16 / (S))
-#define SLICE_WIDE 1
 
 template <int PREC, int NDET, int S, int W = S>
 __global__ void __launch_bounds__(W * 32, SLICE_MIN_BLOCKS(PREC, W)) k_slice(Model M, Tables T, StepArgs A) {
@@ -729,7 +728,7 @@ cudaError_t slice_launch(const Model &M, const Tables &T, int slots, const StepA
     // as many per chain, so the update's last chains finish sooner (GB300,
     // 519,169 bins: 536 -> 467 ms per slice update; on 64,897 bins, where an
     // evaluation has a few tile groups, 15.2 -> 17.5 ms, hence the threshold)
-    if (PREC == 1 && slots == 4 && SLICE_WIDE && M.model == M_GW && M.coop && M.tlg && !M.rb &&
+    if (PREC == 1 && slots == 4 && M.model == M_GW && M.coop && M.tlg && !M.rb &&
         M.N >= 262144) {
         k_slice<PREC, NDET, 4, 8><<<A.k, 256, 0, s>>>(M, T, A);
         return cudaGetLastError();
