@@ -447,9 +447,12 @@ def test_autotune_keeps_the_trajectory(gw):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-def test_checkpoint_resume_is_bit_identical(gw, precision):
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_checkpoint_resume_is_bit_identical(gw, precision, kernel):
+    """A run resumed from a checkpoint continues bit-identically (for the
+    random walk this includes the adapted walk length)."""
     w, pb, th = problem("c0")
-    args = dict(n_live=100, k=50, steps_per_dim=w.steps_per_dim, seed=w.seed_sampler)
+    args = dict(n_live=100, k=50, steps_per_dim=w.steps_per_dim, seed=w.seed_sampler, kernel=kernel)
     with sampler_from(gw, pb, precision, **args) as a:
         for _ in range(3):
             a.step()
