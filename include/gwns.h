@@ -201,6 +201,14 @@ typedef struct {
  * Errors: CAPACITY (samples->count = entries needed), CUDA. */
 int ns_result(ns_ctx *ctx, double *logZ, double *dlogZ, ns_samples *samples);
 
+/* Summary statistics of the last ns_result call: the information
+ * H = sum_i p_i ln(L_i / Z) (p_i the posterior weights; sqrt(H / n) is the
+ * classic evidence-error estimate, Skilling 2006) and the Kish effective sample
+ * size (sum p_i)^2 / sum p_i^2 of the weighted samples (the ESS the paper
+ * reports, Sec. 4). Host pointers, either may be NULL.
+ * Errors: INVALID_ARG (no ns_result yet). */
+int ns_result_info(ns_ctx *ctx, double *H, double *ess);
+
 typedef struct {
     long long iterations;
     long long evals;        /* likelihood evaluations so far (initial draw included) */

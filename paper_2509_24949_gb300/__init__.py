@@ -119,6 +119,7 @@ def lib():
         L.ns_run.argtypes = [vp, ip, P(ip)]
         L.ns_result.argtypes = [vp, P(dp), P(dp), P(_Samples)]
         L.ns_get_stats.argtypes = [vp, P(_Stats)]
+        L.ns_result_info.argtypes = [vp, P(dp), P(dp)]
         L.ns_eval_lnl.argtypes = [vp, vp, ip, vp]
         L.ns_eval_lnl_host.argtypes = [vp, vp, ip, vp]
         L.ns_eval_lnl_theta.argtypes = [vp, vp, ip, vp]
@@ -279,7 +280,7 @@ class Sampler:
         lz, dlz = ctypes.c_double(), ctypes.c_double()
         if not samples:
             _check(lib().ns_result(self._ctx, ctypes.byref(lz), ctypes.byref(dlz), None), "ns_result")
-            return dict(logZ=lz.value, dlogZ=dlz.value)
+            return dict(logZ=lz.value, dlogZ=dlz.value, **self._info())
         st = self.stats()
         cap = st["n_dead"] + self.n_live
         u = np.zeros((cap, self.dim))
@@ -288,10 +289,15 @@ class Sampler:
         theta = np.zeros((cap, NPARAM)) if self.model == NS_MODEL_GW else None
         sm = _Samples(cap, 0, _ptr(theta), _ptr(u), _ptr(logl), _ptr(logw))
         _check(lib().ns_result(self._ctx, ctypes.byref(lz), ctypes.byref(dlz), ctypes.byref(sm)), "ns_result")
-        out = dict(logZ=lz.value, dlogZ=dlz.value, u=u, logl=logl, logw=logw, count=sm.count)
+        out = dict(logZ=lz.value, dlogZ=dlz.value, u=u, logl=logl, logw=logw, count=sm.count, **self._info())
         if theta is not None:
             out["theta"] = theta
         return out
+
+    def _info(self) -> dict:
+        h, e = ctypes.c_double(), ctypes.c_double()
+        _check(lib().ns_result_info(self._ctx, ctypes.byref(h), ctypes.byref(e)), "ns_result_info")
+        return dict(H=h.value, ess=e.value)
 
     # ---------------------------------------------------------- likelihood
     def eval_lnl(self, u, out=None):

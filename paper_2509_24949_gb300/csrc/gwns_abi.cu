@@ -639,6 +639,13 @@ int ns_get_stats(ns_ctx *c, ns_stats *st) {
     return NS_OK;
 }
 
+int ns_result_info(ns_ctx *c, double *H, double *ess) {
+    if (!c || !c->have_info) return NS_ERR_INVALID_ARG;
+    if (H) *H = c->info_H;
+    if (ess) *ess = c->info_ess;
+    return NS_OK;
+}
+
 int ns_result(ns_ctx *c, double *logZ, double *dlogZ, ns_samples *smp) {
     if (!c) return NS_ERR_INVALID_ARG;
     const long long total = c->n_dead + c->n;
@@ -661,6 +668,9 @@ int ns_result(ns_ctx *c, double *logZ, double *dlogZ, ns_samples *smp) {
     CK(cudaStreamSynchronize(c->stream));
     if (logZ) *logZ = lz;
     if (dlogZ) *dlogZ = out4[0];
+    c->info_H = out4[1];
+    c->info_ess = out4[2];
+    c->have_info = true;
     if (smp) {
         const long long nd = c->n_dead;
         const int d = c->d;

@@ -23,6 +23,8 @@ struct ns_ctx {
     int slots = 0;
     double dlogz = 0.1;
     uint64_t seed = 0;
+    double info_H = 0.0, info_ess = 0.0;   // of the last ns_result
+    bool have_info = false;
     int kernel = 0;            // NS_KERNEL_SLICE or NS_KERNEL_WALK
     double walk_scale = 0.0;
     cudaStream_t stream = nullptr;

@@ -305,6 +305,8 @@ def test_toy_run_matches_oracle_run(gw):
     assert it == ref["iterations"]
     assert r["logZ"] == pytest.approx(ref["logZ"], rel=1e-10, abs=1e-10)
     assert r["dlogZ"] == pytest.approx(ref["dlogZ"], rel=1e-8)
+    assert r["H"] == pytest.approx(ref["H"], rel=1e-9)
+    assert r["ess"] == pytest.approx(ref["ess"], rel=1e-9)
     assert np.max(np.abs(r["logl"] - ref["logl"])) < 1e-9
     assert np.max(np.abs(r["logw"] - ref["logw"])) < 1e-9
 
