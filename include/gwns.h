@@ -330,6 +330,10 @@ typedef struct {
     int slots;             /* slice-update slots per chain for every analysis [0: 4] */
     int max_iter;          /* iteration cap per analysis [100000] */
     void *stream;          /* cudaStream_t [NULL: server-owned] */
+    int max_chains;        /* admit while the running analyses' chains per iteration (their k)
+                              stay within this, the first always [0: 16 per SM, ~4 CTAs of
+                              chains per CTA slot]: past it the GPU is saturated and more
+                              analyses only lengthen each one's time to result */
 } ns_server_options;
 
 typedef struct {

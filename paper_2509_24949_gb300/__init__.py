@@ -80,7 +80,8 @@ class _Stats(ctypes.Structure):
 
 class _ServerOptions(ctypes.Structure):
     _fields_ = [("max_active", ctypes.c_int), ("mem_budget", ctypes.c_size_t), ("precision", ctypes.c_int),
-                ("slots", ctypes.c_int), ("max_iter", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("slots", ctypes.c_int), ("max_iter", ctypes.c_int), ("stream", ctypes.c_void_p),
+                ("max_chains", ctypes.c_int)]
 
 
 class _Request(ctypes.Structure):
@@ -418,9 +419,10 @@ def _fill_inputs(kind, lo, hi, data, psd, f0, df, pos, xarm, yarm, ideal, coarse
 class Server:
     """Continuous-batching server of many analyses (ns_server_* in gwns.h)."""
 
-    def __init__(self, *, max_active=16, mem_budget=0, precision=NS_MIXED, slots=0, max_iter=0, stream=None):
+    def __init__(self, *, max_active=16, mem_budget=0, precision=NS_MIXED, slots=0, max_iter=0, stream=None,
+                 max_chains=0):
         o = _ServerOptions(max_active, mem_budget, precision, slots, max_iter,
-                           None if stream is None else int(stream))
+                           None if stream is None else int(stream), max_chains)
         h = ctypes.c_void_p()
         _check(lib().ns_server_create(ctypes.byref(h), ctypes.byref(o)), "ns_server_create")
         self._h = h

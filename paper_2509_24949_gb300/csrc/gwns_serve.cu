@@ -62,6 +62,7 @@ struct ns_server {
     bool own_stream = false;
     uint64_t next_id = 1;
     size_t budget = 0, used = 0;
+    long long chains = 0;          // k of the running analyses
     std::deque<uint64_t> pending;
     std::vector<uint64_t> running;
     std::unordered_map<uint64_t, Request> reqs;
@@ -89,6 +90,7 @@ void release(ns_server *s, Request &r) {
         ns_free(r.ctx);
         r.ctx = nullptr;
         s->used -= r.st.footprint;
+        s->chains -= r.opts.k ? r.opts.k : r.opts.n_live / 2;
     }
 }
 
@@ -119,6 +121,7 @@ int admit(ns_server *s, Request &r) {
     r.ctx = c;
     r.d = c->d;
     s->used += r.st.footprint;
+    s->chains += r.opts.k ? r.opts.k : r.opts.n_live / 2;
     // the pending copies of the inputs are no longer needed
     std::vector<double>().swap(r.re);
     std::vector<double>().swap(r.im);
@@ -216,7 +219,7 @@ int ns_server_create(ns_server **out, const ns_server_options *o) {
     if (!out || !o) return NS_ERR_INVALID_ARG;
     *out = nullptr;
     if (o->precision != NS_FP64 && o->precision != NS_MIXED) return NS_ERR_INVALID_ARG;
-    if (o->max_active < 0 || o->max_iter < 0) return NS_ERR_INVALID_ARG;
+    if (o->max_active < 0 || o->max_iter < 0 || o->max_chains < 0) return NS_ERR_INVALID_ARG;
     if (o->slots != 0 && o->slots != 1 && o->slots != 2 && o->slots != 4 && o->slots != 8) return NS_ERR_INVALID_ARG;
     ns_server *s = new (std::nothrow) ns_server();
     if (!s) return NS_ERR_OOM;
@@ -224,6 +227,12 @@ int ns_server_create(ns_server **out, const ns_server_options *o) {
     if (s->o.max_active == 0) s->o.max_active = 16;
     if (s->o.slots == 0) s->o.slots = 4;
     if (s->o.max_iter == 0) s->o.max_iter = 100000;
+    if (s->o.max_chains == 0) {
+        int dev = 0, nsm = 152;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) nsm = 152;
+        s->o.max_chains = 16 * nsm;
+    }
     if (o->stream) {
         s->stream = (cudaStream_t)o->stream;
     } else {
@@ -302,6 +311,8 @@ int ns_server_tick(ns_server *s, int *n_running, int *n_pending) {
             continue;
         }
         if (s->used + r.st.footprint > s->budget) break;
+        const int kr = r.opts.k ? r.opts.k : r.opts.n_live / 2;
+        if (!s->running.empty() && s->chains + kr > s->o.max_chains) break;
         int rc = admit(s, r);
         s->pending.pop_front();
         if (rc) { r.st.state = rc; continue; }

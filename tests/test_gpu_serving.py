@@ -1,6 +1,6 @@
 """Serving: many analyses interleaved on one GPU give each the same result as
-alone; admission respects the slot count and the memory budget; requests can
-be cancelled. All on the GPU through the C ABI."""
+alone; admission respects the analysis count, the chain budget and the memory
+budget; requests can be cancelled. All on the GPU through the C ABI."""
 import numpy as np
 import pytest
 
@@ -91,6 +91,32 @@ def test_admission_by_slots_and_memory(gw):
         rid = srv.submit(**reqs[0][0])
         srv.tick()
         assert srv.poll(rid)["state"] == -4     # NS_ERR_OOM
+
+
+def test_admission_by_chain_budget(gw):
+    reqs = [_analysis(30 + i) for i in range(4)]          # k = 40 chains each
+    with gw.Server(precision=1, max_chains=100) as srv:
+        ids = [srv.submit(**r) for r, _ in reqs]
+        max_run = 0
+        while True:
+            r, p = srv.tick()
+            max_run = max(max_run, r)
+            assert r <= 2                                  # 3 x 40 > 100
+            if r == 0 and p == 0:
+                break
+        assert max_run == 2
+        assert all(srv.poll(i)["state"] == gw.NS_REQ_DONE for i in ids)
+    # an analysis larger than the budget still runs, alone
+    with gw.Server(precision=1, max_chains=30) as srv:
+        ids = [srv.submit(**r) for r, _ in reqs[:2]]
+        while True:
+            r, p = srv.tick()
+            assert r <= 1
+            if r == 0 and p == 0:
+                break
+        assert all(srv.poll(i)["state"] == gw.NS_REQ_DONE for i in ids)
+    with pytest.raises(gw.GWNSError):
+        gw.Server(precision=1, max_chains=-1)
 
 
 def test_cancel(gw):
