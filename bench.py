@@ -456,19 +456,40 @@ def run_reference(args):
 
 
 FP32_LANE_OPS = 152 * 128 * 2.070e9    # FP32 pipe: 128 lanes/clk/SM x 152 SMs x 2070 MHz
+SFU_LANE_OPS = 152 * 16 * 2.070e9      # MUFU (sin, cos): 16 lanes/clk/SM x 152 SMs x 2070 MHz
 
 
 def mixed_fp32_per_point_bin(n_det: int, tile: int) -> float:
     """FP32 instructions of the mixed form per point-bin (per-tile or per-flush
-    work not counted). Tiled form (tile > 0): C_1 x as an error-free product
-    (3), the Horner sum of C_2..C_6 (5), the reduction of C_1 x (2), x^2 (1);
-    per detector 4 (phase) + 2 (reduction) + 1 (scale) + 4 (complex MAC), the
-    sine/cosine pair on the MUFU pipe. Per-bin form: the double-float dot
-    product of 8 basis terms (12 each) and per detector the double-float delay
-    term, reduction and MAC (20)."""
+    work not counted). Tiles of 32 bins or more: x and x^2 (2), C_1 x as an
+    error-free product (3), the Horner sum of C_2..C_6 (5), the reduction of
+    C_1 x (2), detector 0's phase in radians (3) and complex MAC (4); per
+    further detector the product of the weighted data with detector 0's phasor
+    (4), one step of the Horner sum in its rotation (4) and an eighth of a
+    segment step (6). Shorter tiles: the common part (11) and per detector
+    4 (phase) + 2 (reduction) + 1 (scale) + 4 (complex MAC). Per-bin form
+    (tile 0): the double-float dot product of 8 basis terms (12 each) and per
+    detector the double-float delay term, reduction and MAC (20)."""
+    if tile >= 32:
+        return 19.0 + 8.75 * (n_det - 1)
     if tile:
         return 11.0 + 11.0 * n_det
     return 96.0 + 20.0 * n_det
+
+
+def mixed_mufu_per_point_bin(n_det: int, tile: int) -> float:
+    """MUFU instructions (sine, cosine) per point-bin: detector 0's pair on
+    tiles of 32 bins or more (the rotated detectors take one pair per tile),
+    otherwise a pair per detector."""
+    return 2.0 if tile >= 32 else 2.0 * n_det
+
+
+def mixed_roofline(point_bins: float, seconds: float, n_det: int, tile: int):
+    """Fraction of the binding pipe (FP32 or MUFU) the mixed form reaches: the
+    time the algorithmic instructions need on that pipe over the measured."""
+    t32 = point_bins * mixed_fp32_per_point_bin(n_det, tile) / FP32_LANE_OPS
+    tsfu = point_bins * mixed_mufu_per_point_bin(n_det, tile) / SFU_LANE_OPS
+    return (t32 / seconds, "FP32") if t32 >= tsfu else (tsfu / seconds, "SFU")
 
 
 def _timed_steps(sp, stream, max_steps):
@@ -525,8 +546,7 @@ def table_row(g, name, precision, stream, max_steps=100000, coarse=False):
         frac = pb * fp64_flops_per_point_bin(w.n_det) / (slice_ms / 1e3) / (FP64_PEAK_TFLOPS * 1e12)
         pipe = "FP64"
     else:
-        frac = pb * mixed_fp32_per_point_bin(w.n_det, st1["mixed_tile"]) / (slice_ms / 1e3) / FP32_LANE_OPS
-        pipe = "FP32"
+        frac, pipe = mixed_roofline(pb, slice_ms / 1e3, w.n_det, st1["mixed_tile"])
     return {"config": name + (" (1024 coarse bins)" if coarse else ""),
             "form": "fp64" if precision == g.NS_FP64 else "mixed", "iterations": it, "done": done,
             "evals": ev, "evals_per_s": ev / (sum(ms) / 1e3), "point_bins_per_s": pb / (sum(ms) / 1e3),
@@ -537,21 +557,36 @@ def table_row(g, name, precision, stream, max_steps=100000, coarse=False):
             "logZ": r["logZ"] if r else None, "dlogZ": r["dlogZ"] if r else None}
 
 
-def batch_eval_row(g, name, precision, stream, points=2048):
-    """Batched likelihood throughput (ns_eval_lnl on prior draws)."""
+def batch_eval_row(g, name, precision, stream, points=2048, reps=3):
+    """Batched likelihood throughput (ns_eval_lnl on prior draws): CUDA events
+    on the library's stream around `reps` launches after one warm-up; the
+    point-bins come from the library's own count of the bins each point read."""
     import torch
     w = gi.workload(name)
     sp, th = g.make_analysis(w, precision=precision, n_live=8, k=4, stream=stream.cuda_stream)
     u = torch.tensor(gi.unit_cube(99, points, w.dim), dtype=torch.float64, device="cuda")
-    sp.eval_lnl(u)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    sp.eval_lnl(u)
-    torch.cuda.synchronize()
-    t = time.perf_counter() - t0
+    out = torch.empty(points, dtype=torch.float64, device="cuda")
+    sp.eval_lnl(u, out)
+    st0 = sp.stats()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        a.record(stream)
+        for _ in range(reps):
+            g.lib().ns_eval_lnl(sp._ctx, u.data_ptr(), points, out.data_ptr())
+        b.record(stream)
+    b.synchronize()
+    t = a.elapsed_time(b) / 1e3
+    st1 = sp.stats()
     sp.close()
-    return {"config": name, "form": "fp64" if precision == g.NS_FP64 else "mixed", "batch_points": points,
-            "batch_evals_per_s": points / t}
+    pb = st1["batch_point_bins"] - st0["batch_point_bins"]
+    row = {"config": name, "form": "fp64" if precision == g.NS_FP64 else "mixed", "batch_points": points,
+           "batch_evals_per_s": points * reps / t, "point_bins_per_s": pb / t, "bins_per_eval": pb / (points * reps)}
+    if precision == g.NS_FP64:
+        row["frac"], row["pipe"] = pb * fp64_flops_per_point_bin(w.n_det) / t / (FP64_PEAK_TFLOPS * 1e12), "FP64"
+    else:
+        row["frac"], row["pipe"] = mixed_roofline(pb, t, w.n_det, st1["mixed_tile"])
+        row["mixed_tile"] = st1["mixed_tile"]
+    return row
 
 
 def oracle_rate(name: str, chains: int, steps_per_dim: int, target_s: float):
@@ -602,8 +637,9 @@ def run_table(args):
     for prec in (g.NS_FP64, g.NS_MIXED):
         rows.append(table_row(g, "c4", prec, stream, coarse=True))
     rows.append(table_row(g, "c4", g.NS_MIXED, stream, max_steps=2))
-    rows.append(batch_eval_row(g, "c4", g.NS_FP64, stream))
-    rows.append(batch_eval_row(g, "c4", g.NS_MIXED, stream))
+    for name in ("c2", "c4"):
+        rows.append(batch_eval_row(g, name, g.NS_FP64, stream, points=2048))
+        rows.append(batch_eval_row(g, name, g.NS_MIXED, stream, points=8192))
     if not args.no_oracle:
         for name, chains, spd in (("c0", 64, 5), ("c1", 64, 5), ("c2", 32, 2), ("c4", 16, 1)):
             rows.append(oracle_rate(name, chains, spd, 8.0))

@@ -228,6 +228,9 @@ typedef struct {
                                graph: select, evidence, covariance, slice update, finish */
     int mixed_tile;         /* mixed precision: bins per lane tile of the tiled form (grids fine
                                enough for its Taylor expansion), 0 for the per-bin form */
+    long long batch_evals;       /* points through the batched likelihood (ns_eval_lnl*, ns_init's
+                                    initial live set) */
+    long long batch_point_bins;  /* their sum of the bins each one read */
 } ns_stats;
 
 int ns_get_stats(ns_ctx *ctx, ns_stats *st);

@@ -172,7 +172,7 @@ int build_rb(ns_ctx *c) {
 }
 
 int eval_points(ns_ctx *c, const double *in, int is_theta, int m, double *logl) {
-    CK(launch_eval(c->M, c->T, c->precision, choose_warps(c), in, is_theta, m, logl, c->stream));
+    CK(launch_eval(c->M, c->T, c->precision, choose_warps(c), in, is_theta, m, logl, c->state, c->stream));
     return NS_OK;
 }
 
@@ -636,6 +636,8 @@ int ns_get_stats(ns_ctx *c, ns_stats *st) {
     st->status = s.status;
     for (int i = 0; i < 5; i++) st->kernel_ms[i] = c->timing ? c->kernel_ms[i] : -1.0;
     st->mixed_tile = c->M.tlg ? 1 << c->M.tlg : 0;
+    st->batch_evals = (long long)s.eval_points;
+    st->batch_point_bins = (long long)s.eval_point_bins;
     return NS_OK;
 }
 
@@ -865,7 +867,7 @@ int ns_autotune(ns_ctx *c, int trials, int *slots) {
 
 namespace {
 struct CkptHeader {
-    char magic[8];          // "GWNSCKP1"
+    char magic[8];          // "GWNSCKP2"
     int n, d;
     long long n_dead;
     RunState state;
@@ -880,7 +882,7 @@ int ns_checkpoint(ns_ctx *c, void *buf, size_t *len) {
     if (*len < need) { *len = need; return NS_ERR_CAPACITY; }
     CkptHeader h;
     std::memset(&h, 0, sizeof(h));
-    std::memcpy(h.magic, "GWNSCKP1", 8);
+    std::memcpy(h.magic, "GWNSCKP2", 8);
     h.n = c->n;
     h.d = c->d;
     h.n_dead = c->n_dead;
@@ -909,7 +911,7 @@ int ns_restore(ns_ctx *c, const void *buf, size_t len) {
     if (!c || !buf || len < sizeof(CkptHeader)) return NS_ERR_INVALID_ARG;
     CkptHeader h;
     std::memcpy(&h, buf, sizeof(h));
-    if (std::memcmp(h.magic, "GWNSCKP1", 8) != 0 || h.n != c->n || h.d != c->d || h.n_dead < 0)
+    if (std::memcmp(h.magic, "GWNSCKP2", 8) != 0 || h.n != c->n || h.d != c->d || h.n_dead < 0)
         return NS_ERR_INVALID_ARG;
     const size_t nl = (size_t)c->n, d = c->d, nd = (size_t)h.n_dead;
     if (len < sizeof(CkptHeader) + sizeof(double) * (nl * (d + 1) + nd * (d + 3))) return NS_ERR_INVALID_ARG;

@@ -115,6 +115,12 @@ struct CoefMixed {
     float c0h, c0l;
     float tauh[MAXDET], taul[MAXDET];
     float dtau[MAXDET];     // df tau_d: phase advance per bin [turns]
+    // tiled form, detectors d >= 1 against detector 0: beta_d = 2 pi df (tau_d - tau_0)
+    // [rad per bin], rho_d = exp(-i beta_d), eps8_d = exp(-8 i beta_d) - 1 (its real part
+    // -2 sin^2(4 beta_d) kept to full relative precision)
+    float beta[MAXDET];
+    float rho[MAXDET][2];
+    float eps8[MAXDET][2];
 };
 
 // ------------------------------------------------------------------ Philox
@@ -418,16 +424,30 @@ __device__ __forceinline__ void split_df(double x, float &h, float &l) {
 }
 
 // Mixed-precision coefficients (phase in turns), from lane-parallel
-// conversions; with fid, the differences from the fiducial point's.
+// conversions; with fid, the differences from the fiducial point's; with rot,
+// the rotation constants of the tiled form's long tiles too.
 __device__ __forceinline__ void coef_to_mixed_warp(const Coef &c, int n_det, double df, CoefMixed *m,
-                                                   const Coef *fid = nullptr) {
+                                                   const Coef *fid = nullptr, bool rot = false) {
     const int lane = threadIdx.x & 31;
     if (lane < NB) split_df((c.a[lane] - (fid ? fid->a[lane] : 0.0)) * INV_TWO_PI_D, m->ah[lane], m->al[lane]);
     else if (lane == NB) split_df((c.c0 - (fid ? fid->c0 : 0.0)) * INV_TWO_PI_D, m->c0h, m->c0l);
     else if (lane >= 16 && lane < 16 + n_det)
         split_df(c.tau[lane - 16] - (fid ? fid->tau[lane - 16] : 0.0), m->tauh[lane - 16], m->taul[lane - 16]);
-    else if (lane >= 24 && lane < 24 + n_det)
-        m->dtau[lane - 24] = __double2float_rn(df * (c.tau[lane - 24] - (fid ? fid->tau[lane - 24] : 0.0)));
+    else if (lane >= 24 && lane < 24 + n_det) {
+        const int d = lane - 24;
+        const double td = c.tau[d] - (fid ? fid->tau[d] : 0.0), t0 = c.tau[0] - (fid ? fid->tau[0] : 0.0);
+        m->dtau[d] = __double2float_rn(df * td);
+        if (!rot) return;
+        // the rotation of detector d's phase against detector 0's per bin, its
+        // unit step and eight-bin step (FP32 libm sine: within 2 ulp)
+        const float b = __double2float_rn(TWO_PI_D * df * (td - t0));
+        const float h1 = sinf(0.5f * b), h4 = sinf(4.0f * b);
+        m->beta[d] = b;
+        m->rho[d][0] = 1.0f - 2.0f * h1 * h1;
+        m->rho[d][1] = -sinf(b);
+        m->eps8[d][0] = -2.0f * h4 * h4;
+        m->eps8[d][1] = -sinf(8.0f * b);
+    }
 }
 
 // ------------------------------------------------------------ bin loops
@@ -706,17 +726,28 @@ __device__ __forceinline__ double warp_max(double v) {
 
 // Mixed form, tiled (fine grids). Lane l of a warp owns tile t = 32 g + l of
 // group g, the L bins j = tL + i about the centre c = tL + L/2 (x = i - L/2).
-// The phase in turns of bin j at detector d is
+// The phase of bin j at detector d, in turns, is
 //   [c0 + sum_m a_m B_m(f_c) + f_c tau_d] + sum_{k=1..TK} C_k x^k + x df tau_d,
 // C_k = sum_m a_m B_m^(k)(f_c) df^k / k!: the Taylor expansion of each basis
 // function about the tile centre, its remainder bounded on the host below 1e-8
 // rad when the tiled form is chosen. Per lane and tile, the anchor in brackets
 // and C_1 are double-float dot products (error-free FP32 products via FMA,
-// TwoSum), C_2..C_TK plain FP32 (they contribute below 0.1 turn); per bin, C_1 x
-// is an error-free FP32 product reduced mod 1, the rest a short Horner sum,
-// then FP32 __sincosf and complex MACs, flushed once per tile into double-float
-// accumulators. The only per-bin table is the weighted data.
+// TwoSum), C_2..C_TK plain FP32 (they contribute below 0.1 turn).
+// Detector 0, per bin: C_1 x as an error-free FP32 product reduced mod 1, the
+// rest a short Horner sum, the phase psi_0 in radians, FP32 __sincosf for
+// E = exp(i psi_0) and the complex MAC with the weighted data.
+// Detector d >= 1 differs from detector 0 by alpha_d + beta_d x, linear in the
+// bin, so its tile sum  sum_x w_dx E_x exp(i (alpha_d + beta_d x))  is
+// exp(i (alpha_d + beta_d x_e)) times a Horner sum in rho_d = exp(-i beta_d)
+// anchored at the last bin x_e: S <- S rho_d + w_dx E_x within segments of
+// eight bins, T <- T + T eps8_d + S across them, eps8_d = exp(-8 i beta_d) - 1
+// (the magnitude error of a rounded unit step builds up over seven steps at
+// most). These detectors take no sine or cosine per bin. Tiles of 16 bins or
+// fewer keep a sine and cosine per detector and bin (tile_bins_direct). Each
+// tile's sums are flushed into double-float accumulators; the only per-bin
+// table is the weighted data.
 constexpr int TK = 6;
+constexpr float TWO_PI_F = 6.28318530717958648f;
 
 // Position of bin j in the pair-tile order of the weighted data: at step i of
 // a tile, lanes read consecutive float4s (bins i, i + 1 of their tiles).
@@ -725,12 +756,101 @@ __device__ __forceinline__ int tile_pos2(int j, int lg) {
     return ((t >> 5) << (lg + 5)) + ((i >> 1) << 6) + ((t & 31) << 1) + (i & 1);
 }
 
-// One warp's double-float sums over tile groups g0, g0 + gstride, ... for nc <= NC
-// candidates (coefficients cm[c], last bins jcut[c]) sharing the table loads:
-// zh/zl[c][d][0/1] = real/imaginary part of sum_j w_dj exp(2 pi i phase_dj),
-// not yet reduced over the warp.
+// Constants of one candidate over one lane's tile.
+template <int NDET>
+struct TileCand {
+    float c1h, c1l, ck[TK - 1];     // C_1 (double-float), C_2..C_TK [turns]
+    float aa0, dt0;                 // detector 0: 2 pi anchor, 2 pi df tau_0 [rad]
+    float alpha[NDET];              // detectors d >= 1: alpha_d [rad]
+};
+
+// One candidate over one lane's tile, bins i < nproc (a multiple of 8); with
+// MASK, bins i >= cnt add nothing (tiles at the cutoff). Returns the sums
+// sum_i w_di exp(2 pi i phase_di) per detector in zr, zi.
+template <int NDET, bool MASK>
+__device__ __forceinline__ void tile_one(const float4 *w4, size_t dstride, int lane, int half, int nproc,
+                                         int cnt, const TileCand<NDET> &k, const CoefMixed &cm,
+                                         float (&zr)[NDET], float (&zi)[NDET]) {
+    float pr = 0.f, pim = 0.f;
+    float sr[NDET], si[NDET], tr[NDET], ti[NDET], rr[NDET], ri[NDET], er[NDET], ei[NDET];
+#pragma unroll
+    for (int d = 1; d < NDET; d++) {
+        sr[d] = si[d] = tr[d] = ti[d] = 0.f;
+        rr[d] = cm.rho[d][0];
+        ri[d] = cm.rho[d][1];
+        er[d] = cm.eps8[d][0];
+        ei[d] = cm.eps8[d][1];
+    }
+    for (int q = 0; q < nproc; q += 4) {
+        float4 w[NDET][2];
+#pragma unroll
+        for (int d = 0; d < NDET; d++) {
+            w[d][0] = __ldg(w4 + d * dstride + (q << 4) + lane);
+            w[d][1] = __ldg(w4 + d * dstride + (q << 4) + 32 + lane);
+        }
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            const int i = q + r;
+            const float x = (float)(i - half), x2 = x * x;
+            const float p = k.c1h * x;
+            float e = fmaf(k.c1h, x, -p);
+            e = fmaf(k.c1l, x, e);
+            float hq = k.ck[TK - 2];
+#pragma unroll
+            for (int j = TK - 3; j >= 0; j--) hq = fmaf(hq, x, k.ck[j]);
+            const float sm = fmaf(hq, x2, e);
+            const float P = p - rintf(p);
+            float sv, cv;
+            __sincosf(fmaf(P + sm, TWO_PI_F, fmaf(x, k.dt0, k.aa0)), &sv, &cv);
+            const bool ok = !MASK || i < cnt;
+#pragma unroll
+            for (int d = 0; d < NDET; d++) {
+                const float4 ww = w[d][r >> 1];
+                float wr = (r & 1) ? ww.z : ww.x, wi = (r & 1) ? ww.w : ww.y;
+                if (MASK) {
+                    wr = ok ? wr : 0.f;
+                    wi = ok ? wi : 0.f;
+                }
+                if (d == 0) {
+                    pr = fmaf(wr, cv, fmaf(-wi, sv, pr));
+                    pim = fmaf(wr, sv, fmaf(wi, cv, pim));
+                } else {
+                    const float cr = fmaf(wr, cv, -wi * sv), ci = fmaf(wr, sv, wi * cv);
+                    const float nr = fmaf(sr[d], rr[d], fmaf(-si[d], ri[d], cr));
+                    si[d] = fmaf(sr[d], ri[d], fmaf(si[d], rr[d], ci));
+                    sr[d] = nr;
+                }
+            }
+        }
+        if (q & 4) {        // an eight-bin segment ends
+#pragma unroll
+            for (int d = 1; d < NDET; d++) {
+                const float ur = fmaf(tr[d], er[d], fmaf(-ti[d], ei[d], sr[d]));
+                const float ui = fmaf(tr[d], ei[d], fmaf(ti[d], er[d], si[d]));
+                tr[d] += ur;
+                ti[d] += ui;
+                sr[d] = si[d] = 0.f;
+            }
+        }
+    }
+    zr[0] = pr;
+    zi[0] = pim;
+    const float xe = (float)(nproc - 1 - half);
+#pragma unroll
+    for (int d = 1; d < NDET; d++) {
+        float as, ac;
+        __sincosf(fmaf(cm.beta[d], xe, k.alpha[d]), &as, &ac);
+        zr[d] = fmaf(ac, tr[d], -as * ti[d]);
+        zi[d] = fmaf(ac, ti[d], as * tr[d]);
+    }
+}
+
+// Short tiles (L <= 16): every detector's phase reduced mod 1 and its own
+// FP32 __sincosf per bin, the nc <= NC candidates sharing the table loads (on
+// few bins per tile the rotation's per-tile setup and the candidates taken one
+// after the other cost more than the sines save). Same sums as tile_bins.
 template <int NDET, int NC>
-__device__ __forceinline__ void tile_bins(const Tables &T, int lg, int np, const CoefMixed *cm,
+__device__ __forceinline__ void tile_bins_direct(const Tables &T, int lg, int np, const CoefMixed *cm,
                                           const int *jcut, int nc, int g0, int gstride,
                                           float zh[NC][NDET][2], float zl[NC][NDET][2]) {
     const int lane = threadIdx.x & 31;
@@ -852,6 +972,120 @@ __device__ __forceinline__ void tile_bins(const Tables &T, int lg, int np, const
             }
     }
 }
+// One warp's double-float sums over tile groups g0, g0 + gstride, ... for nc <= NC
+// candidates (coefficients cm[c], last bins jcut[c]): zh/zl[c][d][0/1] =
+// real/imaginary part of sum_j w_dj exp(2 pi i phase_dj), not yet reduced over
+// the warp. Detector 0 direct and the others by their rotation, one candidate
+// after the other over each group.
+template <int NDET, int NC>
+__device__ __forceinline__ void tile_bins_rot(const Tables &T, int lg, int np, const CoefMixed *cm,
+                                              const int *jcut, int nc, int g0, int gstride,
+                                              float zh[NC][NDET][2], float zl[NC][NDET][2]) {
+    const int lane = threadIdx.x & 31;
+    const int L = 1 << lg, half = L >> 1, nt = np >> lg;
+#pragma unroll
+    for (int c = 0; c < NC; c++)
+#pragma unroll
+        for (int d = 0; d < NDET; d++) zh[c][d][0] = zh[c][d][1] = zl[c][d][0] = zl[c][d][1] = 0.f;
+    int jmax = -1;
+#pragma unroll
+    for (int c = 0; c < NC; c++)
+        if (c < nc) jmax = max(jmax, jcut[c]);
+    const int ngroups = jmax < 0 ? 0 : (jmax >> (lg + 5)) + 1;
+    const float4 *wt4 = reinterpret_cast<const float4 *>(T.wt);
+    const size_t dstride = (size_t)np >> 1;
+    for (int g = g0; g < ngroups; g += gstride) {
+        const int t = (g << 5) + lane, s = t << lg, gbin = g << (lg + 5);
+        const float2 fc = __ldg(T.fc + t);
+        const float4 *w4 = wt4 + ((size_t)gbin >> 1);
+#pragma unroll
+        for (int c = 0; c < NC; c++) {
+            if (c >= nc) continue;
+            const int nmax = min(max(jcut[c] - gbin + 1, 0), L);
+            if (nmax == 0) continue;
+            const int cnt = min(max(jcut[c] - s + 1, 0), L);
+            TileCand<NDET> k;
+            float sh = cm[c].c0h, sl = cm[c].c0l, h1 = 0.f, l1 = 0.f;
+#pragma unroll
+            for (int j = 0; j < TK - 1; j++) k.ck[j] = 0.f;
+#pragma unroll
+            for (int m = 0; m < NB; m++) {
+                const float ah = cm[c].ah[m], al = cm[c].al[m];
+                // anchor term a_m B_m(f_c)
+                const float2 b0 = __ldg(T.tb0 + (size_t)m * nt + t);
+                float p = ah * b0.x;
+                float e = fmaf(ah, b0.x, -p);
+                e = fmaf(ah, b0.y, e);
+                e = fmaf(al, b0.x, e);
+                float s2, e2;
+                two_sum(sh, p, s2, e2);
+                sh = s2;
+                sl += e2 + e;
+                // first-order term a_m B_m'(f_c) df
+                const float2 b1 = __ldg(T.tb1 + (size_t)m * nt + t);
+                p = ah * b1.x;
+                e = fmaf(ah, b1.x, -p);
+                e = fmaf(ah, b1.y, e);
+                e = fmaf(al, b1.x, e);
+                two_sum(h1, p, s2, e2);
+                h1 = s2;
+                l1 += e2 + e;
+#pragma unroll
+                for (int j = 0; j < TK - 1; j++)
+                    k.ck[j] = fmaf(ah, __ldg(T.tbk + ((size_t)j * NB + m) * nt + t), k.ck[j]);
+            }
+            k.c1h = h1 + l1;
+            k.c1l = l1 - (k.c1h - h1);
+            sh -= rintf(sh);
+            // detector anchors A_d = anchor + f_c tau_d (turns, reduced), high and low parts
+            float Ah[NDET], Al[NDET];
+#pragma unroll
+            for (int d = 0; d < NDET; d++) {
+                const float th = cm[c].tauh[d], tl = cm[c].taul[d];
+                const float p = th * fc.x;
+                float e = fmaf(th, fc.x, -p);
+                e = fmaf(th, fc.y, e);
+                e = fmaf(tl, fc.x, e);
+                float s2, e2;
+                two_sum(sh, p, s2, e2);
+                Ah[d] = s2 - rintf(s2);
+                Al[d] = sl + (e2 + e);
+            }
+            k.aa0 = TWO_PI_F * (Ah[0] + Al[0]);
+            k.dt0 = TWO_PI_F * cm[c].dtau[0];
+#pragma unroll
+            for (int d = 1; d < NDET; d++) {
+                float a = (Ah[d] - Ah[0]) + (Al[d] - Al[0]);
+                a -= rintf(a);
+                k.alpha[d] = TWO_PI_F * a;
+            }
+            float zr[NDET], zi[NDET];
+            if (jcut[c] >= gbin + (32 << lg) - 1)      // every tile of the group below the cutoff
+                tile_one<NDET, false>(w4, dstride, lane, half, L, L, k, cm[c], zr, zi);
+            else
+                tile_one<NDET, true>(w4, dstride, lane, half, (nmax + 7) & ~7, cnt, k, cm[c], zr, zi);
+#pragma unroll
+            for (int d = 0; d < NDET; d++) {
+                df_acc(zh[c][d][0], zl[c][d][0], zr[d]);
+                df_acc(zh[c][d][1], zl[c][d][1], zi[d]);
+            }
+        }
+    }
+}
+// The tiled form's sums, by rotation (ROT: tiles of 32 bins or more; GB300,
+// 519,169 bins in 64-bin tiles: slice update 478 -> 326 ms) or direct (shorter
+// tiles; 64,897 bins in 16-bin tiles: 14.3 against 15.9 ms by rotation). A
+// kernel compiles one of the two where registers are capped.
+template <int NDET, int NC, bool ROT>
+__device__ __forceinline__ void tile_bins(const Tables &T, int lg, int np, const CoefMixed *cm,
+                                          const int *jcut, int nc, int g0, int gstride,
+                                          float zh[NC][NDET][2], float zl[NC][NDET][2]) {
+    if constexpr (ROT)
+        tile_bins_rot<NDET, NC>(T, lg, np, cm, jcut, nc, g0, gstride, zh, zl);
+    else
+        tile_bins_direct<NDET, NC>(T, lg, np, cm, jcut, nc, g0, gstride, zh, zl);
+}
+
 // Double-float warp sum (TwoSum of the high parts, low parts added).
 __device__ __forceinline__ void warp_sum_df(float &h, float &l) {
 #pragma unroll

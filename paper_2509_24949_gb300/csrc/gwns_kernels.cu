@@ -231,20 +231,20 @@ cudaError_t launch_init_live(const Model &M, uint64_t seed, int n, double *live_
 // in gwns_inst_p<P>_d<D>.cu.
 template <int PREC>
 static cudaError_t eval_d(const Model &M, const Tables &T, int warps, const double *in, int th, int m,
-                          double *logl, cudaStream_t s) {
+                          double *logl, RunState *st, cudaStream_t s) {
     switch (M.n_det) {
-        case 1: return eval_launch<PREC, 1>(M, T, warps, in, th, m, logl, s);
-        case 2: return eval_launch<PREC, 2>(M, T, warps, in, th, m, logl, s);
-        case 3: return eval_launch<PREC, 3>(M, T, warps, in, th, m, logl, s);
-        default: return eval_launch<PREC, 4>(M, T, warps, in, th, m, logl, s);
+        case 1: return eval_launch<PREC, 1>(M, T, warps, in, th, m, logl, st, s);
+        case 2: return eval_launch<PREC, 2>(M, T, warps, in, th, m, logl, st, s);
+        case 3: return eval_launch<PREC, 3>(M, T, warps, in, th, m, logl, st, s);
+        default: return eval_launch<PREC, 4>(M, T, warps, in, th, m, logl, st, s);
     }
 }
 
 cudaError_t launch_eval(const Model &M, const Tables &T, int precision, int warps, const double *in,
-                        int in_is_theta, int m, double *logl, cudaStream_t s) {
+                        int in_is_theta, int m, double *logl, RunState *st, cudaStream_t s) {
     if (m <= 0) return cudaSuccess;
-    return precision == 1 ? eval_d<1>(M, T, warps, in, in_is_theta, m, logl, s)
-                          : eval_d<0>(M, T, warps, in, in_is_theta, m, logl, s);
+    return precision == 1 ? eval_d<1>(M, T, warps, in, in_is_theta, m, logl, st, s)
+                          : eval_d<0>(M, T, warps, in, in_is_theta, m, logl, st, s);
 }
 
 template <int PREC>

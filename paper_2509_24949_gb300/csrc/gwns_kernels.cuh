@@ -26,6 +26,8 @@ struct RunState {
     int walk_len;                    // random-walk kernel: proposals per walk this iteration
     int pad_;
     unsigned long long walk_acc;     // random-walk kernel: accepted moves of this iteration's walks
+    unsigned long long eval_points;      // points through the batched likelihood (k_eval)
+    unsigned long long eval_point_bins;  // their sum of (jcut + 1)
 };
 
 struct StepArgs {
@@ -97,7 +99,7 @@ cudaError_t noalloc_scratch_address(double **ptr);
 // gwns_slice.cuh and instantiated in gwns_inst_p<P>_d<D>.cu.
 template <int PREC, int NDET>
 cudaError_t eval_launch(const Model &M, const Tables &T, int warps, const double *in, int th, int m,
-                        double *logl, cudaStream_t s);
+                        double *logl, RunState *st, cudaStream_t s);
 template <int PREC, int NDET>
 cudaError_t slice_launch(const Model &M, const Tables &T, int slots, const StepArgs &A, cudaStream_t s);
 template <int PREC, int NDET>
@@ -109,7 +111,7 @@ cudaError_t launch_build_tables(const Model &M, const double *data_re, const dou
                                 double *prefix, const MixedTables &X, cudaStream_t s);
 cudaError_t launch_init_live(const Model &M, uint64_t seed, int n, double *live_u, cudaStream_t s);
 cudaError_t launch_eval(const Model &M, const Tables &T, int precision, int warps, const double *in,
-                        int in_is_theta, int m, double *logl, cudaStream_t s);
+                        int in_is_theta, int m, double *logl, RunState *st, cudaStream_t s);
 cudaError_t launch_select(const double *logl, int n, int *order, cudaStream_t s);
 cudaError_t launch_evidence(const Model &M, const StepArgs &A, cudaStream_t s);
 cudaError_t launch_cov_chol(const Model &M, const StepArgs &A, cudaStream_t s);

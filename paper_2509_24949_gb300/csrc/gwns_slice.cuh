@@ -25,7 +25,10 @@ __device__ __forceinline__ void cta_loglike_bins(const Model &M, const Tables &T
     } else if (M.tlg) {
         // tiled form: warp w takes tile groups w, w + W, ...
         float zh[1][NDET][2], zl[1][NDET][2];
-        tile_bins<NDET, 1>(T, M.tlg, M.np, &cm, &coef.jcut, 1, warp, W, zh, zl);
+        if (M.tlg >= 5)
+            tile_bins<NDET, 1, true>(T, M.tlg, M.np, &cm, &coef.jcut, 1, warp, W, zh, zl);
+        else
+            tile_bins<NDET, 1, false>(T, M.tlg, M.np, &cm, &coef.jcut, 1, warp, W, zh, zl);
 #pragma unroll
         for (int d = 0; d < NDET; d++) {
             warp_sum_df(zh[0][d][0], zl[0][d][0]);
@@ -78,13 +81,13 @@ __device__ __forceinline__ void warp_point_coef(const Model &M, const Tables &T,
         point_coef_warp(M, T, in, coef);
     }
     __syncwarp();
-    if (precision == 1) coef_to_mixed_warp(*coef, M.n_det, M.df, cm, M.rb ? T.rb.fid : nullptr);
+    if (precision == 1) coef_to_mixed_warp(*coef, M.n_det, M.df, cm, M.rb ? T.rb.fid : nullptr, M.tlg >= 5);
     (void)lane;
 }
 
 template <int PREC, int NDET, int W>
 __global__ void __launch_bounds__(W * 32) k_eval(Model M, Tables T, const double *in, int in_is_theta,
-                                                 int m, double *logl) {
+                                                 int m, double *logl, RunState *st) {
     __shared__ Coef coef;
     __shared__ CoefMixed cm;
     __shared__ double red[W][2 * MAXDET];
@@ -102,22 +105,31 @@ __global__ void __launch_bounds__(W * 32) k_eval(Model M, Tables T, const double
         if ((threadIdx.x >> 5) == 0) {
             const int lane = threadIdx.x & 31;
             const double v = rb_loglike_warp<NDET, PREC>(M, T.rb, coef, cm, lane);
-            if (lane == 0) logl[i] = v;
+            if (lane == 0) {
+                logl[i] = v;
+                if (st) atomicAdd(&st->eval_points, 1ull);
+            }
         }
         return;
     }
     cta_loglike_bins<PREC, NDET, W>(M, T, coef, cm, red, &lval);
-    if (threadIdx.x == 0) logl[i] = lval;
+    if (threadIdx.x == 0) {
+        logl[i] = lval;
+        if (st) {
+            atomicAdd(&st->eval_points, 1ull);
+            if (M.model != M_TOY) atomicAdd(&st->eval_point_bins, (unsigned long long)(coef.jcut + 1));
+        }
+    }
 }
 
 template <int PREC, int NDET>
 cudaError_t eval_launch(const Model &M, const Tables &T, int warps, const double *in, int th, int m,
-                        double *logl, cudaStream_t s) {
+                        double *logl, RunState *st, cudaStream_t s) {
     switch (warps) {
-        case 1: k_eval<PREC, NDET, 1><<<m, 32, 0, s>>>(M, T, in, th, m, logl); break;
-        case 2: k_eval<PREC, NDET, 2><<<m, 64, 0, s>>>(M, T, in, th, m, logl); break;
-        case 4: k_eval<PREC, NDET, 4><<<m, 128, 0, s>>>(M, T, in, th, m, logl); break;
-        default: k_eval<PREC, NDET, 8><<<m, 256, 0, s>>>(M, T, in, th, m, logl); break;
+        case 1: k_eval<PREC, NDET, 1><<<m, 32, 0, s>>>(M, T, in, th, m, logl, st); break;
+        case 2: k_eval<PREC, NDET, 2><<<m, 64, 0, s>>>(M, T, in, th, m, logl, st); break;
+        case 4: k_eval<PREC, NDET, 4><<<m, 128, 0, s>>>(M, T, in, th, m, logl, st); break;
+        default: k_eval<PREC, NDET, 8><<<m, 256, 0, s>>>(M, T, in, th, m, logl, st); break;
     }
     return cudaGetLastError();
 }
@@ -556,13 +568,13 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
             // mixed, every warp on every candidate of the round: the tiled form
             // shares out the tile groups (two candidates per pass on one table
             // load), the per-bin form strides the bins
-            if (warp < ns) coef_to_mixed_warp(coef[warp], M.n_det, M.df, &cm[warp]);
+            if (warp < ns) coef_to_mixed_warp(coef[warp], M.n_det, M.df, &cm[warp], nullptr, W == 8 && M.tlg);
             if (lane == 0 && warp < ns) jc[warp] = coef[warp].jcut;
             __syncthreads();
             if (M.tlg) {
                 for (int c0 = 0; c0 < ns; c0 += 2) {
                     float zh[2][NDET][2], zl[2][NDET][2];
-                    tile_bins<NDET, 2>(T, M.tlg, M.np, cm + c0, jc + c0, ns - c0 < 2 ? ns - c0 : 2, warp, W, zh,
+                    tile_bins<NDET, 2, W == 8>(T, M.tlg, M.np, cm + c0, jc + c0, ns - c0 < 2 ? ns - c0 : 2, warp, W, zh,
                                        zl);
 #pragma unroll
                     for (int sc = 0; sc < 2; sc++)
@@ -657,11 +669,11 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
                     v += coef[warp].gre[dd] * ZR - coef[warp].gim[dd] * ZI;
                 }
             } else if (M.tlg) {
-                coef_to_mixed_warp(coef[warp], M.n_det, M.df, &cm[warp]);
+                coef_to_mixed_warp(coef[warp], M.n_det, M.df, &cm[warp], nullptr, W == 8 && M.tlg);
                 if (lane == 0) jc[warp] = coef[warp].jcut;
                 __syncwarp();
                 float zh[1][NDET][2], zl[1][NDET][2];
-                tile_bins<NDET, 1>(T, M.tlg, M.np, &cm[warp], &jc[warp], 1, 0, 1, zh, zl);
+                tile_bins<NDET, 1, W == 8>(T, M.tlg, M.np, &cm[warp], &jc[warp], 1, 0, 1, zh, zl);
 #pragma unroll
                 for (int dd = 0; dd < NDET; dd++) {
                     warp_sum_df(zh[0][dd][0], zl[0][dd][0]);
@@ -671,7 +683,7 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
                     v += coef[warp].gre[dd] * ZR - coef[warp].gim[dd] * ZI;
                 }
             } else {
-                coef_to_mixed_warp(coef[warp], M.n_det, M.df, &cm[warp]);
+                coef_to_mixed_warp(coef[warp], M.n_det, M.df, &cm[warp], nullptr, W == 8 && M.tlg);
                 __syncwarp();
                 double zr[NDET], zi[NDET];
                 bins_mixed<NDET>(T, M.N, cm[warp], coef[warp].jcut, lane, 32, zr, zi);
@@ -723,12 +735,13 @@ __global__ void __launch_bounds__(W * 32, SLICE_MIN_BLOCKS(PREC, W)) k_slice(Mod
 
 template <int PREC, int NDET>
 cudaError_t slice_launch(const Model &M, const Tables &T, int slots, const StepArgs &A, cudaStream_t s) {
-    // on grids of 262,144 bins or more the tiled mixed form with cooperative
-    // bins takes 8 warps for 4 slots: as many warps per SM as 4-warp CTAs, twice
-    // as many per chain, so the update's last chains finish sooner (GB300,
-    // 519,169 bins: 536 -> 467 ms per slice update; on 64,897 bins, where an
-    // evaluation has a few tile groups, 15.2 -> 17.5 ms, hence the threshold)
-    if (PREC == 1 && slots == 4 && M.model == M_GW && M.coop && M.tlg && !M.rb &&
+    // on grids of 262,144 bins or more in tiles of 32 bins or more the tiled
+    // mixed form with cooperative bins takes 8 warps for 4 slots: as many warps
+    // per SM as 4-warp CTAs, twice as many per chain, so the update's last chains
+    // finish sooner (GB300, 519,169 bins: 536 -> 467 ms per slice update; on
+    // 64,897 bins, where an evaluation has a few tile groups, 15.2 -> 17.5 ms,
+    // hence the threshold); these kernels sum the tiles by rotation
+    if (PREC == 1 && slots == 4 && M.model == M_GW && M.coop && M.tlg >= 5 && !M.rb &&
         M.N >= 262144) {
         k_slice<PREC, NDET, 4, 8><<<A.k, 256, 0, s>>>(M, T, A);
         return cudaGetLastError();
@@ -764,7 +777,7 @@ cudaError_t slice_multi_launch(const Desc *D, const int2 *map, int nblocks, int 
 // Explicit instantiation of the launchers of one (precision, detectors) pair.
 #define GWNS_INSTANTIATE(P, D)                                                                       \
     template cudaError_t eval_launch<P, D>(const Model &, const Tables &, int, const double *, int, int, \
-                                           double *, cudaStream_t);                                 \
+                                           double *, RunState *, cudaStream_t);                     \
     template cudaError_t slice_launch<P, D>(const Model &, const Tables &, int, const StepArgs &,     \
                                             cudaStream_t);                                          \
     template cudaError_t slice_multi_launch<P, D>(const Desc *, const int2 *, int, int, cudaStream_t);

@@ -83,6 +83,28 @@ def test_lnl_mixed_parity(gw, name, over, warps):
     assert np.max(np.abs(got - want)) < MIXED_ATOL, np.max(np.abs(got - want))
 
 
+@pytest.mark.parametrize("name,over", [("c0", {"N": 12000, "df": 1 / 128}),
+                                       ("c1", {"N": 12000, "df": 1 / 128, "n_det": 2}),
+                                       ("c1", {"N": 12000, "df": 1 / 128}),
+                                       ("c1", {"N": 12000, "df": 1 / 128, "n_det": 4})])
+@pytest.mark.parametrize("warps", [1, 4])
+def test_lnl_mixed_rotation_parity(gw, name, over, warps):
+    """64-bin tiles (df = 1/128 Hz): detector 0 by its own sine and cosine per
+    bin, detectors 1..3 by their rotation against it; cutoffs inside the grid
+    for the heavier draws and a ragged last tile group (12,000 bins)."""
+    w, pb, th = problem(name, **over)
+    u = pts_for(pb, th)
+    want = pb.loglike(u)
+    with sampler_from(gw, pb, 1, n_live=8, warps_per_point=warps) as sp:
+        assert sp.stats()["mixed_tile"] == 64
+        got = sp.eval_lnl(u)
+        import torch
+        g_inj = sp.eval_lnl_theta(torch.tensor(th[None], dtype=torch.float64, device="cuda")).item()
+    assert np.max(np.abs(got - want)) < MIXED_ATOL, np.max(np.abs(got - want))
+    # the injection, where <d|h> is largest
+    assert abs(g_inj - pb.loglike_theta(th)[0]) < MIXED_ATOL
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("name", ["c2", "c4"])
 def test_lnl_full_size_sampled(gw, name, precision):
@@ -535,6 +557,20 @@ def test_mixed_tiled_form_in_slice_update(gw, slots):
     with sampler_from(gw, pb, 1, n_live=60, k=30, steps_per_dim=2, seed=7, slots=slots) as sp:
         sp.step()
         u, l = sp.live()
+    want = pb.loglike(u)
+    assert np.max(np.abs(l - want)) < MIXED_ATOL
+
+
+def test_mixed_rotation_in_slice_update(gw):
+    """Eight one-warp slots on 64-bin tiles: each slot warp sums its
+    candidate's tiles by rotation; live points after one iteration agree with
+    the oracle per point."""
+    w, pb, th = problem("c1", N=12000, df=1 / 128)
+    with sampler_from(gw, pb, 1, n_live=60, k=30, steps_per_dim=2, seed=7, slots=8) as sp:
+        assert sp.stats()["mixed_tile"] == 64
+        sp.step()
+        u, l = sp.live()
+        assert sp.stats()["status"] == 0
     want = pb.loglike(u)
     assert np.max(np.abs(l - want)) < MIXED_ATOL
 
