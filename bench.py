@@ -557,13 +557,15 @@ def table_row(g, name, precision, stream, max_steps=100000, coarse=False):
             "logZ": r["logZ"] if r else None, "dlogZ": r["dlogZ"] if r else None}
 
 
-def batch_eval_row(g, name, precision, stream, points=2048, reps=3):
+def batch_eval_row(g, name, precision, stream, points=2048, reps=3, warps=0):
     """Batched likelihood throughput (ns_eval_lnl on prior draws): CUDA events
     on the library's stream around `reps` launches after one warm-up; the
-    point-bins come from the library's own count of the bins each point read."""
+    point-bins come from the library's own count of the bins each point read.
+    warps: warps per point (0: the library's choice)."""
     import torch
     w = gi.workload(name)
-    sp, th = g.make_analysis(w, precision=precision, n_live=8, k=4, stream=stream.cuda_stream)
+    sp, th = g.make_analysis(w, precision=precision, n_live=8, k=4, stream=stream.cuda_stream,
+                             warps_per_point=warps)
     u = torch.tensor(gi.unit_cube(99, points, w.dim), dtype=torch.float64, device="cuda")
     out = torch.empty(points, dtype=torch.float64, device="cuda")
     sp.eval_lnl(u, out)
@@ -580,6 +582,7 @@ def batch_eval_row(g, name, precision, stream, points=2048, reps=3):
     sp.close()
     pb = st1["batch_point_bins"] - st0["batch_point_bins"]
     row = {"config": name, "form": "fp64" if precision == g.NS_FP64 else "mixed", "batch_points": points,
+           "warps_per_point": warps or None,
            "batch_evals_per_s": points * reps / t, "point_bins_per_s": pb / t, "bins_per_eval": pb / (points * reps)}
     if precision == g.NS_FP64:
         row["frac"], row["pipe"] = pb * fp64_flops_per_point_bin(w.n_det) / t / (FP64_PEAK_TFLOPS * 1e12), "FP64"
@@ -777,13 +780,19 @@ def run_profile_case(args):
     from paper_2509_24949_gb300 import _build
     if not _build.up_to_date():
         _build.build()
+    prec = g.NS_MIXED if args.precision == "mixed" else g.NS_FP64
+    stream = torch.cuda.Stream()
+    if args.batch_points:
+        # the batched likelihood: ns_init's 8-point live set, one warm-up launch,
+        # then `steps` launches of batch_points prior draws
+        r = batch_eval_row(g, args.profile_case, prec, stream, points=args.batch_points, reps=args.steps)
+        print(json.dumps({"profile_case": args.profile_case, "precision": args.precision, **r}))
+        return
     w = gi.workload(args.profile_case)
     if args.n_live:
         w.n_live = args.n_live
     if args.k:
         w.k = args.k
-    prec = g.NS_MIXED if args.precision == "mixed" else g.NS_FP64
-    stream = torch.cuda.Stream()
     sp, th = g.make_analysis(w, precision=prec, stream=stream.cuda_stream)
     for _ in range(args.steps):
         sp.step()
@@ -819,6 +828,9 @@ def main():
                     help="whole-run time against n_live (k = n/2) and against k at n = 1000 (c1)")
     ap.add_argument("--n-live", type=int, default=0)
     ap.add_argument("--k", type=int, default=0)
+    ap.add_argument("--batch-points", type=int, default=0,
+                    help="with --profile-case: time the batched likelihood on this many prior draws "
+                         "(--steps launches) instead of running iterations")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

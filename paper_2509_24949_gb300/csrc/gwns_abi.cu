@@ -60,6 +60,10 @@ int choose_warps(const ns_ctx *c) {
     // warps per point hide FP32 latency. Tuned values come from the autotuner.
     const int bins = c->M.N;
     if (c->precision == NS_FP64) return bins > 32768 ? 2 : 1;
+    // the rotation form (tiles of 32 bins or more) prefetches its loads and
+    // needs fewer warps per point (GB300, 519,169 bins: 8 / 4 / 2 warps give
+    // 1.44 / 1.53 / 1.47 M evals/s)
+    if (c->M.tlg >= 5) return 4;
     return bins > 16384 ? 8 : (bins > 2048 ? 4 : 2);
 }
 

@@ -766,8 +766,11 @@ struct TileCand {
 
 // One candidate over one lane's tile, bins i < nproc (a multiple of 8); with
 // MASK, bins i >= cnt add nothing (tiles at the cutoff). Returns the sums
-// sum_i w_di exp(2 pi i phase_di) per detector in zr, zi.
-template <int NDET, bool MASK>
+// sum_i w_di exp(2 pi i phase_di) per detector in zr, zi. With PF the next
+// four bins' weighted data are loaded while these four are summed (the
+// batched likelihood waits on these loads otherwise; the slice kernels, at
+// their register cap, do not).
+template <int NDET, bool MASK, bool PF>
 __device__ __forceinline__ void tile_one(const float4 *w4, size_t dstride, int lane, int half, int nproc,
                                          int cnt, const TileCand<NDET> &k, const CoefMixed &cm,
                                          float (&zr)[NDET], float (&zi)[NDET]) {
@@ -781,12 +784,29 @@ __device__ __forceinline__ void tile_one(const float4 *w4, size_t dstride, int l
         er[d] = cm.eps8[d][0];
         ei[d] = cm.eps8[d][1];
     }
-    for (int q = 0; q < nproc; q += 4) {
-        float4 w[NDET][2];
+    float4 w[NDET][2];
+    if (PF) {
 #pragma unroll
         for (int d = 0; d < NDET; d++) {
-            w[d][0] = __ldg(w4 + d * dstride + (q << 4) + lane);
-            w[d][1] = __ldg(w4 + d * dstride + (q << 4) + 32 + lane);
+            w[d][0] = __ldg(w4 + d * dstride + lane);
+            w[d][1] = __ldg(w4 + d * dstride + 32 + lane);
+        }
+    }
+    for (int q = 0; q < nproc; q += 4) {
+        float4 wn[NDET][2];
+        if (PF) {
+            const int qn = q + 4 < nproc ? q + 4 : q;     // the last step reloads its own bins
+#pragma unroll
+            for (int d = 0; d < NDET; d++) {
+                wn[d][0] = __ldg(w4 + d * dstride + (qn << 4) + lane);
+                wn[d][1] = __ldg(w4 + d * dstride + (qn << 4) + 32 + lane);
+            }
+        } else {
+#pragma unroll
+            for (int d = 0; d < NDET; d++) {
+                w[d][0] = __ldg(w4 + d * dstride + (q << 4) + lane);
+                w[d][1] = __ldg(w4 + d * dstride + (q << 4) + 32 + lane);
+            }
         }
 #pragma unroll
         for (int r = 0; r < 4; r++) {
@@ -820,6 +840,13 @@ __device__ __forceinline__ void tile_one(const float4 *w4, size_t dstride, int l
                     si[d] = fmaf(sr[d], ri[d], fmaf(si[d], rr[d], ci));
                     sr[d] = nr;
                 }
+            }
+        }
+        if (PF) {
+#pragma unroll
+            for (int d = 0; d < NDET; d++) {
+                w[d][0] = wn[d][0];
+                w[d][1] = wn[d][1];
             }
         }
         if (q & 4) {        // an eight-bin segment ends
@@ -977,7 +1004,7 @@ __device__ __forceinline__ void tile_bins_direct(const Tables &T, int lg, int np
 // real/imaginary part of sum_j w_dj exp(2 pi i phase_dj), not yet reduced over
 // the warp. Detector 0 direct and the others by their rotation, one candidate
 // after the other over each group.
-template <int NDET, int NC>
+template <int NDET, int NC, bool PF>
 __device__ __forceinline__ void tile_bins_rot(const Tables &T, int lg, int np, const CoefMixed *cm,
                                               const int *jcut, int nc, int g0, int gstride,
                                               float zh[NC][NDET][2], float zl[NC][NDET][2]) {
@@ -1061,9 +1088,9 @@ __device__ __forceinline__ void tile_bins_rot(const Tables &T, int lg, int np, c
             }
             float zr[NDET], zi[NDET];
             if (jcut[c] >= gbin + (32 << lg) - 1)      // every tile of the group below the cutoff
-                tile_one<NDET, false>(w4, dstride, lane, half, L, L, k, cm[c], zr, zi);
+                tile_one<NDET, false, PF>(w4, dstride, lane, half, L, L, k, cm[c], zr, zi);
             else
-                tile_one<NDET, true>(w4, dstride, lane, half, (nmax + 7) & ~7, cnt, k, cm[c], zr, zi);
+                tile_one<NDET, true, PF>(w4, dstride, lane, half, (nmax + 7) & ~7, cnt, k, cm[c], zr, zi);
 #pragma unroll
             for (int d = 0; d < NDET; d++) {
                 df_acc(zh[c][d][0], zl[c][d][0], zr[d]);
@@ -1076,12 +1103,12 @@ __device__ __forceinline__ void tile_bins_rot(const Tables &T, int lg, int np, c
 // 519,169 bins in 64-bin tiles: slice update 478 -> 326 ms) or direct (shorter
 // tiles; 64,897 bins in 16-bin tiles: 14.3 against 15.9 ms by rotation). A
 // kernel compiles one of the two where registers are capped.
-template <int NDET, int NC, bool ROT>
+template <int NDET, int NC, bool ROT, bool PF = false>
 __device__ __forceinline__ void tile_bins(const Tables &T, int lg, int np, const CoefMixed *cm,
                                           const int *jcut, int nc, int g0, int gstride,
                                           float zh[NC][NDET][2], float zl[NC][NDET][2]) {
     if constexpr (ROT)
-        tile_bins_rot<NDET, NC>(T, lg, np, cm, jcut, nc, g0, gstride, zh, zl);
+        tile_bins_rot<NDET, NC, PF>(T, lg, np, cm, jcut, nc, g0, gstride, zh, zl);
     else
         tile_bins_direct<NDET, NC>(T, lg, np, cm, jcut, nc, g0, gstride, zh, zl);
 }

@@ -26,7 +26,7 @@ __device__ __forceinline__ void cta_loglike_bins(const Model &M, const Tables &T
         // tiled form: warp w takes tile groups w, w + W, ...
         float zh[1][NDET][2], zl[1][NDET][2];
         if (M.tlg >= 5)
-            tile_bins<NDET, 1, true>(T, M.tlg, M.np, &cm, &coef.jcut, 1, warp, W, zh, zl);
+            tile_bins<NDET, 1, true, true>(T, M.tlg, M.np, &cm, &coef.jcut, 1, warp, W, zh, zl);
         else
             tile_bins<NDET, 1, false>(T, M.tlg, M.np, &cm, &coef.jcut, 1, warp, W, zh, zl);
 #pragma unroll
