@@ -462,18 +462,18 @@ SFU_LANE_OPS = 152 * 16 * 2.070e9      # MUFU (sin, cos): 16 lanes/clk/SM x 152 
 def mixed_fp32_per_point_bin(n_det: int, tile: int) -> float:
     """FP32 instructions of the mixed form per point-bin (per-tile or per-flush
     work not counted). Tiles of 32 bins or more: x and x^2 (2), C_1 x as an
-    error-free product (3), the Horner sum of C_2..C_6 (5), the reduction of
+    error-free product (3), the Horner sum of C_2..C_7 (6), the reduction of
     C_1 x (2), detector 0's phase in radians (3) and complex MAC (4); per
     further detector the product of the weighted data with detector 0's phasor
     (4), one step of the Horner sum in its rotation (4) and an eighth of a
-    segment step (6). Shorter tiles: the common part (11) and per detector
+    segment step (6). Shorter tiles: the common part (12) and per detector
     4 (phase) + 2 (reduction) + 1 (scale) + 4 (complex MAC). Per-bin form
     (tile 0): the double-float dot product of 8 basis terms (12 each) and per
     detector the double-float delay term, reduction and MAC (20)."""
     if tile >= 32:
-        return 19.0 + 8.75 * (n_det - 1)
+        return 20.0 + 8.75 * (n_det - 1)
     if tile:
-        return 11.0 + 11.0 * n_det
+        return 12.0 + 11.0 * n_det
     return 96.0 + 20.0 * n_det
 
 

@@ -732,7 +732,8 @@ __device__ __forceinline__ double warp_max(double v) {
 // function about the tile centre, its remainder bounded on the host below 1e-8
 // rad when the tiled form is chosen. Per lane and tile, the anchor in brackets
 // and C_1 are double-float dot products (error-free FP32 products via FMA,
-// TwoSum), C_2..C_TK plain FP32 (they contribute below 0.1 turn).
+// TwoSum), C_2..C_TK plain FP32 (below a turn on 128-bin tiles, so their FP32
+// rounding stays below 4e-7 rad).
 // Detector 0, per bin: C_1 x as an error-free FP32 product reduced mod 1, the
 // rest a short Horner sum, the phase psi_0 in radians, FP32 __sincosf for
 // E = exp(i psi_0) and the complex MAC with the weighted data.
@@ -746,7 +747,7 @@ __device__ __forceinline__ double warp_max(double v) {
 // fewer keep a sine and cosine per detector and bin (tile_bins_direct). Each
 // tile's sums are flushed into double-float accumulators; the only per-bin
 // table is the weighted data.
-constexpr int TK = 6;
+constexpr int TK = 7;
 constexpr float TWO_PI_F = 6.28318530717958648f;
 
 // Position of bin j in the pair-tile order of the weighted data: at step i of

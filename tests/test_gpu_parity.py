@@ -70,11 +70,13 @@ def test_lnl_fp64_parity(gw, name, over, warps):
 
 @pytest.mark.parametrize("name,over", [("c0", {}), ("c1", {}), ("c1", {"N": 1013}),
                                        ("c1", {"N": 33, "df": 4.0}), ("c1", {"N": 8000, "df": 0.03125}),
-                                       ("c1", {"N": 3001, "df": 0.03125})])
+                                       ("c1", {"N": 3001, "df": 0.03125}), ("c1", {"N": 3001, "df": 0.0625}),
+                                       ("c1", {"N": 1500, "df": 0.125})])
 @pytest.mark.parametrize("warps", [1, 2, 8])
 def test_lnl_mixed_parity(gw, name, over, warps):
-    """Coarse grids take the per-bin mixed form, fine ones (df = 1/32 Hz here:
-    16-bin tiles, the second with a ragged last group) the tiled form."""
+    """Coarse grids take the per-bin mixed form, fine ones the tiled form:
+    df = 1/32 Hz 32-bin tiles (rotation), 1/16 Hz 16-bin and 1/8 Hz 8-bin
+    tiles (direct), some with a ragged last group."""
     w, pb, th = problem(name, **over)
     u = pts_for(pb, th)
     want = pb.loglike(u)
@@ -83,20 +85,21 @@ def test_lnl_mixed_parity(gw, name, over, warps):
     assert np.max(np.abs(got - want)) < MIXED_ATOL, np.max(np.abs(got - want))
 
 
-@pytest.mark.parametrize("name,over", [("c0", {"N": 12000, "df": 1 / 128}),
-                                       ("c1", {"N": 12000, "df": 1 / 128, "n_det": 2}),
-                                       ("c1", {"N": 12000, "df": 1 / 128}),
-                                       ("c1", {"N": 12000, "df": 1 / 128, "n_det": 4})])
+@pytest.mark.parametrize("name,over,tile", [("c0", {"N": 12000, "df": 1 / 128}, 128),
+                                            ("c1", {"N": 12000, "df": 1 / 128, "n_det": 2}, 128),
+                                            ("c1", {"N": 12000, "df": 1 / 128}, 128),
+                                            ("c1", {"N": 12000, "df": 1 / 128, "n_det": 4}, 128),
+                                            ("c1", {"N": 6000, "df": 1 / 64}, 64)])
 @pytest.mark.parametrize("warps", [1, 4])
-def test_lnl_mixed_rotation_parity(gw, name, over, warps):
-    """64-bin tiles (df = 1/128 Hz): detector 0 by its own sine and cosine per
-    bin, detectors 1..3 by their rotation against it; cutoffs inside the grid
-    for the heavier draws and a ragged last tile group (12,000 bins)."""
+def test_lnl_mixed_rotation_parity(gw, name, over, tile, warps):
+    """128- and 64-bin tiles (df = 1/128, 1/64 Hz): detector 0 by its own sine
+    and cosine per bin, detectors 1..3 by their rotation against it; cutoffs
+    inside the grid for the heavier draws and a ragged last tile group."""
     w, pb, th = problem(name, **over)
     u = pts_for(pb, th)
     want = pb.loglike(u)
     with sampler_from(gw, pb, 1, n_live=8, warps_per_point=warps) as sp:
-        assert sp.stats()["mixed_tile"] == 64
+        assert sp.stats()["mixed_tile"] == tile
         got = sp.eval_lnl(u)
         import torch
         g_inj = sp.eval_lnl_theta(torch.tensor(th[None], dtype=torch.float64, device="cuda")).item()
@@ -524,8 +527,9 @@ def test_mixed_large_grid_cooperative_bins(gw, slots):
     assert np.max(np.abs(l - want)) < MIXED_ATOL
 
 
-@pytest.mark.parametrize("name,over,tile", [("c1", {}, 0), ("c1", {"N": 8000, "df": 0.03125}, 16),
-                                            ("c2", {}, 16), ("c4", {}, 64), ("c1", {"N": 33, "df": 4.0}, 0)])
+@pytest.mark.parametrize("name,over,tile", [("c1", {}, 0), ("c1", {"N": 8000, "df": 0.03125}, 32),
+                                            ("c1", {"N": 3001, "df": 0.0625}, 16),
+                                            ("c2", {}, 32), ("c4", {}, 128), ("c1", {"N": 33, "df": 4.0}, 0)])
 def test_mixed_form_choice(gw, name, over, tile):
     """The tiled form is taken where the Taylor remainder bound allows (the
     longest such tile), the per-bin form elsewhere."""
@@ -536,11 +540,11 @@ def test_mixed_form_choice(gw, name, over, tile):
 
 def test_mixed_wide_ctas_on_the_largest_grid(gw):
     """The 519,169-bin grid runs the mixed slice update with 8-warp CTAs
-    (64-bin tiles shared out by all warps): live points after one iteration
-    agree with the oracle per point."""
+    (128-bin tiles shared out by all warps, by rotation): live points after one
+    iteration agree with the oracle per point."""
     w, pb, th = problem("c4")
     with sampler_from(gw, pb, 1, n_live=24, k=12, steps_per_dim=1, seed=11) as sp:
-        assert sp.stats()["mixed_tile"] == 64
+        assert sp.stats()["mixed_tile"] == 128
         sp.step()
         u, l = sp.live()
         assert sp.stats()["status"] == 0
@@ -550,9 +554,9 @@ def test_mixed_wide_ctas_on_the_largest_grid(gw):
 
 @pytest.mark.parametrize("slots", [1, 2, 4])
 def test_mixed_tiled_form_in_slice_update(gw, slots):
-    """A fine grid below the cooperative size (8000 bins at 1/32 Hz): each slot
-    warp runs the tiled mixed form on its own candidate; live points after one
-    iteration agree with the oracle per point."""
+    """A fine grid below the cooperative size (8000 bins at 1/32 Hz, 32-bin
+    tiles): each slot warp runs the direct tiled form on its own candidate;
+    live points after one iteration agree with the oracle per point."""
     w, pb, th = problem("c1", N=8000, df=0.03125)
     with sampler_from(gw, pb, 1, n_live=60, k=30, steps_per_dim=2, seed=7, slots=slots) as sp:
         sp.step()
@@ -562,12 +566,12 @@ def test_mixed_tiled_form_in_slice_update(gw, slots):
 
 
 def test_mixed_rotation_in_slice_update(gw):
-    """Eight one-warp slots on 64-bin tiles: each slot warp sums its
+    """Eight one-warp slots on 128-bin tiles: each slot warp sums its
     candidate's tiles by rotation; live points after one iteration agree with
     the oracle per point."""
     w, pb, th = problem("c1", N=12000, df=1 / 128)
     with sampler_from(gw, pb, 1, n_live=60, k=30, steps_per_dim=2, seed=7, slots=8) as sp:
-        assert sp.stats()["mixed_tile"] == 64
+        assert sp.stats()["mixed_tile"] == 128
         sp.step()
         u, l = sp.live()
         assert sp.stats()["status"] == 0
