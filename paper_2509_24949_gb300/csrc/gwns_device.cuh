@@ -1101,9 +1101,10 @@ __device__ __forceinline__ void tile_bins_rot(const Tables &T, int lg, int np, c
     }
 }
 // The tiled form's sums, by rotation (ROT: tiles of 32 bins or more; GB300,
-// 519,169 bins in 64-bin tiles: slice update 478 -> 326 ms) or direct (shorter
-// tiles; 64,897 bins in 16-bin tiles: 14.3 against 15.9 ms by rotation). A
-// kernel compiles one of the two where registers are capped.
+// 519,169 bins in 64-bin tiles: slice update 478 -> 326 ms; 64,897 bins in
+// 32-bin tiles: 14.3 -> 13.8 ms) or direct (shorter tiles, where the per-tile
+// rotation setup outweighs the saved sines: 64,897 bins in 16-bin tiles, 14.3
+// against 15.9 ms by rotation). Callers choose by the tile length.
 template <int NDET, int NC, bool ROT, bool PF = false>
 __device__ __forceinline__ void tile_bins(const Tables &T, int lg, int np, const CoefMixed *cm,
                                           const int *jcut, int nc, int g0, int gstride,

@@ -568,14 +568,17 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
             // mixed, every warp on every candidate of the round: the tiled form
             // shares out the tile groups (two candidates per pass on one table
             // load), the per-bin form strides the bins
-            if (warp < ns) coef_to_mixed_warp(coef[warp], M.n_det, M.df, &cm[warp], nullptr, W == 8 && M.tlg);
+            if (warp < ns) coef_to_mixed_warp(coef[warp], M.n_det, M.df, &cm[warp], nullptr, M.tlg >= 5);
             if (lane == 0 && warp < ns) jc[warp] = coef[warp].jcut;
             __syncthreads();
             if (M.tlg) {
                 for (int c0 = 0; c0 < ns; c0 += 2) {
                     float zh[2][NDET][2], zl[2][NDET][2];
-                    tile_bins<NDET, 2, W == 8>(T, M.tlg, M.np, cm + c0, jc + c0, ns - c0 < 2 ? ns - c0 : 2, warp, W, zh,
-                                       zl);
+                    const int nc = ns - c0 < 2 ? ns - c0 : 2;
+                    if (M.tlg >= 5)
+                        tile_bins<NDET, 2, true>(T, M.tlg, M.np, cm + c0, jc + c0, nc, warp, W, zh, zl);
+                    else
+                        tile_bins<NDET, 2, false>(T, M.tlg, M.np, cm + c0, jc + c0, nc, warp, W, zh, zl);
 #pragma unroll
                     for (int sc = 0; sc < 2; sc++)
 #pragma unroll
@@ -669,11 +672,14 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
                     v += coef[warp].gre[dd] * ZR - coef[warp].gim[dd] * ZI;
                 }
             } else if (M.tlg) {
-                coef_to_mixed_warp(coef[warp], M.n_det, M.df, &cm[warp], nullptr, W == 8 && M.tlg);
+                coef_to_mixed_warp(coef[warp], M.n_det, M.df, &cm[warp], nullptr, M.tlg >= 5);
                 if (lane == 0) jc[warp] = coef[warp].jcut;
                 __syncwarp();
                 float zh[1][NDET][2], zl[1][NDET][2];
-                tile_bins<NDET, 1, W == 8>(T, M.tlg, M.np, &cm[warp], &jc[warp], 1, 0, 1, zh, zl);
+                if (M.tlg >= 5)
+                    tile_bins<NDET, 1, true>(T, M.tlg, M.np, &cm[warp], &jc[warp], 1, 0, 1, zh, zl);
+                else
+                    tile_bins<NDET, 1, false>(T, M.tlg, M.np, &cm[warp], &jc[warp], 1, 0, 1, zh, zl);
 #pragma unroll
                 for (int dd = 0; dd < NDET; dd++) {
                     warp_sum_df(zh[0][dd][0], zl[0][dd][0]);
@@ -683,7 +689,7 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
                     v += coef[warp].gre[dd] * ZR - coef[warp].gim[dd] * ZI;
                 }
             } else {
-                coef_to_mixed_warp(coef[warp], M.n_det, M.df, &cm[warp], nullptr, W == 8 && M.tlg);
+                coef_to_mixed_warp(coef[warp], M.n_det, M.df, &cm[warp], nullptr, M.tlg >= 5);
                 __syncwarp();
                 double zr[NDET], zi[NDET];
                 bins_mixed<NDET>(T, M.N, cm[warp], coef[warp].jcut, lane, 32, zr, zi);
@@ -740,7 +746,7 @@ cudaError_t slice_launch(const Model &M, const Tables &T, int slots, const StepA
     // per SM as 4-warp CTAs, twice as many per chain, so the update's last chains
     // finish sooner (GB300, 519,169 bins: 536 -> 467 ms per slice update; on
     // 64,897 bins, where an evaluation has a few tile groups, 15.2 -> 17.5 ms,
-    // hence the threshold); these kernels sum the tiles by rotation
+    // hence the threshold)
     if (PREC == 1 && slots == 4 && M.model == M_GW && M.coop && M.tlg >= 5 && !M.rb &&
         M.N >= 262144) {
         k_slice<PREC, NDET, 4, 8><<<A.k, 256, 0, s>>>(M, T, A);
