@@ -272,7 +272,7 @@ def time_to_logz(g, w, precision, stream):
             "evals_per_s": s["evals"] / (t2 - t1), "logZ": r["logZ"], "dlogZ": r["dlogZ"]}
 
 
-def precision_agreement(g, w, stream, seeds: int = 16, points: int = 4096):
+def precision_agreement(g, w, stream, seeds: int = 16, points: int = 4096, name: str = WORKLOAD):
     """Mixed against FP64 on the GPU: per-point log L difference on prior
     draws, and log Z over `seeds` sampler seeds (same data), reported as the
     mean difference with its standard error."""
@@ -286,7 +286,7 @@ def precision_agreement(g, w, stream, seeds: int = 16, points: int = 4096):
     for i in range(seeds):
         zs = []
         for prec in (g.NS_FP64, g.NS_MIXED):
-            w2 = build_workload(g, prec)
+            w2 = gi.workload(name)
             w2.seed_sampler += 1000 * (i + 1)
             sp, _ = g.make_analysis(w2, precision=prec, stream=stream.cuda_stream)
             sp.run()
@@ -295,7 +295,8 @@ def precision_agreement(g, w, stream, seeds: int = 16, points: int = 4096):
         dz.append(zs[1] - zs[0])
         z64.append(zs[0])
     dz = np.array(dz)
-    return {"points": points, "max_abs_dlogL": float(d.max()), "rms_dlogL": float(np.sqrt(np.mean(d * d))),
+    return {"workload": name, "points": points, "max_abs_dlogL": float(d.max()),
+            "rms_dlogL": float(np.sqrt(np.mean(d * d))),
             "seeds": seeds, "mean_dlogZ": float(dz.mean()), "stderr_dlogZ": float(dz.std(ddof=1) / np.sqrt(seeds)),
             "max_abs_dlogZ_single_seed": float(np.abs(dz).max()), "sd_logZ_fp64_over_seeds": float(np.std(z64, ddof=1))}
 
@@ -772,6 +773,19 @@ def run_kernel_study(args):
                           "sd_logZ": float(z.std(ddof=1)), "mean_dlogZ": float(np.mean(dz))}), flush=True)
 
 
+def run_precision_study(args):
+    """precision_agreement on one workload, one JSON line."""
+    import torch
+    import paper_2509_24949_gb300 as g
+    from paper_2509_24949_gb300 import _build
+    if not _build.up_to_date():
+        _build.build()
+    stream = torch.cuda.Stream()
+    w = gi.workload(args.precision_study)
+    r = precision_agreement(g, w, stream, seeds=args.seeds, name=args.precision_study)
+    print(json.dumps({"study": "mixed against FP64", **r}), flush=True)
+
+
 def run_profile_case(args):
     """A few iterations of one workload and form, untimed, for profiler captures
     of its kernels (e.g. ncu -k regex:k_slice -s <warm-up launches> -c 1)."""
@@ -826,6 +840,10 @@ def main():
                     help="log Z scatter over seeds vs dlogZ (5, 10, 20 steps per dim) and noise-only log BF (c1)")
     ap.add_argument("--scaling-study", action="store_true",
                     help="whole-run time against n_live (k = n/2) and against k at n = 1000 (c1)")
+    ap.add_argument("--precision-study", default=None,
+                    help="mixed against FP64 on one workload (c0, c1, c2): per-point log L on 4096 prior "
+                         "draws and log Z over --seeds sampler seeds")
+    ap.add_argument("--seeds", type=int, default=8)
     ap.add_argument("--n-live", type=int, default=0)
     ap.add_argument("--k", type=int, default=0)
     ap.add_argument("--batch-points", type=int, default=0,
@@ -834,6 +852,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.precision_study:
+        run_precision_study(args)
+        return
     if args.table:
         run_table(args)
         return

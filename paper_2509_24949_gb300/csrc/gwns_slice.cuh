@@ -454,7 +454,7 @@ __device__ int walk_plan(const Model &M, const StepArgs &A, const Chain &c, int 
     return ns;
 }
 
-template <int PREC, int NDET, int S, int W = S>
+template <int PREC, int NDET, int S, int W = S, bool ROTOK = true>
 __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, const int chain) {
     __shared__ Coef coef[S];
     __shared__ CoefMixed cm[S];
@@ -568,14 +568,14 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
             // mixed, every warp on every candidate of the round: the tiled form
             // shares out the tile groups (two candidates per pass on one table
             // load), the per-bin form strides the bins
-            if (warp < ns) coef_to_mixed_warp(coef[warp], M.n_det, M.df, &cm[warp], nullptr, M.tlg >= 5);
+            if (warp < ns) coef_to_mixed_warp(coef[warp], M.n_det, M.df, &cm[warp], nullptr, ROTOK && M.tlg >= 5);
             if (lane == 0 && warp < ns) jc[warp] = coef[warp].jcut;
             __syncthreads();
             if (M.tlg) {
                 for (int c0 = 0; c0 < ns; c0 += 2) {
                     float zh[2][NDET][2], zl[2][NDET][2];
                     const int nc = ns - c0 < 2 ? ns - c0 : 2;
-                    if (M.tlg >= 5)
+                    if (ROTOK && M.tlg >= 5)
                         tile_bins<NDET, 2, true>(T, M.tlg, M.np, cm + c0, jc + c0, nc, warp, W, zh, zl);
                     else
                         tile_bins<NDET, 2, false>(T, M.tlg, M.np, cm + c0, jc + c0, nc, warp, W, zh, zl);
@@ -672,11 +672,11 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
                     v += coef[warp].gre[dd] * ZR - coef[warp].gim[dd] * ZI;
                 }
             } else if (M.tlg) {
-                coef_to_mixed_warp(coef[warp], M.n_det, M.df, &cm[warp], nullptr, M.tlg >= 5);
+                coef_to_mixed_warp(coef[warp], M.n_det, M.df, &cm[warp], nullptr, ROTOK && M.tlg >= 5);
                 if (lane == 0) jc[warp] = coef[warp].jcut;
                 __syncwarp();
                 float zh[1][NDET][2], zl[1][NDET][2];
-                if (M.tlg >= 5)
+                if (ROTOK && M.tlg >= 5)
                     tile_bins<NDET, 1, true>(T, M.tlg, M.np, &cm[warp], &jc[warp], 1, 0, 1, zh, zl);
                 else
                     tile_bins<NDET, 1, false>(T, M.tlg, M.np, &cm[warp], &jc[warp], 1, 0, 1, zh, zl);
@@ -689,7 +689,7 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
                     v += coef[warp].gre[dd] * ZR - coef[warp].gim[dd] * ZI;
                 }
             } else {
-                coef_to_mixed_warp(coef[warp], M.n_det, M.df, &cm[warp], nullptr, M.tlg >= 5);
+                coef_to_mixed_warp(coef[warp], M.n_det, M.df, &cm[warp], nullptr, ROTOK && M.tlg >= 5);
                 __syncwarp();
                 double zr[NDET], zi[NDET];
                 bins_mixed<NDET>(T, M.N, cm[warp], coef[warp].jcut, lane, 32, zr, zi);
@@ -761,12 +761,15 @@ cudaError_t slice_launch(const Model &M, const Tables &T, int slots, const StepA
     return cudaGetLastError();
 }
 
+// Many analyses in one launch (serving): the tiled grids take the direct form
+// at every tile length. Compiling the rotation form too spilled registers, and
+// the serving stream slowed from p50 4.0 to 5.8 s.
 template <int PREC, int NDET, int S>
 __global__ void __launch_bounds__(S * 32, SLICE_MIN_BLOCKS(PREC, S)) k_slice_multi(const Desc *D, const int2 *map) {
     __shared__ Desc d;
     const int2 ac = map[blockIdx.x];
     load_desc(D + ac.x, d);
-    slice_body<PREC, NDET, S>(d.M, d.T, d.A, ac.y);
+    slice_body<PREC, NDET, S, S, false>(d.M, d.T, d.A, ac.y);
 }
 
 template <int PREC, int NDET>
