@@ -10,10 +10,12 @@ import oracle
 pytestmark = pytest.mark.gpu
 
 
-def _analysis(seed_offset, N=1200, n_live=80, n_det=3):
+def _analysis(seed_offset, N=1200, n_live=80, n_det=3, df=None):
     w = gi.workload("c1", n_live=n_live, k=n_live // 2)
     w.N = N
     w.n_det = n_det
+    if df is not None:
+        w.df = df
     w.seed_noise += seed_offset
     w.seed_injection += seed_offset
     w.seed_sampler += seed_offset
@@ -46,6 +48,32 @@ def test_alone_equals_in_the_mix(gw, precision):
     assert st_alone["state"] == gw.NS_REQ_DONE
     assert mixed["logZ"] == alone["logZ"] and mixed["dlogZ"] == alone["dlogZ"]
     assert np.array_equal(mixed["u"], alone["u"]) and np.array_equal(mixed["logl"], alone["logl"])
+
+
+def test_tiled_forms_share_a_server(gw):
+    """Mixed analyses whose grids take different mixed forms (32- and 16-bin
+    tiles, the per-bin form) interleaved in one server: each result equals the
+    analysis alone."""
+    reqs = [_analysis(40, N=3000, df=1 / 32), _analysis(41, N=1500, df=1 / 16), _analysis(42)]
+    alone = []
+    for r, dim in reqs:
+        with gw.Server(precision=1, slots=2) as srv:
+            rid = srv.submit(**r)
+            srv.run_until_idle()
+            alone.append(srv.result(rid, dim))
+    with gw.Server(precision=1, slots=2) as srv:
+        ids = [srv.submit(**r) for r, _ in reqs]
+        max_run = 0
+        while True:
+            n, p = srv.tick()
+            max_run = max(max_run, n)
+            if n == 0 and p == 0:
+                break
+        assert max_run == 3
+        mixed = [srv.result(i, dim) for i, (_, dim) in zip(ids, reqs)]
+    for a, m in zip(alone, mixed):
+        assert m["logZ"] == a["logZ"]
+        assert np.array_equal(m["logl"], a["logl"])
 
 
 def test_server_equals_single_context(gw):
