@@ -205,6 +205,9 @@ def run_gpu(args):
     extras = rank == 0 and not args.core_only
     serving = serving_stream(g) if extras else None
     agreement = precision_agreement(g, w, stream) if extras else None
+    # the mixed-precision likelihood against its roofline: the batched
+    # likelihood on the 519,169-bin workload (8192 prior draws, three launches)
+    mixed_lik = mixed_likelihood_roofline(g, stream) if extras else None
 
     if rank == 0:
         cpu = cpu_baseline() if ws == 1 and not args.core_only else None
@@ -220,6 +223,7 @@ def run_gpu(args):
             "time_to_logZ": ttl,
             "serving": serving,
             "mixed_vs_fp64": agreement,
+            "mixed_likelihood": mixed_lik,
             "e2e": e2e,
             "gpu_launches": 5 * args.steps,   # the 5 library kernels of each ns_step (the L2 flush fill is torch's)
             "kernel_ms_per_step": [(b - a) / args.steps for a, b in zip(st0["kernel_ms"], st1["kernel_ms"])],
@@ -230,6 +234,21 @@ def run_gpu(args):
         print(json.dumps(out))
     if dist:
         dist.destroy_process_group()
+
+
+def mixed_likelihood_roofline(g, stream):
+    """The mixed batched likelihood (`ns_eval_lnl`, kernel k_eval) on the c4
+    grid: throughput and the fraction of its binding pipe (derived peaks, as
+    for the mixed rows of the table)."""
+    r = batch_eval_row(g, "c4", g.NS_MIXED, stream, points=8192, reps=3)
+    peak = FP32_LANE_OPS if r["pipe"] == "FP32" else SFU_LANE_OPS
+    return {"workload": "c4: 3 detectors, 20-2048 Hz at df=1/256 (519,169 bins), 8192 prior draws, "
+                        "mixed precision, 128-bin tiles", "kernel": "k_eval<MIXED,3 det>",
+            "evals_per_s": r["batch_evals_per_s"], "point_bins_per_s": r["point_bins_per_s"],
+            "bound": r["pipe"], "frac": r["frac"], "peak_lane_ops_per_s": peak,
+            "instr_per_point_bin": (mixed_fp32_per_point_bin(3, r["mixed_tile"]) if r["pipe"] == "FP32"
+                                    else mixed_mufu_per_point_bin(3, r["mixed_tile"])),
+            "peak_source": "derived (not measured): 128 FP32 / 16 MUFU lanes/clk/SM x 152 SMs x 2070 MHz"}
 
 
 def slice_kernel_roofline(st0, st1, steps, n_det):
@@ -328,7 +347,7 @@ def e2e_run(g, w, steps, stream):
             "note": "ns_init from host arrays (data, PSD upload amortised over the steps) + ns_step_host"}
 
 
-def serving_stream(g, count=64, time_limit_s=240.0):
+def serving_stream(g, count=64, time_limit_s=240.0, max_chains=0):
     """The serving workload: `count` analyses arriving as a Poisson stream at
     2/s (durations 4-64 s at 20-2048 Hz, n_live U{500..2000}, k = n/2, SNR
     U[10, 40], 3 detectors, mixed precision), served by one ns_server that
@@ -350,7 +369,7 @@ def serving_stream(g, count=64, time_limit_s=240.0):
         reqs.append((r["arrival_s"], dict(kind=w.kind, lo=w.lo, hi=w.hi, data=data, psd=psd, f0=w.f0, df=w.df,
                                           pos=pos, xarm=xarm, yarm=yarm, n_live=w.n_live, k=w.k,
                                           steps_per_dim=w.steps_per_dim, seed=w.seed_sampler)))
-    srv = g.Server(precision=g.NS_MIXED, max_active=16)
+    srv = g.Server(precision=g.NS_MIXED, max_active=16, max_chains=max_chains)
     ids, arrival = [], []
     t0 = srv.time()
     nxt = 0

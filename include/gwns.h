@@ -334,9 +334,9 @@ typedef struct {
     int max_iter;          /* iteration cap per analysis [100000] */
     void *stream;          /* cudaStream_t [NULL: server-owned] */
     int max_chains;        /* admit while the running analyses' chains per iteration (their k)
-                              stay within this, the first always [0: 16 per SM, ~4 CTAs of
-                              chains per CTA slot]: past it the GPU is saturated and more
-                              analyses only lengthen each one's time to result */
+                              stay within this, the first always [0: 20 per SM]: past it the
+                              GPU is saturated and more analyses only lengthen each one's
+                              time to result */
 } ns_server_options;
 
 typedef struct {

@@ -231,7 +231,7 @@ int ns_server_create(ns_server **out, const ns_server_options *o) {
         int dev = 0, nsm = 152;
         cudaGetDevice(&dev);
         if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) nsm = 152;
-        s->o.max_chains = 16 * nsm;
+        s->o.max_chains = 20 * nsm;
     }
     if (o->stream) {
         s->stream = (cudaStream_t)o->stream;
