@@ -29,10 +29,11 @@
  *     over geometric coarse bins, and the ratio r = h/h0 interpolated linearly
  *     inside each bin from its values at the bin edges.
  *
- * Parity status: the aligned-spin gamma term (2.5PN spin-orbit) is parity
- * unpinned; the other spin terms are pinned through an independent published
- * form; the non-spinning phasing is pinned by re-deriving it from the PN energy
- * and flux. Everything is FP64 with the C library's cbrt/pow/log/sincos.
+ * Parity status: the non-spinning phasing is pinned by re-deriving it from the
+ * PN energy and flux, and so are the spin-orbit terms beta (1.5PN) and gamma
+ * (2.5PN), from the spin-orbit parts of the energy and flux; beta and sigma
+ * also against the Cutler-Flanagan mass-weighted form. Everything is FP64 with
+ * the C library's cbrt/pow/log/sincos.
  */
 #include <math.h>
 #include <stdint.h>

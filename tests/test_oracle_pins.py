@@ -138,6 +138,49 @@ def test_spin_terms_mass_weighted_form():
         assert p[4] - p0[4] == pytest.approx(-10 * sigma, rel=1e-13, abs=1e-13)
 
 
+def _spin_orbit_terms(eta, m1, m2, chi1, chi2):
+    ns = {"eta": eta, "S": m1 * m1 * chi1 + m2 * m2 * chi2, "Sig": m2 * chi2 - m1 * chi1, "d": m1 - m2}
+    out = {}
+    for line in open(os.path.join(GOLDEN, "pn_spin_orbit.txt")):
+        if not line.strip() or line.startswith("#"):
+            continue
+        name, expr = line.split(None, 1)
+        out[name] = float(eval(expr, {"__builtins__": {}}, ns))
+    return out
+
+
+def _energy_balance_series(eta, so):
+    """Coefficients a_k (k <= 5) of -E'(v)/F(v) / (v^-9 (5/32)/eta), the
+    integrand of the energy balance, with the spin-orbit terms `so` added."""
+    c = _energy_flux_coeffs(eta)
+    b = {0: 1.0, 1: 0.0, 2: c["f2"], 3: c["f3"] + so.get("f3s", 0.0), 4: c["f4"], 5: c["f5"] + so.get("f5s", 0.0)}
+    inv = {0: 1.0}
+    for k in range(1, 6):
+        inv[k] = -sum(b[i] * inv[k - i] for i in range(1, k + 1))
+    num = {0: 1.0, 1: 0.0, 2: 2 * c["e2"], 3: 2.5 * so.get("e3s", 0.0), 4: 3 * c["e4"],
+           5: 3.5 * so.get("e5s", 0.0)}
+    return {k: sum(num[i] * inv[k - i] for i in range(k + 1)) for k in range(6)}
+
+
+@pytest.mark.parametrize("q,chi1,chi2", [(0.8, 0.3, 0.0), (0.3, 0.0, 0.4), (0.5, -0.45, 0.2), (1.0, 0.2, -0.1)])
+def test_spin_orbit_phasing_matches_energy_balance(q, chi1, chi2):
+    """The 1.5PN and 2.5PN spin-orbit phase terms (4 beta and -gamma) from the
+    spin-orbit parts of the energy and flux: term-by-term integration of the
+    energy balance gives psi_3 = 4 a_3 and, from the ln v term of the 2.5PN
+    order, psi_5 = -(40/9) a_5 (the same steps as the non-spinning pin)."""
+    eta = q / (1 + q) ** 2
+    m1, m2 = 1.0 / (1 + q), q / (1 + q)
+    a = _energy_balance_series(eta, _spin_orbit_terms(eta, m1, m2, chi1, chi2))
+    a0 = _energy_balance_series(eta, {})
+    v = 0.21
+    delta = (1 - q) / (1 + q)
+    p = oracle.pn_phi(eta, delta, chi1, chi2, v)
+    p0 = oracle.pn_phi(eta, delta, 0.0, 0.0, v)
+    log_factor = 1.0 + 3.0 * math.log(v * math.sqrt(6.0))
+    assert p[3] - p0[3] == pytest.approx(4 * (a[3] - a0[3]), rel=1e-12, abs=1e-12)
+    assert (p[5] - p0[5]) / log_factor == pytest.approx(-40.0 / 9.0 * (a[5] - a0[5]), rel=1e-12, abs=1e-12)
+
+
 # ----------------------------------------------------------------- amplitude
 def test_amplitude_matches_time_domain_chirp():
     """Face-on |h_+(f)| = h0(f) / (2 sqrt(fdot)) with the quadrupole chirp
