@@ -744,7 +744,8 @@ __device__ __forceinline__ double warp_max(double v) {
 // eight bins, T <- T + T eps8_d + S across them, eps8_d = exp(-8 i beta_d) - 1
 // (the magnitude error of a rounded unit step builds up over seven steps at
 // most). These detectors take no sine or cosine per bin. Tiles of 16 bins or
-// fewer keep a sine and cosine per detector and bin (tile_bins_direct). Each
+// fewer keep a sine and cosine per detector and bin (tile_bins_direct), as does
+// the serving kernel at every tile length. Each
 // tile's sums are flushed into double-float accumulators; the only per-bin
 // table is the weighted data.
 constexpr int TK = 7;
