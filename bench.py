@@ -48,7 +48,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # detectors, in FMA-equivalents: 8 basis FMAs + one sincos (32 FMA-equivalents
 # on this GPU) + per detector 4 (phasor product) + 4 (complex MAC) + 4
 # (phasor rotation). 1 FMA = 2 flops.
-K_SLICE_FP64_C1_DRAM_BYTES = 365824   # re-captured after the kernel changes
+K_SLICE_FP64_C1_DRAM_BYTES = 547328   # ncu dram__bytes_read.sum + dram__bytes_write.sum of the current kernel
 
 
 def fp64_flops_per_point_bin(n_det: int) -> float:
