@@ -306,6 +306,13 @@ int ns_set_live(ns_ctx *ctx, const double *u, const double *logl);
  * results. *slots (may be NULL) receives the choice. */
 int ns_autotune(ns_ctx *ctx, int trials, int *slots);
 
+/* Autotune the batched likelihood (ns_eval_lnl*): time `trials` launches (>= 1)
+ * on the context's live points with 1, 2, 4 and 8 warps per point, after one
+ * warm-up launch each, and keep the fastest for this context (as if its
+ * options had set warps_per_point). Nothing of the run changes; these launches
+ * are not counted in ns_stats. *warps (may be NULL) receives the choice. */
+int ns_autotune_eval(ns_ctx *ctx, int trials, int *warps);
+
 /* Synchronise the context's stream. */
 int ns_sync(ns_ctx *ctx);
 

@@ -133,6 +133,7 @@ def lib():
         L.ns_set_live.argtypes = [vp, vp, vp]
         L.ns_sync.argtypes = [vp]
         L.ns_autotune.argtypes = [vp, ip, P(ip)]
+        L.ns_autotune_eval.argtypes = [vp, ip, P(ip)]
         L.ns_checkpoint.argtypes = [vp, vp, P(ctypes.c_size_t)]
         L.ns_restore.argtypes = [vp, vp, ctypes.c_size_t]
         L.ns_free.argtypes = [vp]; L.ns_free.restype = None
@@ -151,7 +152,7 @@ def lib():
                      "ns_get_stats", "ns_eval_lnl", "ns_eval_lnl_host", "ns_eval_lnl_theta",
                      "ns_eval_lnl_host_noalloc",
                      "ns_waveform", "ns_prior_transform", "ns_optimal_snr2", "ns_get_live", "ns_set_live", "ns_sync",
-                     "ns_autotune", "ns_checkpoint", "ns_restore"):
+                     "ns_autotune", "ns_autotune_eval", "ns_checkpoint", "ns_restore"):
             getattr(L, name).restype = ctypes.c_int
         _LIB = L
     return _LIB
@@ -388,6 +389,12 @@ class Sampler:
         s = ctypes.c_int()
         _check(lib().ns_autotune(self._ctx, trials, ctypes.byref(s)), "ns_autotune")
         return s.value
+
+    def autotune_eval(self, trials: int = 3) -> int:
+        """Pick the fastest warps per point for the batched likelihood."""
+        w = ctypes.c_int()
+        _check(lib().ns_autotune_eval(self._ctx, trials, ctypes.byref(w)), "ns_autotune_eval")
+        return w.value
 
 
 def _fill_inputs(kind, lo, hi, data, psd, f0, df, pos, xarm, yarm, ideal, coarse_bins, theta_fid, keep):

@@ -872,6 +872,37 @@ int ns_autotune(ns_ctx *c, int trials, int *slots) {
     return NS_OK;
 }
 
+int ns_autotune_eval(ns_ctx *c, int trials, int *warps) {
+    if (!c || trials < 1) return NS_ERR_INVALID_ARG;
+    const int m = c->n;
+    int rc = ensure_scratch(c, sizeof(double) * (size_t)m);
+    if (rc) return rc;
+    double *out = c->scratch;
+    const int cand[4] = {1, 2, 4, 8};
+    float best_ms = 3.4e38f;
+    int best = choose_warps(c);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    for (int i = 0; i < 4 && e == cudaSuccess; i++) {
+        e = launch_eval(c->M, c->T, c->precision, cand[i], c->live_u, 0, m, out, nullptr, c->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+        for (int t = 0; t < trials && e == cudaSuccess; t++)
+            e = launch_eval(c->M, c->T, c->precision, cand[i], c->live_u, 0, m, out, nullptr, c->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && ms < best_ms) { best_ms = ms; best = cand[i]; }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(e);
+    c->warps = best;
+    if (warps) *warps = best;
+    return NS_OK;
+}
+
 namespace {
 struct CkptHeader {
     char magic[8];          // "GWNSCKP2"

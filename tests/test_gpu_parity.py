@@ -474,6 +474,26 @@ def test_autotune_keeps_the_trajectory(gw):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
+def test_autotune_eval_keeps_parity(gw, precision):
+    """The batched likelihood's warps-per-point autotuner picks one of 1, 2, 4,
+    8; its launches are not counted, and the likelihood then still matches the
+    oracle (8000 bins at 1/32 Hz: 32-bin tiles in the mixed form)."""
+    w, pb, th = problem("c1", N=8000, df=0.03125)
+    u = pts_for(pb, th)
+    want = pb.loglike(u)
+    with sampler_from(gw, pb, precision, n_live=64) as sp:
+        before = sp.stats()["batch_evals"]
+        chosen = sp.autotune_eval(trials=2)
+        assert chosen in (1, 2, 4, 8)
+        assert sp.stats()["batch_evals"] == before
+        got = sp.eval_lnl(u)
+    if precision == 0:
+        assert np.max(np.abs(got - want) / np.maximum(1.0, np.abs(want))) < FP64_RTOL
+    else:
+        assert np.max(np.abs(got - want)) < MIXED_ATOL
+
+
+@pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("kernel", [0, 1])
 def test_checkpoint_resume_is_bit_identical(gw, precision, kernel):
     """A run resumed from a checkpoint continues bit-identically (for the
