@@ -44,3 +44,23 @@ def test_replica_aggregation_two_ranks():
 def test_single_rank_passthrough():
     import bench
     assert bench.reduce_ranks(None, 12.5, 7) == (12.5, 7.0)
+
+
+def test_mixed_roofline_takes_the_binding_pipe():
+    """The mixed form's roofline is that of the pipe its instruction counts bind:
+    the FP32 pipe for the rotation form (tiles of 32+ bins), the MUFU pipe for
+    the direct tiled form (6 sin/cos per point-bin at 3 detectors)."""
+    import bench
+    assert bench.mixed_fp32_per_point_bin(3, 128) == 37.5
+    assert bench.mixed_mufu_per_point_bin(3, 128) == 2.0
+    assert bench.mixed_fp32_per_point_bin(3, 16) == 45.0
+    assert bench.mixed_mufu_per_point_bin(3, 16) == 6.0
+    assert bench.mixed_fp32_per_point_bin(3, 0) == 156.0
+    pb, secs = 1e12, 1.0
+    frac, pipe = bench.mixed_roofline(pb, secs, 3, 128)
+    assert pipe == "FP32" and abs(frac - pb * 37.5 / bench.FP32_LANE_OPS) < 1e-12
+    frac, pipe = bench.mixed_roofline(pb, secs, 3, 16)
+    assert pipe == "SFU" and abs(frac - pb * 6.0 / bench.SFU_LANE_OPS) < 1e-12
+    # one detector in the direct form: 23 FP32 against 2 MUFU -> FP32 binds (23/128 > 2/16)
+    frac, pipe = bench.mixed_roofline(pb, secs, 1, 16)
+    assert pipe == "FP32"
