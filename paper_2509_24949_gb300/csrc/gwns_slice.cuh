@@ -454,6 +454,9 @@ __device__ int walk_plan(const Model &M, const StepArgs &A, const Chain &c, int 
     return ns;
 }
 
+// ROTOK: the tiled mixed form sums tiles of 32 bins or more by rotation
+// (tile_bins_rot); without it every tile length takes the direct form, and
+// the kernel compiles one form only.
 template <int PREC, int NDET, int S, int W = S, bool ROTOK = true>
 __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, const int chain) {
     __shared__ Coef coef[S];
