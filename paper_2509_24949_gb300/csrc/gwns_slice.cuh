@@ -85,51 +85,77 @@ __device__ __forceinline__ void warp_point_coef(const Model &M, const Tables &T,
     (void)lane;
 }
 
+// Points per CTA of the batched likelihood: the coefficient stage packs up to
+// four points into one warp pass (8 lanes each), so the per-point FP64 work that
+// binds the mixed form on grids of a few thousand bins is shared. GB300, 8192
+// prior draws of the 64,897-bin workload: 4.0e7 -> 5.9e7 evals/s. Where the
+// bins bind (the FP64 form; 519,169 bins) the coarser grid of CTAs cost 4-9%,
+// and there, as for physical-parameter and toy inputs, a CTA takes one point.
+constexpr int EVAL_PPC = 4;
+
 template <int PREC, int NDET, int W>
 __global__ void __launch_bounds__(W * 32) k_eval(Model M, Tables T, const double *in, int in_is_theta,
-                                                 int m, double *logl, RunState *st) {
-    __shared__ Coef coef;
-    __shared__ CoefMixed cm;
+                                                 int m, int ppc, double *logl, RunState *st) {
+    __shared__ Coef coef[EVAL_PPC];
+    __shared__ CoefMixed cm[EVAL_PPC];
     __shared__ double red[W][2 * MAXDET];
     __shared__ double lval;
-    __shared__ double pt[NPARAM + MAXD];
-    const int i = blockIdx.x;
-    if (i >= m) return;
+    __shared__ double pt[EVAL_PPC][NPARAM + MAXD];
+    const int i0 = blockIdx.x * ppc;
+    if (i0 >= m) return;
+    const int np = m - i0 < ppc ? m - i0 : ppc;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int stride_in = in_is_theta ? NPARAM : M.dim;
-    if (threadIdx.x < stride_in) pt[threadIdx.x] = in[(size_t)i * stride_in + threadIdx.x];
+    for (int t = threadIdx.x; t < np * stride_in; t += W * 32)
+        pt[t / stride_in][t % stride_in] = in[(size_t)i0 * stride_in + t];
     __syncthreads();
-    if ((threadIdx.x >> 5) == 0) warp_point_coef(M, T, pt, in_is_theta, PREC, &coef, &cm);
+    if (warp == 0) {
+        if (ppc == 1) {
+            warp_point_coef(M, T, pt[0], in_is_theta, PREC, &coef[0], &cm[0]);
+        } else {
+            point_coef_group(M, T, pt[0], NPARAM + MAXD, coef, np, 0);
+            __syncwarp();
+            if (PREC == 1)
+                for (int p = 0; p < np; p++)
+                    coef_to_mixed_warp(coef[p], M.n_det, M.df, &cm[p], M.rb ? T.rb.fid : nullptr, M.tlg >= 5);
+        }
+    }
     __syncthreads();
-    if (M.rb) {
-        // relative-binning sums: one warp
-        if ((threadIdx.x >> 5) == 0) {
-            const int lane = threadIdx.x & 31;
-            const double v = rb_loglike_warp<NDET, PREC>(M, T.rb, coef, cm, lane);
-            if (lane == 0) {
-                logl[i] = v;
-                if (st) atomicAdd(&st->eval_points, 1ull);
+    for (int p = 0; p < np; p++) {
+        if (M.rb) {
+            // relative-binning sums: one warp
+            if (warp == 0) {
+                const double v = rb_loglike_warp<NDET, PREC>(M, T.rb, coef[p], cm[p], lane);
+                if (lane == 0) {
+                    logl[i0 + p] = v;
+                    if (st) atomicAdd(&st->eval_points, 1ull);
+                }
+            }
+            continue;
+        }
+        cta_loglike_bins<PREC, NDET, W>(M, T, coef[p], cm[p], red, &lval);
+        if (threadIdx.x == 0) {
+            logl[i0 + p] = lval;
+            if (st) {
+                atomicAdd(&st->eval_points, 1ull);
+                if (M.model != M_TOY) atomicAdd(&st->eval_point_bins, (unsigned long long)(coef[p].jcut + 1));
             }
         }
-        return;
-    }
-    cta_loglike_bins<PREC, NDET, W>(M, T, coef, cm, red, &lval);
-    if (threadIdx.x == 0) {
-        logl[i] = lval;
-        if (st) {
-            atomicAdd(&st->eval_points, 1ull);
-            if (M.model != M_TOY) atomicAdd(&st->eval_point_bins, (unsigned long long)(coef.jcut + 1));
-        }
+        __syncthreads();    // red and lval serve the next point
     }
 }
 
 template <int PREC, int NDET>
 cudaError_t eval_launch(const Model &M, const Tables &T, int warps, const double *in, int th, int m,
                         double *logl, RunState *st, cudaStream_t s) {
+    const int nbins = M.rb ? T.rb.nb : M.N;
+    const int ppc = (PREC == 1 && M.model == M_GW && !th && nbins <= 262144) ? EVAL_PPC : 1;
+    const int g = (m + ppc - 1) / ppc;
     switch (warps) {
-        case 1: k_eval<PREC, NDET, 1><<<m, 32, 0, s>>>(M, T, in, th, m, logl, st); break;
-        case 2: k_eval<PREC, NDET, 2><<<m, 64, 0, s>>>(M, T, in, th, m, logl, st); break;
-        case 4: k_eval<PREC, NDET, 4><<<m, 128, 0, s>>>(M, T, in, th, m, logl, st); break;
-        default: k_eval<PREC, NDET, 8><<<m, 256, 0, s>>>(M, T, in, th, m, logl, st); break;
+        case 1: k_eval<PREC, NDET, 1><<<g, 32, 0, s>>>(M, T, in, th, m, ppc, logl, st); break;
+        case 2: k_eval<PREC, NDET, 2><<<g, 64, 0, s>>>(M, T, in, th, m, ppc, logl, st); break;
+        case 4: k_eval<PREC, NDET, 4><<<g, 128, 0, s>>>(M, T, in, th, m, ppc, logl, st); break;
+        default: k_eval<PREC, NDET, 8><<<g, 256, 0, s>>>(M, T, in, th, m, ppc, logl, st); break;
     }
     return cudaGetLastError();
 }
