@@ -198,6 +198,48 @@ def test_amplitude_matches_time_domain_chirp():
         assert hc == pytest.approx(-1j * hp, rel=1e-12, abs=0)
 
 
+def test_polarizations_edge_on():
+    """Edge-on (cos i = 0): the cross polarisation vanishes and |h_+| is half
+    the face-on amplitude of the quadrupole chirp, h0 / (4 sqrt(fdot))."""
+    th = np.zeros(gi.NPARAM)
+    th[gi.P_MC], th[gi.P_Q], th[gi.P_DL], th[gi.P_COSI], th[gi.P_PHIC] = 18.0, 0.7, 410.0, 0.0, 0.4
+    tmc = th[gi.P_MC] * TSUN
+    D = th[gi.P_DL] * MPC
+    for f in [20.0, 55.5, 131.0]:
+        hp, hc = oracle.polarizations(th, f)
+        h0 = 4 * C_SI * tmc ** (5 / 3) * (math.pi * f) ** (2 / 3) / D
+        fdot = 96 / 5 * math.pi ** (8 / 3) * tmc ** (5 / 3) * f ** (11 / 3)
+        assert hc == 0
+        assert abs(hp) == pytest.approx(h0 / (4 * math.sqrt(fdot)), rel=1e-12, abs=0)
+
+
+def test_polarizations_orientation_average_is_four_fifths():
+    """Averaged over an isotropic orientation (cos i uniform on [-1, 1]), the
+    polarisation power (|h_+|^2 + |h_x|^2) / |h_+(face-on)|^2 is 4/5 (the
+    quadrupole radiation pattern (1 + cos^2 i)^2/4 + cos^2 i). Gauss-Legendre
+    quadrature over the oracle's own polarisations; a wrong power of cos i in
+    either polarisation changes the average."""
+    th = np.zeros(gi.NPARAM)
+    th[gi.P_MC], th[gi.P_Q], th[gi.P_DL], th[gi.P_PHIC] = 27.0, 0.55, 800.0, 2.1
+    x, w = np.polynomial.legendre.leggauss(8)
+    for f in [25.0, 90.0]:
+        th[gi.P_COSI] = 1.0
+        ref = abs(oracle.polarizations(th, f)[0]) ** 2
+        avg = 0.0
+        for ci, wi in zip(x, w):
+            th[gi.P_COSI] = ci
+            hp, hc = oracle.polarizations(th, f)
+            avg += 0.5 * wi * (abs(hp) ** 2 + abs(hc) ** 2) / ref
+        assert avg == pytest.approx(0.8, rel=1e-13)
+        # and the two polarisations separately: <(1 + c^2)^2/4> = 7/15, <c^2> = 1/3
+        ap = sum(0.5 * wi * abs(oracle.polarizations(np.where(np.arange(gi.NPARAM) == gi.P_COSI, ci, th), f)[0]) ** 2
+                 for ci, wi in zip(x, w)) / ref
+        ac = sum(0.5 * wi * abs(oracle.polarizations(np.where(np.arange(gi.NPARAM) == gi.P_COSI, ci, th), f)[1]) ** 2
+                 for ci, wi in zip(x, w)) / ref
+        assert ap == pytest.approx(7 / 15, rel=1e-13)
+        assert ac == pytest.approx(1 / 3, rel=1e-13)
+
+
 def test_equal_mass_limit_is_finite():
     """q -> 1: (m1 - m2)/M -> 0 and the likelihood stays finite."""
     w = gi.workload("c1")
@@ -238,17 +280,87 @@ def test_antenna_psi_invariance_and_bounds():
         assert vals[0] <= 1.0 + 1e-14
 
 
+def _textbook_pattern(cos_th, phi, psi):
+    """F+ and Fx of an L-shaped detector with arms along x and y, for a source
+    at polar angle th and azimuth phi in the detector frame and polarisation
+    angle psi: the standard interferometer response of the gravitational-wave
+    literature (e.g. Sathyaprakash and Schutz, Living Rev. Rel. 12 (2009) 2,
+    eq. 34), written here from that statement."""
+    a = 0.5 * (1.0 + cos_th * cos_th) * math.cos(2 * phi)
+    b = cos_th * math.sin(2 * phi)
+    return a * math.cos(2 * psi) - b * math.sin(2 * psi), a * math.sin(2 * psi) + b * math.cos(2 * psi)
+
+
 def test_antenna_textbook_pole_detector():
-    """Arms along x and y at the north pole: F+^2 + Fx^2 =
-    (1 + cos^2 th)^2 cos^2(2 ph)/4 + cos^2 th sin^2(2 ph), th = pi/2 - dec, ph = ra."""
+    """Arms along x and y at the north pole: F+ and Fx each equal the textbook
+    pattern with th = pi/2 - dec, phi = RA and the textbook polarisation angle
+    pi/2 - psi (the wave frame of Anderson et al. 2001 measures psi from the
+    other axis and in the opposite sense). Swapping F+ and Fx or flipping the
+    sign of either fails this."""
     x, y = np.array([1.0, 0, 0]), np.array([0, 1.0, 0])
     rng = np.random.default_rng(5)
-    for _ in range(25):
+    for _ in range(40):
         ra, sd, psi = rng.uniform(0, 2 * math.pi), rng.uniform(-1, 1), rng.uniform(0, math.pi)
         fp, fc = oracle.antenna(x, y, ra, sd, psi)
-        ct = sd
-        want = (1 + ct * ct) ** 2 * math.cos(2 * ra) ** 2 / 4 + ct * ct * math.sin(2 * ra) ** 2
-        assert fp * fp + fc * fc == pytest.approx(want, rel=1e-12, abs=1e-14)
+        want_p, want_c = _textbook_pattern(sd, ra, 0.5 * math.pi - psi)
+        assert fp == pytest.approx(want_p, abs=1e-13)
+        assert fc == pytest.approx(want_c, abs=1e-13)
+    # special directions, with the textbook angle psi' = pi/2 - psi: overhead
+    # (th = 0) F+ = cos 2psi' = -cos 2psi and Fx = sin 2psi' = sin 2psi
+    for psi in (0.0, 0.3, 1.1):
+        fp, fc = oracle.antenna(x, y, 0.0, 1.0, psi)
+        assert fp == pytest.approx(-math.cos(2 * psi), abs=1e-14)
+        assert fc == pytest.approx(math.sin(2 * psi), abs=1e-14)
+    # in the arms' plane along the x arm (th = pi/2, phi = 0) only the y arm
+    # responds: half the overhead response
+    for psi in (0.2, 0.9):
+        fp, fc = oracle.antenna(x, y, 0.0, 0.0, psi)
+        assert fp == pytest.approx(-0.5 * math.cos(2 * psi), abs=1e-14)
+        assert fc == pytest.approx(0.5 * math.sin(2 * psi), abs=1e-14)
+    # along the diagonal between the arms in their plane (phi = pi/4): no response
+    for psi in (0.2, 0.9):
+        fp, fc = oracle.antenna(x, y, 0.25 * math.pi, 0.0, psi)
+        assert fp == pytest.approx(0.0, abs=1e-14)
+        assert fc == pytest.approx(0.0, abs=1e-14)
+
+
+def test_antenna_rotated_arms_shift_the_azimuth():
+    """Arms rotated by alpha about the local vertical (pole detector): the
+    pattern is the textbook one at azimuth phi - alpha."""
+    rng = np.random.default_rng(8)
+    for alpha in (0.4, 1.3, -2.0):
+        x = np.array([math.cos(alpha), math.sin(alpha), 0.0])
+        y = np.array([-math.sin(alpha), math.cos(alpha), 0.0])
+        for _ in range(10):
+            ra, sd, psi = rng.uniform(0, 2 * math.pi), rng.uniform(-1, 1), rng.uniform(0, math.pi)
+            fp, fc = oracle.antenna(x, y, ra, sd, psi)
+            want_p, want_c = _textbook_pattern(sd, ra - alpha, 0.5 * math.pi - psi)
+            assert fp == pytest.approx(want_p, abs=1e-13)
+            assert fc == pytest.approx(want_c, abs=1e-13)
+
+
+def test_antenna_sky_average_is_one_fifth():
+    """Averaged over an isotropic sky and polarisation angle, <F+^2> = <Fx^2> =
+    1/5 and <F+ Fx> = 0 for any orthogonal-arm detector (quadrature: Gauss-
+    Legendre in sin dec, trapezoid in RA and psi, exact for these trigonometric
+    polynomials)."""
+    pos, xa, ya = gi.detectors(13, 2)
+    xg, wg = np.polynomial.legendre.leggauss(12)
+    ras = np.linspace(0, 2 * math.pi, 16, endpoint=False)
+    psis = np.linspace(0, math.pi, 8, endpoint=False)
+    for i in range(2):
+        spp = scc = spc = 0.0
+        for sd, wsd in zip(xg, wg):
+            for ra in ras:
+                for psi in psis:
+                    fp, fc = oracle.antenna(xa[i], ya[i], ra, sd, psi)
+                    wt = 0.5 * wsd / (len(ras) * len(psis))
+                    spp += wt * fp * fp
+                    scc += wt * fc * fc
+                    spc += wt * fp * fc
+        assert spp == pytest.approx(0.2, abs=1e-12)
+        assert scc == pytest.approx(0.2, abs=1e-12)
+        assert spc == pytest.approx(0.0, abs=1e-12)
 
 
 def test_antenna_zenith_and_delay():
@@ -527,14 +639,77 @@ def test_toy_evidence_analytic(d):
     """Analytic log Z = -d ln 20 for a normalised Gaussian well inside [-10,10]^d."""
     pb = oracle.toy_problem(d)
     truth = -d * math.log(20.0)
+    # information of the posterior N(0, Sigma) against the uniform prior on the
+    # box: H = d ln 20 - ln det(2 pi e Sigma)/2
+    h_true = d * math.log(20.0) - 0.5 * np.linalg.slogdet(2 * math.pi * math.e * gi.toy_covariance(d))[1]
     hits = 0
     seeds = range(6)
+    hs = []
     for s in seeds:
         r = ons.run(pb, n_live=200, k=100, steps=5 * d, seed=100 + s, replicates=50)
         sig = max(r["dlogZ"], 1e-3)
         hits += abs(r["logZ"] - truth) < 3 * sig
         assert 0.5 * r["dlogZ_info"] < r["dlogZ"] < 2.5 * r["dlogZ_info"]
+        hs.append(r["H"])
     assert hits >= 5
+    # per run the estimate scatters by ~0.13 at n = 200 (measured over seeds)
+    assert np.all(np.abs(np.array(hs) - h_true) < 0.6)
+    assert abs(np.mean(hs) - h_true) < 0.2
+
+
+def _closed_form_state(n, k, iters, dead_level, live_level, d=2):
+    """A run state built without the sampler: `iters` iterations of k deletions
+    from n live points, every dead point at log L = dead_level, the final live
+    points at live_level; the enclosed prior mass after the j-th deletion of an
+    iteration is X_j = X_{j-1} exp(-1/(n - j + 1)), so the weight of that point
+    is X_{j-1} - X_j. Returns the state and the closed-form X sequence."""
+    logx = [0.0]
+    st = ons.NSState(live_u=np.full((n, d), 0.5), live_logl=np.full(n, float(live_level)))
+    for _ in range(iters):
+        lw = []
+        for j in range(1, k + 1):
+            x0 = logx[-1]
+            x1 = x0 - 1.0 / (n - j + 1)
+            lw.append(math.log(math.exp(x0) - math.exp(x1)))
+            logx.append(x1)
+        st.dead_u.append(np.full((k, d), 0.5))
+        st.dead_logl.append(np.full(k, float(dead_level)))
+        st.dead_logw.append(np.array(lw))
+        st.dead_nlive.append(n - np.arange(k, dtype=np.float64))
+    st.logX = logx[-1]
+    st.logZ = float(np.logaddexp.reduce(np.concatenate(st.dead_logw) + dead_level))
+    return st, logx
+
+
+@pytest.mark.parametrize("dead_level,live_level", [(0.0, 0.0), (0.0, 6.0), (-3.0, 2.5)])
+def test_finalize_closed_forms(dead_level, live_level):
+    """finalize() against closed forms on two-level likelihoods: the final live
+    points add the mass X_k - X_end, X_end = X_k exp(-sum_{j=1..n} 1/j); with
+    mass M_dead = 1 - X_k at L_dead and M_live = X_k - X_end at L_live,
+    Z = M_dead L_dead + M_live L_live, H = sum_g (M_g L_g / Z) ln(L_g / Z), and
+    the Kish ESS is (sum w L)^2 / sum (w L)^2 over the individual weights."""
+    n, k, iters = 40, 20, 5
+    st, logx = _closed_form_state(n, k, iters, dead_level, live_level)
+    r = ons.finalize(st, seed=1, replicates=8)
+    x_k = math.exp(logx[-1])
+    x_end = x_k * math.exp(-sum(1.0 / j for j in range(1, n + 1)))
+    m_dead, m_live = 1.0 - x_k, x_k - x_end
+    Z = m_dead * math.exp(dead_level) + m_live * math.exp(live_level)
+    assert r["logZ"] == pytest.approx(math.log(Z), abs=1e-12)
+    H = (m_dead * math.exp(dead_level) / Z * (dead_level - math.log(Z))
+         + m_live * math.exp(live_level) / Z * (live_level - math.log(Z)))
+    assert r["H"] == pytest.approx(H, abs=1e-12)
+    # individual weights: the dead ones from the closed-form X sequence, the
+    # live ones continuing it with Delta_j = 1/(n - j + 1)
+    xs = list(np.exp(logx))
+    for j in range(1, n + 1):
+        xs.append(xs[-1] * math.exp(-1.0 / (n - j + 1)))
+    w = -np.diff(np.array(xs))
+    lv = np.concatenate([np.full(k * iters, dead_level), np.full(n, live_level)])
+    wl = w * np.exp(lv)
+    assert r["ess"] == pytest.approx(wl.sum() ** 2 / np.sum(wl ** 2), rel=1e-12)
+    assert len(r["logw"]) == k * iters + n
+    assert np.allclose(np.exp(r["logw"]), w, rtol=1e-12, atol=0)
 
 
 def test_log_x_shrinkage_statistics():
