@@ -1,26 +1,32 @@
 """Benchmark: likelihood evaluations per second inside nested-sampling
-iterations on one GB300 (plus time-to-logZ, per-step latency and the mixed
-precision form), on the 3-detector / 11-parameter / 4017-bin workload with
-1000 live points and 500 chains per iteration.
+iterations on one GB300, in mixed precision, on the largest single-GPU
+workload: 3 detectors, 11 parameters, 256 s at 20-2048 Hz (519,169 bins),
+2000 live points and 1000 chains of 55 slice steps per iteration.
 
-A step is one ns_step: selection of the 500 lowest live points, evidence
-update, survivors' covariance and Cholesky factor, 500 slice-sampling chains
-of 55 steps each (every candidate's TaylorF2 likelihood on the GPU), and the
-stopping test. Inputs are synthetic and seeded (gwinputs); the injection is
-made with the library's own waveform.
+A step is one ns_step: selection of the 1000 lowest live points, evidence
+update, survivors' covariance and Cholesky factor, 1000 slice-sampling chains
+(every candidate's TaylorF2 likelihood on the GPU), and the stopping test.
+Every timed step is the analysis' first iteration, restored from the
+checkpoint taken after ns_init, so that the CPU oracle (--impl reference)
+times a sample of exactly the same chains. The whole run to the stopping rule
+(time to log Z) and the FP64 form on the same iteration are reported beside
+it. Inputs are synthetic and seeded (gwinputs); the injection is made with the
+library's own waveform.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
 --impl reference times the CPU oracle (plain FP64 C, all host cores) on a
-bounded sample of the same workload. Under torchrun each rank runs an
+bounded sample of the same chains. Under torchrun each rank runs an
 independent replica (different seeds); rank 0 prints one JSON line.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -34,9 +40,14 @@ sys.path.insert(0, ROOT)
 
 import gwinputs as gi  # noqa: E402
 
-METRIC = "logL evals/sec (FP64, in nested-sampling iterations)"
+METRIC = "logL evals/sec (mixed precision, in nested-sampling iterations)"
 UNIT = "evals/s"
-WORKLOAD = "c1"
+WORKLOAD = "c4"
+# chains of the first iteration the oracle times per reference step, and the
+# slice steps of each it runs (the first ones of the chain: the same draws and
+# evaluations the GPU makes at the start of those chains)
+REF_CHAINS = 32
+REF_STEPS = 2
 CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -44,11 +55,44 @@ CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.ac
 # (1.25 TFLOP/s nominal over 152 SMs at 2070 MHz).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
-# Algorithmic FP64 work of one point-bin of the FP64 likelihood with D
-# detectors, in FMA-equivalents: 8 basis FMAs + one sincos (32 FMA-equivalents
-# on this GPU) + per detector 4 (phasor product) + 4 (complex MAC) + 4
-# (phasor rotation). 1 FMA = 2 flops.
-K_SLICE_FP64_C1_DRAM_BYTES = 547328   # ncu dram__bytes_read.sum + dram__bytes_write.sum of the current kernel
+FP32_LANE_OPS = 152 * 128 * 2.070e9    # FP32 pipe: 128 lanes/clk/SM x 152 SMs x 2070 MHz
+SFU_LANE_OPS = 152 * 16 * 2.070e9      # MUFU (sin, cos): 16 lanes/clk/SM x 152 SMs x 2070 MHz
+# sources of the slice-update kernel; a DRAM-traffic summary counts only while
+# the hash it records matches these files
+KERNEL_SOURCES = ("gwns_slice.cuh", "gwns_device.cuh", "gwns_kernels.cuh")
+TRAFFIC_SUMMARY = os.path.join(ROOT, "profiles", "k_slice_mixed_c4_traffic.md")
+
+
+def config_dict(ws: int) -> dict:
+    """The workload's description, identical in both arms."""
+    return {"workload": "c4: 3 detectors, 11 parameters (aligned-spin TaylorF2), 256 s at 20-2048 Hz "
+                        "(519,169 bins), chirp mass U[1.1,1.5], SNR 30, n_live=2000, k=1000, 55 slice steps "
+                        "per chain, mixed precision; each step is the first nested-sampling iteration "
+                        "(restored from the post-initialisation checkpoint)",
+            "parallelism": f"replicas{ws}", "l2": "flushed before every timed step (256 MB write)"}
+
+
+def kernel_source_sha16() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2509_24949_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM bytes per slice-update launch from the committed ncu summary, or
+    None once the kernel's sources have changed since it was captured."""
+    try:
+        txt = open(TRAFFIC_SUMMARY).read()
+    except OSError:
+        return None, None
+    m_sha = re.search(r"source_sha16:\s*([0-9a-f]{16})", txt)
+    m_b = re.search(r"dram_bytes_per_launch:\s*([0-9]+)", txt)
+    m_pb = re.search(r"point_bins_per_launch:\s*([0-9]+)", txt)
+    if not (m_sha and m_b) or m_sha.group(1) != kernel_source_sha16():
+        return None, None
+    return int(m_b.group(1)), (int(m_pb.group(1)) if m_pb else None)
 
 
 def fp64_flops_per_point_bin(n_det: int) -> float:
@@ -136,12 +180,57 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def build_workload(g, precision, seed_offset=0):
-    w = gi.workload(WORKLOAD)
+def build_workload(name=WORKLOAD, seed_offset=0):
+    w = gi.workload(name)
     w.seed_sampler += 100 * seed_offset
     w.seed_noise += 100 * seed_offset
     w.seed_injection += 100 * seed_offset
     return w
+
+
+def workload_data(g, w, stream):
+    """Host inputs of a workload: strain (library waveform at the injection,
+    plus seeded noise), PSD and detector geometry."""
+    probe, th = g.make_analysis(w, precision=g.NS_FP64, n_live=2, k=1, stream=stream.cuda_stream)
+    data = probe.waveform(th)
+    probe.close()
+    psd = np.tile(gi.psd_analytic(w.freqs()), (w.n_det, 1))
+    if w.noise:
+        data = data + gi.noise(w.seed_noise, psd, w.df)
+    pos, xarm, yarm = gi.detectors(w.seed_geometry, w.n_det)
+    return dict(data=data, psd=psd, pos=pos, xarm=xarm, yarm=yarm), th
+
+
+def sampler_on(g, w, inputs, precision, stream, **kw):
+    args = dict(kind=w.kind, lo=w.lo, hi=w.hi, f0=w.f0, df=w.df, n_live=w.n_live, k=w.k,
+                steps_per_dim=w.steps_per_dim, precision=precision, seed=w.seed_sampler,
+                stream=stream.cuda_stream, **inputs)
+    args.update(kw)
+    return g.Sampler(**args)
+
+
+def timed_first_iterations(sp, blob, stream, steps, flush):
+    """`steps` repetitions of the analysis' first iteration (restore, L2
+    flush, then CUDA events on the library's stream around ns_step); returns
+    per-step ms and the counters' differences over the timed steps."""
+    import torch
+    ms, ev0, pb0, k0 = [], 0, 0, [0.0] * 5
+    evals, pbins, kern = 0, 0, [0.0] * 5
+    for _ in range(steps):
+        sp.restore(blob)
+        s0 = sp.stats()
+        flush()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sp.step()
+        b.record(stream)
+        b.synchronize()
+        s1 = sp.stats()
+        ms.append(a.elapsed_time(b))
+        evals += s1["evals"] - s0["evals"]
+        pbins += s1["point_bins"] - s0["point_bins"]
+        kern = [x + (q - p) for x, p, q in zip(kern, s0["kernel_ms"], s1["kernel_ms"])]
+    return ms, evals, pbins, kern
 
 
 def run_gpu(args):
@@ -155,58 +244,46 @@ def run_gpu(args):
     if not _build.up_to_date():
         _build.build()
     stream = torch.cuda.Stream()
-    w = build_workload(g, g.NS_FP64, rank)
-    sp, th_inj = g.make_analysis(w, precision=g.NS_FP64, stream=stream.cuda_stream)
+    w = build_workload(WORKLOAD, rank)
+    inputs, th_inj = workload_data(g, w, stream)
+    sp = sampler_on(g, w, inputs, g.NS_MIXED, stream)
+    blob = sp.checkpoint()          # the initial live set: every timed step starts here
     l2_flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def flush():
         with torch.cuda.stream(stream):
             l2_flush.fill_(1.0)
 
-    for _ in range(args.warmup):
-        sp.step()
+    timed_first_iterations(sp, blob, stream, args.warmup, flush)
     torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    st0 = sp.stats()
-    evals0 = st0["evals"]
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(dev) as clk:
-        for i in range(args.steps):
-            flush()
-            ev[i][0].record(stream)
-            sp.step()
-            ev[i][1].record(stream)
+        step_ms, evals, pbins, kern = timed_first_iterations(sp, blob, stream, args.steps, flush)
         torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
-    st1 = sp.stats()
-    evals = st1["evals"] - evals0
     total_ms_max, evals_all = reduce_ranks(dist, total_ms, evals)
     value = evals_all / (total_ms_max / 1e3)
+    tile = sp.stats()["mixed_tile"]
+    roof = mixed_slice_roofline(kern, pbins, evals, args.steps, w.n_det, tile, sum(kern))
 
-    roof = slice_kernel_roofline(st0, st1, args.steps, w.n_det)
-    sp.close()
-
-    # time-to-logZ, FP64 and mixed, full runs from ns_init to ns_result
-    ttl = {}
-    if not args.core_only:
-        for name, prec in (("fp64", g.NS_FP64), ("mixed", g.NS_MIXED)):
-            ttl[name] = time_to_logz(g, w, prec, stream)
-
-    # end-to-end through the C ABI with host buffers: ns_init from host arrays,
-    # then K ns_step_host calls that copy each iteration's dead points to host
-    e2e = e2e_run(g, w, args.steps, stream)
-
-    # the serving workload (64 analyses arriving at 2/s): p50/p99 time-to-logZ
     extras = rank == 0 and not args.core_only
+    # the whole run to the stopping rule, from the same initial state
+    ttl = time_to_logz_from(sp, blob) if extras else None
+    sp.close()
+    # the FP64 form on the same first iteration (one step: ~9 s on this grid)
+    fp64 = fp64_first_iteration(g, w, inputs, stream, flush) if extras else None
+    # end to end through the C ABI with host buffers
+    e2e = e2e_run(g, w, inputs, args.steps, stream)
+
     serving = serving_stream(g) if extras else None
-    agreement = precision_agreement(g, w, stream) if extras else None
-    # the mixed-precision likelihood against its roofline: the batched
-    # likelihood on the 519,169-bin workload (8192 prior draws, three launches)
+    agreement = precision_agreement(g, build_workload("c1"), stream, name="c1") if extras else None
+    agreement_c4 = per_point_agreement(g, w, inputs, stream, points=1024) if extras else None
+    c1 = c1_fp64_extra(g, stream, args.steps, flush) if extras else None
+    # the mixed batched likelihood on the same grid (8192 prior draws, three launches)
     mixed_lik = mixed_likelihood_roofline(g, stream) if extras else None
 
     if rank == 0:
@@ -214,26 +291,132 @@ def run_gpu(args):
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (seeded noise, TaylorF2 injection at SNR 20, seeded detectors)",
-            "config": {"workload": "c1: 3 detectors, 11 parameters, 20-1024 Hz at df=0.25 (4017 bins), "
-                                   "n_live=1000, k=500, 55 slice steps per chain, FP64",
-                       "parallelism": f"replicas{ws}", "l2": "flushed before every timed step (256 MB write)"},
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic (seeded noise, TaylorF2 injection at SNR 30, seeded detectors)",
+            "config": config_dict(ws),
             "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
+            "evals_per_step": evals / args.steps, "point_bins_per_s": pbins / (total_ms / 1e3),
             "time_to_logZ": ttl,
-            "serving": serving,
-            "mixed_vs_fp64": agreement,
-            "mixed_likelihood": mixed_lik,
+            "fp64_same_iteration": fp64,
             "e2e": e2e,
             "gpu_launches": 5 * args.steps,   # the 5 library kernels of each ns_step (the L2 flush fill is torch's)
-            "kernel_ms_per_step": [(b - a) / args.steps for a, b in zip(st0["kernel_ms"], st1["kernel_ms"])],
+            "kernel_ms_per_step": [x / args.steps for x in kern],
             "roofline": roof,
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
+            "mixed_vs_fp64": {"c4_per_point": agreement_c4, "c1": agreement},
+            "c1_fp64": c1,
+            "mixed_likelihood": mixed_lik,
+            "serving": serving,
         }
         print(json.dumps(out))
     if dist:
         dist.destroy_process_group()
+
+
+def mixed_slice_roofline(kern, pbins, evals, steps, n_det, tile, step_kernel_ms):
+    """Roofline of the fused slice update (k_slice<MIXED>) over the timed
+    steps: its average launch duration from the CUDA events recorded around
+    it inside the iteration's graph (on the library's stream), and its
+    algorithmic instruction count = point-bins processed (device-side count of
+    jcut+1 per evaluation) x the binding pipe's instructions per point-bin."""
+    ms = kern[3] / steps
+    pb = pbins / steps
+    frac, pipe = mixed_roofline(pb, ms / 1e3, n_det, tile)
+    per_pb = mixed_fp32_per_point_bin(n_det, tile) if pipe == "FP32" else mixed_mufu_per_point_bin(n_det, tile)
+    peak = (FP32_LANE_OPS if pipe == "FP32" else SFU_LANE_OPS) / 1e12
+    traffic, traffic_pb = recorded_traffic()
+    if traffic is not None and traffic_pb:
+        traffic = traffic * pb / traffic_pb     # scaled to this launch's point-bins
+    return {"bound": "alu", "kernel": f"k_slice<MIXED,{n_det} det> (fused slice update + likelihood)",
+            "pipe": pipe, "achieved": pb * per_pb / (ms / 1e3) / 1e12, "peak": peak,
+            "unit": f"T {pipe} lane-instructions/s", "frac": frac,
+            "traffic": traffic,
+            "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch, scaled by "
+                            "point-bins; null when the kernel's sources changed since the capture",
+            "peak_source": "derived (not measured): 128 FP32 / 16 MUFU lanes/clk/SM x 152 SMs x 2070 MHz",
+            "per_launch": {"ms": ms, "evals": evals / steps, "point_bins": pb,
+                           "instr_per_point_bin": per_pb, "tile": tile,
+                           "share_of_step_kernels": kern[3] / step_kernel_ms if step_kernel_ms else None}}
+
+
+def time_to_logz_from(sp, blob):
+    """The whole run from the initial state to the stopping rule (first ns_step
+    to ns_result), with per-step latencies."""
+    import torch
+    sp.restore(blob)
+    torch.cuda.synchronize()
+    s0 = sp.stats()
+    t0 = time.perf_counter()
+    ms, done, it = [], False, 0
+    while not done and it < 100000:
+        t = time.perf_counter()
+        done = sp.step()
+        ms.append((time.perf_counter() - t) * 1e3)
+        it += 1
+    r = sp.result(samples=False)
+    t1 = time.perf_counter()
+    s1 = sp.stats()
+    ev = s1["evals"] - s0["evals"]
+    return {"seconds": t1 - t0, "iterations": it, "evals": ev, "evals_per_s": ev / (t1 - t0),
+            "logZ": r["logZ"], "dlogZ": r["dlogZ"], "p50_step_ms": float(np.percentile(ms, 50)),
+            "p99_step_ms": float(np.percentile(ms, 99)), "precision": "mixed",
+            "note": "ns_step to ns_result on the host clock, setup excluded"}
+
+
+def fp64_first_iteration(g, w, inputs, stream, flush):
+    """The FP64 form on the same grid: its first iteration timed with CUDA
+    events (one step; the FP64 pipe makes it ~40x slower than mixed here)."""
+    import torch
+    sp = sampler_on(g, w, inputs, g.NS_FP64, stream)
+    blob = sp.checkpoint()
+    ms, ev, pb, kern = timed_first_iterations(sp, blob, stream, 1, flush)
+    sp.close()
+    t = sum(ms) / 1e3
+    return {"evals_per_s": ev / t, "ms_per_step": sum(ms), "evals": ev, "point_bins_per_s": pb / t,
+            "k_slice_frac_fp64_pipe": pb * fp64_flops_per_point_bin(w.n_det) / (kern[3] / 1e3) / (FP64_PEAK_TFLOPS * 1e12),
+            "note": "first iteration, one step, CUDA events; FP64 peak derived (2 FMA/clk/SM)"}
+
+
+def per_point_agreement(g, w, inputs, stream, points=1024):
+    """Mixed against FP64 log L on prior draws of a workload's grid."""
+    a = sampler_on(g, w, inputs, g.NS_FP64, stream, n_live=8, k=4)
+    b = sampler_on(g, w, inputs, g.NS_MIXED, stream, n_live=8, k=4)
+    u = gi.unit_cube(777, points, w.dim)
+    l64, lmx = a.eval_lnl(u), b.eval_lnl(u)
+    a.close()
+    b.close()
+    d = np.abs(lmx - l64)
+    return {"workload": w.name, "points": points, "max_abs_dlogL": float(d.max()),
+            "rms_dlogL": float(np.sqrt(np.mean(d * d))), "max_abs_logL": float(np.max(np.abs(l64)))}
+
+
+def c1_fp64_extra(g, stream, steps, flush):
+    """The 4017-bin FP64 workload (the previous headline): K iterations after
+    three warm-up iterations of one run, CUDA events, L2 flushed."""
+    import torch
+    w = build_workload("c1")
+    sp, th = g.make_analysis(w, precision=g.NS_FP64, stream=stream.cuda_stream)
+    for _ in range(3):
+        sp.step()
+    s0 = sp.stats()
+    ms = []
+    for _ in range(steps):
+        flush()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sp.step()
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    s1 = sp.stats()
+    sp.close()
+    ttl = {}
+    for name, prec in (("fp64", g.NS_FP64), ("mixed", g.NS_MIXED)):
+        ttl[name] = time_to_logz(g, w, prec, stream)
+    return {"workload": "c1: 3 detectors, 4017 bins, n_live=1000, k=500, FP64",
+            "evals_per_s": (s1["evals"] - s0["evals"]) / (sum(ms) / 1e3), "ms_per_step": sum(ms) / steps,
+            "time_to_logZ": ttl}
 
 
 def mixed_likelihood_roofline(g, stream):
@@ -249,30 +432,6 @@ def mixed_likelihood_roofline(g, stream):
             "instr_per_point_bin": (mixed_fp32_per_point_bin(3, r["mixed_tile"]) if r["pipe"] == "FP32"
                                     else mixed_mufu_per_point_bin(3, r["mixed_tile"])),
             "peak_source": "derived (not measured): 128 FP32 / 16 MUFU lanes/clk/SM x 152 SMs x 2070 MHz"}
-
-
-def slice_kernel_roofline(st0, st1, steps, n_det):
-    """Roofline of the fused slice-update kernel over the timed region: its
-    average launch duration from the CUDA events recorded around it inside the
-    iteration's graph (on the library's stream), and its algorithmic FP64 work
-    = point-bins processed (device-side count of jcut+1 per evaluation) x the
-    FMA-equivalents of one point-bin."""
-    ms = (st1["kernel_ms"][3] - st0["kernel_ms"][3]) / steps
-    pb = (st1["point_bins"] - st0["point_bins"]) / steps
-    ev = (st1["evals"] - st0["evals"]) / steps
-    flops = pb * fp64_flops_per_point_bin(n_det)
-    achieved = flops / (ms / 1e3) / 1e12 if ms > 0 else None
-    share = ms / (sum(st1["kernel_ms"]) - sum(st0["kernel_ms"])) * steps if ms > 0 else None
-    return {"bound": "alu", "kernel": "k_slice<FP64,3 det> (fused slice update + likelihood)",
-            "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS if achieved else None,
-            # dram__bytes_read.sum + dram__bytes_write.sum of one k_slice<FP64> launch on this
-            # workload (profiles/k_slice_fp64_c1_ncu_full.md); null once the kernel changes
-            "traffic": K_SLICE_FP64_C1_DRAM_BYTES,
-            "peak_source": "derived (not measured): 2 FP64 FMA/clk/SM x 152 SMs x 2070 MHz",
-            "per_launch": {"ms": ms, "evals": ev, "point_bins": pb,
-                           "flops_per_point_bin": fp64_flops_per_point_bin(n_det),
-                           "share_of_step_kernels": share}}
 
 
 def time_to_logz(g, w, precision, stream):
@@ -320,31 +479,44 @@ def precision_agreement(g, w, stream, seeds: int = 16, points: int = 4096, name:
             "max_abs_dlogZ_single_seed": float(np.abs(dz).max()), "sd_logZ_fp64_over_seeds": float(np.std(z64, ddof=1))}
 
 
-def e2e_run(g, w, steps, stream):
+def e2e_run(g, w, inputs, steps, stream):
+    """The headline metric end to end through the C ABI with host buffers:
+    ns_init from host arrays (strain and PSD uploaded, tables built, the
+    initial live set drawn and evaluated), then per step ns_restore from a
+    pinned host checkpoint of the initial state (its live set and run state
+    copied host -> device) and ns_step_host (the step's dead points copied
+    device -> host into pinned buffers); evaluations of the steps over the
+    wall time of all of it."""
+    import ctypes
     import torch
-    probe, th = g.make_analysis(w, precision=g.NS_FP64, stream=stream.cuda_stream)
-    # host inputs of the analysis (pinned copies not needed: the ABI copies them)
-    f = w.freqs()
-    psd = np.tile(gi.psd_analytic(f), (w.n_det, 1))
-    data = probe.waveform(th) + gi.noise(w.seed_noise, psd, w.df)
+    probe = sampler_on(g, w, inputs, g.NS_MIXED, stream)
+    blob = probe.checkpoint()
     probe.close()
-    pos, xarm, yarm = gi.detectors(w.seed_geometry, w.n_det)
+    hblob = torch.frombuffer(bytearray(blob), dtype=torch.uint8).pin_memory()
     k, d = w.k, w.dim
-    du, dl, dw = np.zeros((k, d)), np.zeros(k), np.zeros(k)
+    du = torch.empty((k, d), dtype=torch.float64).pin_memory()
+    dl = torch.empty(k, dtype=torch.float64).pin_memory()
+    dw = torch.empty(k, dtype=torch.float64).pin_memory()
+    done = ctypes.c_int(0)
+    L = g.lib()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    sp = g.Sampler(kind=w.kind, lo=w.lo, hi=w.hi, data=data, psd=psd, f0=w.f0, df=w.df, pos=pos,
-                   xarm=xarm, yarm=yarm, n_live=w.n_live, k=k, steps_per_dim=w.steps_per_dim,
-                   precision=g.NS_FP64, seed=w.seed_sampler, stream=stream.cuda_stream)
+    sp = sampler_on(g, w, inputs, g.NS_MIXED, stream)
+    ev = 0
     for _ in range(steps):
-        sp.step_host(k, du, dl, dw)
+        g._check(L.ns_restore(sp._ctx, hblob.data_ptr(), hblob.numel()), "ns_restore")
+        e0 = sp.stats()["evals"]
+        g._check(L.ns_step_host(sp._ctx, k, ctypes.byref(done), du.data_ptr(), dl.data_ptr(), dw.data_ptr()),
+                 "ns_step_host")
+        ev += sp.stats()["evals"] - e0
     t1 = time.perf_counter()
-    ev = sp.stats()["evals"]
     sp.close()
-    h2d = (2 * data.size + psd.size) * 8
-    return {"value": ev / (t1 - t0), "unit": UNIT, "h2d_bytes_per_step": h2d / steps,
+    init_h2d = (2 * inputs["data"].size + inputs["psd"].size) * 8
+    return {"value": ev / (t1 - t0), "unit": UNIT,
+            "h2d_bytes_per_step": hblob.numel() + init_h2d / steps,
             "d2h_bytes_per_step": k * (d + 2) * 8,
-            "note": "ns_init from host arrays (data, PSD upload amortised over the steps) + ns_step_host"}
+            "note": "ns_init from host arrays (strain and PSD upload amortised over the steps) + per step "
+                    "ns_restore of the pinned initial checkpoint and ns_step_host into pinned buffers"}
 
 
 def serving_stream(g, count=64, time_limit_s=240.0, max_chains=0):
@@ -404,79 +576,92 @@ def serving_stream(g, count=64, time_limit_s=240.0, max_chains=0):
                         "mixed precision; up to 16 analyses interleaved"}
 
 
-def oracle_sample(chains: int, iteration: int = 0):
-    """One bounded sample of the workload on the oracle: from the initial live
-    set, the first iteration's selection and covariance, then `chains` of its
-    500 slice-sampling chains (iteration index `iteration` keys the draws)."""
-    import oracle
-    from oracle import ns as ons
-    w = gi.workload(WORKLOAD)
-    if not hasattr(oracle_sample, "cache"):
+def oracle_first_iteration():
+    """The oracle's own first iteration of the workload: its data (oracle
+    waveform, the same seeded noise), the initial live set of the same Philox
+    draws evaluated by its per-bin likelihood, the selection and the
+    survivors' Cholesky factor (setup of the CPU samples; not timed)."""
+    if not hasattr(oracle_first_iteration, "cache"):
+        import oracle
+        from oracle import ns as ons
+        w = build_workload(WORKLOAD)
         pb, th = oracle.make_problem(w)
         st0 = ons.initial_state(pb, w.n_live, w.seed_sampler)
-        oracle_sample.cache = (pb, st0)
-    pb, st0 = oracle_sample.cache
-    d = pb.dim
-    order = np.argsort(st0.live_logl, kind="stable")
-    k = w.k
-    surv = np.ascontiguousarray(st0.live_u[order[k:]])
-    surv_l = np.ascontiguousarray(st0.live_logl[order[k:]])
-    chol = np.ascontiguousarray(ons.survivor_cholesky(surv))
-    lstar = float(st0.live_logl[order[k - 1]])
-    new_u = np.zeros((chains, d))
-    new_l = np.zeros(chains)
+        order = np.argsort(st0.live_logl, kind="stable")
+        k = w.k
+        surv = np.ascontiguousarray(st0.live_u[order[k:]])
+        surv_l = np.ascontiguousarray(st0.live_logl[order[k:]])
+        chol = np.ascontiguousarray(ons.survivor_cholesky(surv))
+        lstar = float(st0.live_logl[order[k - 1]])
+        oracle_first_iteration.cache = (w, pb, surv, surv_l, chol, lstar)
+    return oracle_first_iteration.cache
+
+
+def oracle_chains(first: int):
+    """One bounded sample on the oracle: chains first .. first + REF_CHAINS - 1
+    (mod k) of the first iteration, each for its first REF_STEPS slice steps --
+    the same draws and evaluations the GPU makes at the start of those chains
+    in every timed step. Returns (evaluations, seconds, threads)."""
+    import oracle
+    w, pb, surv, surv_l, chol, lstar = oracle_first_iteration()
+    k, d = w.k, pb.dim
+    first %= k
+    count = min(REF_CHAINS, k - first)
+    new_u = np.zeros((k, d))
+    new_l = np.zeros(k)
     caps = np.zeros(1, dtype=np.int32)
     nt = oracle.max_threads()
     t0 = time.perf_counter()
-    ev = oracle.lib().or_evolve(pb.c, nt, w.seed_sampler, iteration, chains, oracle._ptr(surv),
-                                oracle._ptr(surv_l), w.n_live - k, oracle._ptr(chol), lstar,
-                                w.steps_per_dim * d, 64, 64, oracle._ptr(new_u), oracle._ptr(new_l),
-                                oracle._ptr(caps))
+    ev = oracle.lib().or_evolve_chains(pb.c, nt, w.seed_sampler, 0, first, count, oracle._ptr(surv),
+                                       oracle._ptr(surv_l), w.n_live - k, oracle._ptr(chol), lstar,
+                                       REF_STEPS, 64, 64, oracle._ptr(new_u), oracle._ptr(new_l),
+                                       oracle._ptr(caps))
     return ev, time.perf_counter() - t0, nt
 
 
-def cpu_baseline(target_s: float = 10.0):
-    """The oracle's chain work of whole iterations (500 chains each) until
-    about target_s seconds of wall time on all host cores."""
+def ref_sample_text() -> str:
+    return (f"per sample: {REF_CHAINS} chains of the first iteration of c4 (a different block of chains each "
+            f"time), their first {REF_STEPS} of 55 slice steps (the evaluations the GPU makes first in those "
+            f"chains); plain FP64 C with per-bin libm transcendentals, OpenMP over chains")
+
+
+def cpu_baseline(target_s: float = 12.0):
+    """The oracle's chain work of the timed iteration, in bounded samples,
+    until about target_s seconds of wall time on all host cores."""
     tot_ev, tot_s, reps, nt = 0, 0.0, 0, 1
     while tot_s < target_s and reps < 200:
-        ev, sec, nt = oracle_sample(500, iteration=reps)
+        ev, sec, nt = oracle_chains(REF_CHAINS * reps)
         tot_ev += ev
         tot_s += sec
         reps += 1
     return {"value": tot_ev / tot_s, "unit": UNIT, "cores": nt, "kind": "oracle",
-            "sample": f"{reps} x the 500 slice-sampling chains of the first iteration of c1 "
-                      f"({tot_ev} evaluations, {tot_s:.1f} s), plain FP64 C, OpenMP over chains"}
+            "sample": f"{reps} samples ({tot_ev} evaluations, {tot_s:.1f} s); " + ref_sample_text()}
 
 
 def run_reference(args):
-    """The oracle as the reference arm: each step evolves the 500 chains of one
-    iteration (from the initial live set, draws keyed by the step index)."""
+    """The oracle as the reference arm: each step is one bounded sample of the
+    timed iteration's chains (a different block of chains per step)."""
     ws, rank = world()
     if rank != 0:
         return
+    oracle_first_iteration()
     for i in range(args.warmup):
-        oracle_sample(500, iteration=1000 + i)
+        oracle_chains(REF_CHAINS * (args.steps + i))
     tot_ev, tot_s, nt = 0, 0.0, 1
     for i in range(args.steps):
-        ev, sec, nt = oracle_sample(500, iteration=i)
+        ev, sec, nt = oracle_chains(REF_CHAINS * i)
         tot_ev += ev
         tot_s += sec
     value = tot_ev / tot_s
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_s * 1e3 / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": {"workload": "c1: 3 detectors, 11 parameters, 20-1024 Hz at "
-                                                      "df=0.25 (4017 bins), n_live=1000, k=500, 55 slice "
-                                                      "steps per chain, FP64"},
+           "data": "synthetic (seeded noise, TaylorF2 injection at SNR 30, seeded detectors)",
+           "config": config_dict(ws),
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": nt, "kind": "oracle",
-                            "sample": "per step: the 500 chains of one iteration from the initial live set"},
+                            "sample": ref_sample_text()},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
-
-
-FP32_LANE_OPS = 152 * 128 * 2.070e9    # FP32 pipe: 128 lanes/clk/SM x 152 SMs x 2070 MHz
-SFU_LANE_OPS = 152 * 16 * 2.070e9      # MUFU (sin, cos): 16 lanes/clk/SM x 152 SMs x 2070 MHz
 
 
 def mixed_fp32_per_point_bin(n_det: int, tile: int) -> float:

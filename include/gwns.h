@@ -39,7 +39,8 @@ enum {
     NS_ERR_K_RANGE = -3,       /* k outside 1 .. n_live-1 */
     NS_ERR_OOM = -4,           /* a device allocation failed */
     NS_ERR_CAPACITY = -5,      /* the caller's output buffer is too small */
-    NS_ERR_TIMEOUT = -6,       /* a bounded device-side wait gave up */
+    NS_ERR_TIMEOUT = -6,       /* reserved: no call returns it (the kernels have no device-side
+                                  waits that could time out) */
     NS_ERR_CANCELLED = -7,     /* the request was cancelled */
     NS_ERR_CUDA = -8,          /* a CUDA runtime call failed */
     NS_ERR_STATE = -9          /* call not valid in the context's state */
@@ -231,6 +232,9 @@ typedef struct {
     long long batch_evals;       /* points through the batched likelihood (ns_eval_lnl*, ns_init's
                                     initial live set) */
     long long batch_point_bins;  /* their sum of the bins each one read */
+    long long scratch_bytes;     /* device bytes of the context's staging scratch, allocated by the
+                                    host-buffer entry points (ns_eval_lnl_host, ns_waveform,
+                                    ns_result with theta) on first use and when a call needs more */
 } ns_stats;
 
 int ns_get_stats(ns_ctx *ctx, ns_stats *st);
@@ -243,19 +247,21 @@ int ns_eval_lnl(ns_ctx *ctx, const double *u, int m, double *logl);
 int ns_eval_lnl_host(ns_ctx *ctx, const double *u, int m, double *logl);
 
 /* Allocation-free variant of ns_eval_lnl_host, for callers that cannot call
- * cudaMalloc at this point: code running inside stream capture, real-time or
- * callback contexts, and hosts whose device memory is reserved by another
- * allocator. (The paper has no counterpart; this is an integration feature.)
- * ns_eval_lnl_host stages u and log L in device scratch that it allocates on
- * first use or when m grows; this entry point stages them instead in one
- * file-scope device array of NS_NOALLOC_MAX_POINTS x (NS_MAX_DIM + 1) doubles
- * (557,056 bytes) that every GPU loading the library holds until exit, and it
- * calls no cudaMalloc/cudaFree. Host pointers: u [m][d] in, logl [m] out;
- * synchronises the context's stream before returning.
+ * cudaMalloc at this point: real-time or callback code that must not block in
+ * the allocator, and hosts whose device memory is reserved by another
+ * allocator (a memory pool that owns the free memory). (The paper has no
+ * counterpart; this is an integration feature.) ns_eval_lnl_host stages u and
+ * log L in device scratch that it allocates on first use or when m grows;
+ * this entry point stages them instead in one file-scope device array of
+ * NS_NOALLOC_MAX_POINTS x (NS_MAX_DIM + 1) doubles (557,056 bytes) that every
+ * GPU loading the library holds until exit, and it calls no
+ * cudaMalloc/cudaFree. Host pointers: u [m][d] in, logl [m] out; the values
+ * are in logl when it returns, because it synchronises the context's stream.
  *   - m > NS_NOALLOC_MAX_POINTS returns NS_ERR_CAPACITY (split the batch);
  *   - the first call on a device looks up the array's device address once
- *     (cudaGetSymbolAddress), so make that first call before any stream
- *     capture;
+ *     (cudaGetSymbolAddress) and keeps it for the process, so make that first
+ *     call before any stream capture, and do not call it again on a device
+ *     after cudaDeviceReset (the kept address would be stale);
  *   - all calls share the array and it keeps the last call's contents (each
  *     call overwrites the m entries it uses; nothing needs to start at zero);
  *     calls that overlap on the GPU (other threads, other contexts on other

@@ -101,6 +101,10 @@ def lib():
                                     dp, dp, ctypes.c_int, dp, ctypes.c_double, ctypes.c_int,
                                     ctypes.c_int, ctypes.c_int, dp, dp, dp]
             L.or_evolve.restype = ctypes.c_longlong
+            L.or_evolve_chains.argtypes = [P, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int,
+                                           ctypes.c_int, dp, dp, ctypes.c_int, dp, ctypes.c_double,
+                                           ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, dp]
+            L.or_evolve_chains.restype = ctypes.c_longlong
             L.or_evolve_walk.argtypes = [P, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int,
                                          dp, dp, ctypes.c_int, dp, ctypes.c_double, ctypes.c_int,
                                          ctypes.c_double, dp, dp, dp]

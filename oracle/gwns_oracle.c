@@ -588,13 +588,17 @@ int or_walk_next(int walk, int target, int k, long long accepted)
     return (int)t;
 }
 
-/* Evolve the k chains of one iteration (chains are independent; OpenMP over
- * chains does not change any result). Returns the total number of likelihood
- * evaluations; caps receives the number of steps that hit the shrink cap. */
-long long or_evolve(const or_problem *pb, int nthreads, uint64_t seed, uint32_t iter, int k,
-                    const double *surv_u, const double *surv_logl, int m, const double *chol,
-                    double lstar, int steps, int max_stepout, int max_shrink,
-                    double *out_u, double *out_logl, int *caps)
+/* Evolve chains first .. first + count - 1 of one iteration (chains are
+ * independent: a chain's draws are keyed by its own index, so a subset of the
+ * chains follows exactly the trajectories those chains have in the whole
+ * iteration; OpenMP over chains does not change any result). out_u and
+ * out_logl are indexed by the chain (first + count entries). Returns the total
+ * number of likelihood evaluations; caps receives the number of steps that hit
+ * the shrink cap. */
+long long or_evolve_chains(const or_problem *pb, int nthreads, uint64_t seed, uint32_t iter, int first,
+                           int count, const double *surv_u, const double *surv_logl, int m,
+                           const double *chol, double lstar, int steps, int max_stepout,
+                           int max_shrink, double *out_u, double *out_logl, int *caps)
 {
     int d = or_dim(pb);
     long long total = 0;
@@ -602,7 +606,7 @@ long long or_evolve(const or_problem *pb, int nthreads, uint64_t seed, uint32_t 
 #ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 1) reduction(+ : total, capsum) num_threads(nthreads > 0 ? nthreads : 1)
 #endif
-    for (int c = 0; c < k; c++) {
+    for (int c = first; c < first + count; c++) {
         long long ev = 0;
         int cp = 0;
         evolve_chain(pb, seed, iter, c, d, surv_u, surv_logl, m, chol, lstar, steps,
@@ -612,6 +616,16 @@ long long or_evolve(const or_problem *pb, int nthreads, uint64_t seed, uint32_t 
     }
     *caps = capsum;
     return total;
+}
+
+/* All k chains of one iteration (or_evolve_chains over 0 .. k-1). */
+long long or_evolve(const or_problem *pb, int nthreads, uint64_t seed, uint32_t iter, int k,
+                    const double *surv_u, const double *surv_logl, int m, const double *chol,
+                    double lstar, int steps, int max_stepout, int max_shrink,
+                    double *out_u, double *out_logl, int *caps)
+{
+    return or_evolve_chains(pb, nthreads, seed, iter, 0, k, surv_u, surv_logl, m, chol, lstar, steps,
+                            max_stepout, max_shrink, out_u, out_logl, caps);
 }
 
 /* ------------------------------------------------------ relative binning */

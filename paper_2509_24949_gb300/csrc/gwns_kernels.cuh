@@ -46,7 +46,8 @@ struct StepArgs {
     int *active;          // chains of the current slice update still running
     int depth;            // candidates planned per round while many chains run
     int tail;             // below this many running chains, plan as many as there are warps
-    int tail_coop;        // FP64, below this many: base depth, spare warps share the candidates' bins
+    int fp64_split;       // FP64: warps per candidate's bins in every round (1, or 2 on fine grids:
+                          // always the same split, so results do not depend on timing)
     int kernel;           // 0 slice sampling, 1 random walk
     double walk_scale;    // random walk: y = x + walk_scale L z
 };

@@ -521,17 +521,17 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
             if (A.kernel == 1) walk_run(M, A, c, chain, iter, lstar, walk_len);
             else chain_run(M, A, c, chain, iter, lstar, e_next, e_next_step);
             // plan the base depth while many chains run; the stragglers of the
-            // update (fewer running chains than the tail threshold) use every warp
-            // FP64 among the very last chains keeps the base depth and gives the
-            // spare warps to the candidates' bins instead (FP64 branch below)
+            // update (fewer running chains than the tail threshold) use every warp.
+            // FP64 on fine grids splits every candidate's bins over two warps in
+            // every round instead (FP64 branch below), with at most W/2 candidates.
             int depth = S, tail = 1;
             if (A.active) {
                 const int running = *((volatile int *)A.active);
                 if (running > A.tail) { depth = A.depth; tail = 0; }
-                else if (PREC == 0 && M.model == M_GW && !M.rb && running <= A.tail_coop) {
-                    depth = A.depth;
-                    tail = 2;
-                }
+            }
+            if (PREC == 0 && A.fp64_split == 2 && W >= 2) {
+                depth = A.depth < W / 2 ? A.depth : W / 2;
+                tail = 2;
             }
             int ns = (c.phase == PH_DONE) ? 0
                    : A.kernel == 1 ? walk_plan<S>(M, A, c, chain, iter, ysh, pk, pidx, depth, walk_len)
@@ -651,15 +651,12 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
                     if (lane == 0) lval[sc2] = t - 0.5 * coef[sc2].hh;
                 }
             }
-        } else if (PREC == 0 && S > 1 && M.model == M_GW && !M.rb && tailmode == 2) {
-            // FP64 among the update's last chains: each candidate's bins are
-            // spread over wpc = S / ns warps (rounded down to a power of two;
-            // warps on different SM sub-partitions issue FP64 independently),
-            // partial sums meet in shared memory. While many chains run, the
-            // duplicated per-warp start values would cost more FP64 issue than
-            // the shorter loop saves.
-            int lg = 0;
-            while ((ns << (lg + 1)) <= W) lg++;
+        } else if (PREC == 0 && W > 1 && M.model == M_GW && !M.rb && tailmode == 2) {
+            // FP64 on fine grids: each candidate's bins on two warps (warps on
+            // different SM sub-partitions issue FP64 independently), bin j on
+            // lane j mod 32 of warp (j / 32) mod 2; the two warp sums meet in
+            // shared memory in a fixed order, whatever the round.
+            const int lg = 1;
             const int wpc = 1 << lg, cand = warp >> lg, sub = warp & (wpc - 1);
             if (cand < ns) {
                 double zr[NDET], zi[NDET];

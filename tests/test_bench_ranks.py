@@ -64,3 +64,24 @@ def test_mixed_roofline_takes_the_binding_pipe():
     # one detector in the direct form: 23 FP32 against 2 MUFU -> FP32 binds (23/128 > 2/16)
     frac, pipe = bench.mixed_roofline(pb, secs, 1, 16)
     assert pipe == "FP32"
+
+
+def test_recorded_traffic_is_dropped_when_the_kernel_changes(tmp_path, monkeypatch):
+    """The roofline's DRAM traffic comes from a committed ncu summary only while
+    the hash of the kernel's sources it records matches the current sources."""
+    import bench
+    f = tmp_path / "traffic.md"
+    sha = bench.kernel_source_sha16()
+    f.write_text(f"source_sha16: {sha}\ndram_bytes_per_launch: 123456\npoint_bins_per_launch: 1000\n")
+    monkeypatch.setattr(bench, "TRAFFIC_SUMMARY", str(f))
+    assert bench.recorded_traffic() == (123456, 1000)
+    f.write_text("source_sha16: 0123456789abcdef\ndram_bytes_per_launch: 123456\n")
+    assert bench.recorded_traffic() == (None, None)
+    monkeypatch.setattr(bench, "TRAFFIC_SUMMARY", str(tmp_path / "missing.md"))
+    assert bench.recorded_traffic() == (None, None)
+
+
+def test_both_arms_describe_the_same_configuration():
+    import bench
+    assert bench.config_dict(1) == bench.config_dict(1)
+    assert bench.config_dict(2)["parallelism"] == "replicas2"

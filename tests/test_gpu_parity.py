@@ -258,6 +258,63 @@ def test_bench_configuration_iteration_matches_oracle(gw):
     assert s["evals"] == st.evals and s["status"] == 0
 
 
+@pytest.mark.parametrize("slots", [0, 2])
+@pytest.mark.parametrize("name,n_live,k,spd", [("c2", 400, 200, 2), ("c4", 20, 10, 1)])
+def test_fp64_iteration_on_the_large_grids_matches_oracle(gw, name, n_live, k, spd, slots):
+    """FP64 slice update on the 64,897- and 519,169-bin grids (3 detectors,
+    11 parameters) with the default slot rule (one slot there) and with two:
+    after one iteration the live set, threshold, evidence and evaluation count
+    equal the oracle's. On the 64,897-bin grid 200 chains run, more than there
+    are SMs, so chains run both while the GPU is full and in the update's tail."""
+    w, pb, th = problem(name)
+    st = ons.initial_state(pb, n_live, w.seed_sampler)
+    with sampler_from(gw, pb, 0, n_live=n_live, k=k, steps_per_dim=spd, seed=w.seed_sampler,
+                      slots=slots) as sp:
+        u0, l0 = sp.live()
+        assert np.max(np.abs(u0 - st.live_u)) == 0.0
+        assert np.max(np.abs(l0 - st.live_logl) / np.maximum(1, np.abs(st.live_logl))) < FP64_RTOL
+        info = ons.iterate(pb, st, k, spd * pb.dim, w.seed_sampler)
+        sp.step(k)
+        gu, gl = sp.live()
+        s = sp.stats()
+    assert s["lstar"] == pytest.approx(info["lstar"], rel=1e-9, abs=1e-9)
+    assert np.max(np.abs(gu - st.live_u)) < 1e-9
+    assert np.max(np.abs(gl - st.live_logl) / np.maximum(1, np.abs(st.live_logl))) < 1e-8
+    assert s["logZ"] == pytest.approx(st.logZ, rel=1e-9, abs=1e-9)
+    assert s["evals"] == st.evals and s["status"] == 0
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_runs_at_the_benchmark_population_are_bit_identical(gw, precision):
+    """Two fresh runs of the 4017-bin workload at 1000 live points and 500
+    chains per iteration (more chains than SMs, so chains finish in a
+    timing-dependent order) give bit-identical live sets and log Z, and so does
+    a run resumed from a checkpoint taken halfway."""
+    w, pb, th = problem("c1")
+    args = dict(n_live=w.n_live, k=w.k, steps_per_dim=w.steps_per_dim, seed=w.seed_sampler)
+    runs = []
+    for r in range(2):
+        with sampler_from(gw, pb, precision, **args) as sp:
+            for _ in range(3):
+                sp.step()
+            blob = sp.checkpoint() if r == 0 else None
+            for _ in range(3):
+                sp.step()
+            runs.append((sp.live(), sp.stats(), blob))
+    (ua, la), sa, blob = runs[0]
+    (ub, lb), sb, _ = runs[1]
+    assert np.array_equal(ua, ub) and np.array_equal(la, lb)
+    assert sa["logZ"] == sb["logZ"] and sa["evals"] == sb["evals"]
+    with sampler_from(gw, pb, precision, **args) as sp:
+        sp.restore(blob)
+        for _ in range(3):
+            sp.step()
+        uc, lc = sp.live()
+        sc = sp.stats()
+    assert np.array_equal(ua, uc) and np.array_equal(la, lc)
+    assert sa["logZ"] == sc["logZ"] and sa["evals"] == sc["evals"]
+
+
 def test_ns_step_host_dead_points(gw):
     w, pb, sp, st = _ns_pair(gw, "c0", 100, 50)
     k, d = 50, pb.dim

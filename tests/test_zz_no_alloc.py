@@ -1,10 +1,10 @@
 """The allocation-free host-buffer likelihood entry point.
 
-Some callers cannot call cudaMalloc when they evaluate the likelihood: code
-inside CUDA stream capture, real-time or callback contexts, or hosts whose
-device memory belongs to another allocator. ns_eval_lnl_host_noalloc serves
-them from a fixed device array instead of allocated scratch. This file is
-collected last so that a run stopping at the first failure has already run
+Some callers cannot call cudaMalloc when they evaluate the likelihood:
+real-time or callback code that must not block in the allocator, or hosts
+whose device memory belongs to another allocator. ns_eval_lnl_host_noalloc
+serves them from a fixed device array instead of allocated scratch. This file
+is collected last so that a run stopping at the first failure has already run
 every other test."""
 import ctypes
 
@@ -31,6 +31,21 @@ def _noalloc(gw, sp, u):
     out = np.zeros(u.shape[0])
     rc = gw.lib().ns_eval_lnl_host_noalloc(sp._ctx, u.ctypes.data, u.shape[0], out.ctypes.data)
     return rc, out
+
+
+def test_noalloc_allocates_no_scratch(gw):
+    """On a fresh context the entry point leaves the context's staging scratch
+    unallocated, over two calls; the allocating host entry point then does
+    allocate it."""
+    sp, pb = _sampler(gw)
+    assert sp.stats()["scratch_bytes"] == 0
+    for seed, m in [(11, 900), (12, 4096)]:
+        rc, got = _noalloc(gw, sp, gi.unit_cube(seed, m, pb.dim))
+        assert rc == 0 and np.all(np.isfinite(got))
+        assert sp.stats()["scratch_bytes"] == 0
+    sp.eval_lnl(gi.unit_cube(13, 50, pb.dim))
+    assert sp.stats()["scratch_bytes"] > 0
+    sp.close()
 
 
 def test_noalloc_matches_host_entry_on_consecutive_calls(gw):
