@@ -450,33 +450,59 @@ def time_to_logz(g, w, precision, stream):
             "evals_per_s": s["evals"] / (t2 - t1), "logZ": r["logZ"], "dlogZ": r["dlogZ"]}
 
 
+def analysis_inputs(g, w, stream):
+    """Host inputs of a workload and its (possibly narrowed) prior: the
+    single-detector workload fixes its distance from the target SNR."""
+    if w.dl_from_snr or w.ideal:
+        probe, th = g.make_analysis(w, precision=g.NS_FP64, n_live=2, k=1, stream=stream.cuda_stream)
+        data = probe.waveform(th)
+        probe.close()
+        w2 = gi.workload(w.name)
+        w2.seed_sampler = w.seed_sampler
+        w2.lo, w2.hi = w.lo.copy(), w.hi.copy()
+        w2.lo[gi.P_DL] = w2.hi[gi.P_DL] = th[gi.P_DL]
+        psd = np.tile(gi.psd_analytic(w.freqs()), (w.n_det, 1))
+        return w2, dict(data=data, psd=psd, ideal=True), th
+    inputs, th = workload_data(g, w, stream)
+    return w, inputs, th
+
+
 def precision_agreement(g, w, stream, seeds: int = 16, points: int = 4096, name: str = WORKLOAD):
     """Mixed against FP64 on the GPU: per-point log L difference on prior
-    draws, and log Z over `seeds` sampler seeds (same data), reported as the
-    mean difference with its standard error."""
-    sp64, th = g.make_analysis(w, precision=g.NS_FP64, stream=stream.cuda_stream)
-    spmx, _ = g.make_analysis(w, precision=g.NS_MIXED, stream=stream.cuda_stream)
-    u = gi.unit_cube(777, points, w.dim)
-    d = np.abs(spmx.eval_lnl(u) - sp64.eval_lnl(u))
-    sp64.close()
-    spmx.close()
-    dz, z64 = [], []
+    draws, and log Z over `seeds` sampler seeds on the same data (seed pair i:
+    both forms with sampler seed + 1000 (i + 1)), reported as the mean
+    difference with its standard error."""
+    w = gi.workload(name)
+    w, inputs, th = analysis_inputs(g, w, stream)
+    agree = per_point_agreement(g, w, inputs, stream, points=points)
+    if seeds < 2:
+        return {"workload": name, "points": points, **{k: agree[k] for k in
+                                                       ("max_abs_dlogL", "rms_dlogL", "max_abs_logL")}}
+    dz, z64, zmx, dl64 = [], [], [], []
+    base = w.seed_sampler
     for i in range(seeds):
         zs = []
         for prec in (g.NS_FP64, g.NS_MIXED):
-            w2 = gi.workload(name)
-            w2.seed_sampler += 1000 * (i + 1)
-            sp, _ = g.make_analysis(w2, precision=prec, stream=stream.cuda_stream)
+            sp = sampler_on(g, w, inputs, prec, stream, seed=base + 1000 * (i + 1))
             sp.run()
-            zs.append(sp.result(samples=False)["logZ"])
+            r = sp.result(samples=False)
+            zs.append(r["logZ"])
+            if prec == g.NS_FP64:
+                dl64.append(r["dlogZ"])
             sp.close()
         dz.append(zs[1] - zs[0])
         z64.append(zs[0])
+        zmx.append(zs[1])
     dz = np.array(dz)
-    return {"workload": name, "points": points, "max_abs_dlogL": float(d.max()),
-            "rms_dlogL": float(np.sqrt(np.mean(d * d))),
+    return {"workload": name, "points": points, "max_abs_dlogL": agree["max_abs_dlogL"],
+            "rms_dlogL": agree["rms_dlogL"], "max_abs_logL": agree["max_abs_logL"],
             "seeds": seeds, "mean_dlogZ": float(dz.mean()), "stderr_dlogZ": float(dz.std(ddof=1) / np.sqrt(seeds)),
-            "max_abs_dlogZ_single_seed": float(np.abs(dz).max()), "sd_logZ_fp64_over_seeds": float(np.std(z64, ddof=1))}
+            "sd_dlogZ_pairs": float(dz.std(ddof=1)),
+            "max_abs_dlogZ_single_seed": float(np.abs(dz).max()),
+            "mean_logZ_fp64": float(np.mean(z64)), "mean_logZ_mixed": float(np.mean(zmx)),
+            "sd_logZ_fp64_over_seeds": float(np.std(z64, ddof=1)),
+            "sd_logZ_mixed_over_seeds": float(np.std(zmx, ddof=1)),
+            "mean_dlogZ_reported_fp64": float(np.mean(dl64))}
 
 
 def e2e_run(g, w, inputs, steps, stream):
@@ -935,6 +961,60 @@ def run_calibration(args):
               flush=True)
 
 
+def run_population_calibration(args):
+    """Evidence calibration over a population of injections (paper Sec. 4
+    leaves the validation of its evidence estimates open): --injections
+    synthetic 4017-bin analyses (3 detectors, 11 parameters; each its own
+    injection drawn from the prior and scaled to SNR 20, and its own noise),
+    each run with --seeds sampler seeds at 5, 10 and 20 slice steps per
+    dimension. Per injection the runs' mean log Z stands in for the unknown
+    true value; z = (log Z - mean) / (dlogZ sqrt(1 - 1/R)) is N(0, 1) if the
+    reported dlogZ is the run-to-run error. One JSON line per chain length:
+    the fractions of |z| < 1 and < 2 (0.68 and 0.95 if calibrated) and the
+    pooled scatter over the mean reported dlogZ."""
+    import torch
+    import paper_2509_24949_gb300 as g
+    from paper_2509_24949_gb300 import _build
+    if not _build.up_to_date():
+        _build.build()
+    prec = g.NS_MIXED if args.precision == "mixed" else g.NS_FP64
+    stream = torch.cuda.Stream()
+    R = max(2, args.seeds)
+    per_spd = {5: [], 10: [], 20: []}
+    t0 = time.perf_counter()
+    for i in range(args.injections):
+        w = gi.workload("c1")
+        w.seed_injection += 10 * (i + 1)
+        w.seed_noise += 10 * (i + 1)
+        inputs, th = workload_data(g, w, stream)
+        for spd in per_spd:
+            z, dz = [], []
+            for r in range(R):
+                sp = sampler_on(g, w, inputs, prec, stream, steps_per_dim=spd,
+                                seed=w.seed_sampler + 7919 * (r + 1) + 104729 * i)
+                sp.run()
+                res = sp.result(samples=False)
+                sp.close()
+                z.append(res["logZ"])
+                dz.append(res["dlogZ"])
+            per_spd[spd].append((np.array(z), np.array(dz)))
+    for spd, runs in per_spd.items():
+        zs, ratio_num, ratio_den = [], [], []
+        for z, dz in runs:
+            dev = z - z.mean()
+            zs.extend(dev / (dz * math.sqrt(1.0 - 1.0 / R)))
+            ratio_num.append(np.var(z, ddof=1))
+            ratio_den.append(np.mean(dz) ** 2)
+        zs = np.abs(np.array(zs))
+        print(json.dumps({"study": "evidence calibration over injections", "workload": "c1",
+                          "precision": args.precision, "steps_per_dim": spd, "injections": len(runs),
+                          "seeds_per_injection": R, "frac_within_1_dlogZ": float(np.mean(zs < 1.0)),
+                          "frac_within_2_dlogZ": float(np.mean(zs < 2.0)),
+                          "pooled_sd_over_mean_dlogZ": float(math.sqrt(np.mean(ratio_num) / np.mean(ratio_den))),
+                          "mean_dlogZ": float(np.mean([np.mean(d) for _, d in runs])),
+                          "seconds": time.perf_counter() - t0}), flush=True)
+
+
 def probe_snr2(g, w, th, stream):
     sp = g.sampler_for_workload(w, data=None, precision=g.NS_FP64, n_live=2, k=1, stream=stream.cuda_stream)
     v = sp.snr2(th)
@@ -1048,6 +1128,9 @@ def main():
                     help="mixed against FP64 on one workload (c0, c1, c2): per-point log L on 4096 prior "
                          "draws and log Z over --seeds sampler seeds")
     ap.add_argument("--seeds", type=int, default=8)
+    ap.add_argument("--injections", type=int, default=0,
+                    help="evidence calibration over this many injections (c1; --seeds runs each at 5, 10, "
+                         "20 steps per dimension)")
     ap.add_argument("--n-live", type=int, default=0)
     ap.add_argument("--k", type=int, default=0)
     ap.add_argument("--batch-points", type=int, default=0,
@@ -1058,6 +1141,9 @@ def main():
         args.warmup = 3
     if args.precision_study:
         run_precision_study(args)
+        return
+    if args.injections:
+        run_population_calibration(args)
         return
     if args.table:
         run_table(args)

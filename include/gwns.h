@@ -39,8 +39,8 @@ enum {
     NS_ERR_K_RANGE = -3,       /* k outside 1 .. n_live-1 */
     NS_ERR_OOM = -4,           /* a device allocation failed */
     NS_ERR_CAPACITY = -5,      /* the caller's output buffer is too small */
-    NS_ERR_TIMEOUT = -6,       /* reserved: no call returns it (the kernels have no device-side
-                                  waits that could time out) */
+    NS_ERR_TIMEOUT = -6,       /* a bounded device-side wait gave up (the work-shared slice update
+                                  of mixed precision on the finest grids; ns_stats.status bit 1) */
     NS_ERR_CANCELLED = -7,     /* the request was cancelled */
     NS_ERR_CUDA = -8,          /* a CUDA runtime call failed */
     NS_ERR_STATE = -9          /* call not valid in the context's state */
@@ -223,7 +223,8 @@ typedef struct {
     int n_live;
     int n_dead;
     long long point_bins;   /* sum over slice-update evaluations of the bins each one read */
-    int status;             /* 0, or bit 0: a chain ended early (internal inconsistency) */
+    int status;             /* 0, or bit 0: a chain ended early (internal inconsistency);
+                               bit 1: a bounded wait of the work-shared slice update gave up */
     double kernel_ms[5];    /* cumulative device time of the iteration's kernels, from CUDA
                                events recorded on the context's stream inside the iteration's
                                graph: select, evidence, covariance, slice update, finish */
@@ -367,7 +368,10 @@ typedef struct {
     double logZ, dlogZ;    /* when done */
     long long iterations, evals;
     double t_submit, t_admit, t_done;   /* seconds on the server's clock */
-    size_t footprint;      /* estimated device bytes while running */
+    size_t footprint;      /* estimated device bytes while running: at admission with a dead
+                              list of 64 n entries, then grown with the dead list (which doubles
+                              when a run outgrows it); memory in use is the running analyses'
+                              footprints */
     int n_samples;         /* weighted samples kept (dead + final live) */
 } ns_request_status;
 

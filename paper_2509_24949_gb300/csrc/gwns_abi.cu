@@ -251,6 +251,14 @@ StepArgs step_args(ns_ctx *c, int k) {
                     slots_alloc(c) >= 2) ? 2 : 1;
     A.kernel = c->kernel;
     A.walk_scale = c->walk_scale;
+    // the work-shared update runs where the 8-warp cooperative kernel would
+    const bool ws = c->ws && c->precision == NS_MIXED && !c->M.rb && slots_alloc(c) == 4;
+    A.chain_ctr = ws ? c->chain_ctr : nullptr;
+    A.ws = ws ? c->ws : nullptr;
+    A.ws_part = ws ? c->ws_part : nullptr;
+    A.ws_nslot = ws ? c->ws_nslot : 0;
+    A.ws_gchunk = c->ws_gchunk;
+    A.ws_maxchunk = c->ws_maxchunk;
     return A;
 }
 
@@ -289,7 +297,7 @@ const char *ns_strerror(int code) {
         case NS_ERR_K_RANGE: return "k outside 1 .. n_live-1";
         case NS_ERR_OOM: return "device allocation failed";
         case NS_ERR_CAPACITY: return "output buffer too small";
-        case NS_ERR_TIMEOUT: return "timed out (reserved; not returned)";
+        case NS_ERR_TIMEOUT: return "a bounded device-side wait gave up";
         case NS_ERR_CANCELLED: return "cancelled";
         case NS_ERR_CUDA: return "CUDA runtime error";
         case NS_ERR_STATE: return "call not valid in this state";
@@ -309,7 +317,7 @@ void ns_free(ns_ctx *c) {
                     c->fin_logl, c->fin_logw, c->fin_nlive, c->res, c->rb_J, c->rb_nedge, c->rb_fid,
                     c->rb_fe, c->rb_basis64, c->rb_basis32, c->rb_fe32, c->rb_fm, c->rb_inv_de, c->rb_A0,
                     c->rb_A1, c->rb_B0, c->rb_B1, c->rb_A0f, c->rb_A1f, c->rb_B0f, c->rb_B1f,
-                    c->rb_inv_de_f, c->active};
+                    c->rb_inv_de_f, c->active, c->chain_ctr, c->ws, c->ws_part};
     for (void *p : bufs) dfree(p);
     if (c->h_state) cudaFreeHost(c->h_state);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -513,6 +521,27 @@ int ns_init(ns_ctx **out, const ns_prior *prior, const ns_data *data, const ns_p
         ns_free(c);
         return rc;
     }
+    if (M.model == M_GW && o->precision == NS_MIXED && M.coop && M.tlg >= 5 && M.N >= 262144 &&
+        !(grid && grid->coarse_bins > 0)) {
+        // work-shared slice update: one slot per CTA that fits on the GPU at once;
+        // chunks of 16,384 bins (4 tile groups of 128-bin tiles)
+        const int per_sm = gwns::ws_blocks_per_sm(NS_MIXED, M.n_det);
+        if (per_sm > 0) {
+            c->ws_nslot = per_sm * c->n_sm;
+            c->ws_gchunk = std::max(1, 16384 >> (M.tlg + 5));
+            const int ngroups = (M.np + (32 << M.tlg) - 1) >> (M.tlg + 5);
+            c->ws_maxchunk = (ngroups + c->ws_gchunk - 1) / c->ws_gchunk;
+            if ((rc = dalloc(&c->chain_ctr, 1)) || (rc = dalloc(&c->ws, c->ws_nslot)) ||
+                (rc = dalloc(&c->ws_part, (size_t)c->ws_nslot * c->ws_maxchunk * gwns::WS_PART_PER_CHUNK))) {
+                ns_free(c);
+                return rc;
+            }
+            if (cudaMemsetAsync(c->ws, 0, sizeof(gwns::WsSlot) * c->ws_nslot, c->stream) != cudaSuccess) {
+                ns_free(c);
+                return NS_ERR_CUDA;
+            }
+        }
+    }
     if (cudaMallocHost((void **)&c->h_state, sizeof(RunState)) != cudaSuccess) { ns_free(c); return NS_ERR_OOM; }
     c->timing = true;
     for (cudaEvent_t &e : c->ev)
@@ -602,6 +631,8 @@ static int step_impl(ns_ctx *c, int k, int *done) {
         }
     }
     if (done) *done = c->h_state->done;
+    // status bit 1: a bounded wait of the work-shared slice update gave up
+    if (c->h_state->status & 2) return NS_ERR_TIMEOUT;
     return NS_OK;
 }
 

@@ -38,6 +38,11 @@ struct ns_ctx {
     double *live_u = nullptr, *live_logl = nullptr;
     int *order = nullptr;
     int *active = nullptr;           // running-chain counter of the slice update
+    // work-shared slice update (mixed precision, grids of 262,144 bins or more)
+    int *chain_ctr = nullptr;
+    gwns::WsSlot *ws = nullptr;
+    double *ws_part = nullptr;
+    int ws_nslot = 0, ws_gchunk = 0, ws_maxchunk = 0;
     int n_sm = 152;
     double *chol = nullptr;
     double *dead_u = nullptr, *dead_logl = nullptr, *dead_logw = nullptr, *dead_nlive = nullptr;

@@ -881,7 +881,8 @@ __device__ __forceinline__ void tile_one(const float4 *w4, size_t dstride, int l
 template <int NDET, int NC>
 __device__ __forceinline__ void tile_bins_direct(const Tables &T, int lg, int np, const CoefMixed *cm,
                                           const int *jcut, int nc, int g0, int gstride,
-                                          float zh[NC][NDET][2], float zl[NC][NDET][2]) {
+                                          float zh[NC][NDET][2], float zl[NC][NDET][2],
+                                          int g_end = 0x7fffffff) {
     const int lane = threadIdx.x & 31;
     const int L = 1 << lg, half = L >> 1, nt = np >> lg;
 #pragma unroll
@@ -892,7 +893,7 @@ __device__ __forceinline__ void tile_bins_direct(const Tables &T, int lg, int np
 #pragma unroll
     for (int c = 0; c < NC; c++)
         if (c < nc) jmax = max(jmax, jcut[c]);
-    const int ngroups = jmax < 0 ? 0 : (jmax >> (lg + 5)) + 1;
+    const int ngroups = min(jmax < 0 ? 0 : (jmax >> (lg + 5)) + 1, g_end);
     const float4 *wt4 = reinterpret_cast<const float4 *>(T.wt);
     for (int g = g0; g < ngroups; g += gstride) {
         const int t = (g << 5) + lane, s = t << lg;
@@ -1009,7 +1010,8 @@ __device__ __forceinline__ void tile_bins_direct(const Tables &T, int lg, int np
 template <int NDET, int NC, bool PF>
 __device__ __forceinline__ void tile_bins_rot(const Tables &T, int lg, int np, const CoefMixed *cm,
                                               const int *jcut, int nc, int g0, int gstride,
-                                              float zh[NC][NDET][2], float zl[NC][NDET][2]) {
+                                              float zh[NC][NDET][2], float zl[NC][NDET][2],
+                                              int g_end = 0x7fffffff) {
     const int lane = threadIdx.x & 31;
     const int L = 1 << lg, half = L >> 1, nt = np >> lg;
 #pragma unroll
@@ -1020,7 +1022,7 @@ __device__ __forceinline__ void tile_bins_rot(const Tables &T, int lg, int np, c
 #pragma unroll
     for (int c = 0; c < NC; c++)
         if (c < nc) jmax = max(jmax, jcut[c]);
-    const int ngroups = jmax < 0 ? 0 : (jmax >> (lg + 5)) + 1;
+    const int ngroups = min(jmax < 0 ? 0 : (jmax >> (lg + 5)) + 1, g_end);
     const float4 *wt4 = reinterpret_cast<const float4 *>(T.wt);
     const size_t dstride = (size_t)np >> 1;
     for (int g = g0; g < ngroups; g += gstride) {
@@ -1109,11 +1111,12 @@ __device__ __forceinline__ void tile_bins_rot(const Tables &T, int lg, int np, c
 template <int NDET, int NC, bool ROT, bool PF = false>
 __device__ __forceinline__ void tile_bins(const Tables &T, int lg, int np, const CoefMixed *cm,
                                           const int *jcut, int nc, int g0, int gstride,
-                                          float zh[NC][NDET][2], float zl[NC][NDET][2]) {
+                                          float zh[NC][NDET][2], float zl[NC][NDET][2],
+                                          int g_end = 0x7fffffff) {
     if constexpr (ROT)
-        tile_bins_rot<NDET, NC, PF>(T, lg, np, cm, jcut, nc, g0, gstride, zh, zl);
+        tile_bins_rot<NDET, NC, PF>(T, lg, np, cm, jcut, nc, g0, gstride, zh, zl, g_end);
     else
-        tile_bins_direct<NDET, NC>(T, lg, np, cm, jcut, nc, g0, gstride, zh, zl);
+        tile_bins_direct<NDET, NC>(T, lg, np, cm, jcut, nc, g0, gstride, zh, zl, g_end);
 }
 
 // Double-float warp sum (TwoSum of the high parts, low parts added).

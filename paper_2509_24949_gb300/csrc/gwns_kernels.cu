@@ -257,6 +257,16 @@ static cudaError_t slice_d(const Model &M, const Tables &T, int slots, const Ste
     }
 }
 
+int ws_blocks_per_sm(int precision, int ndet) {
+    if (precision != 1) return 0;
+    switch (ndet) {
+        case 1: return slice_ws_blocks_per_sm<1, 1>();
+        case 2: return slice_ws_blocks_per_sm<1, 2>();
+        case 3: return slice_ws_blocks_per_sm<1, 3>();
+        default: return slice_ws_blocks_per_sm<1, 4>();
+    }
+}
+
 cudaError_t launch_slice(const Model &M, const Tables &T, int precision, int slots, const StepArgs &A,
                          cudaStream_t s) {
     return precision == 1 ? slice_d<1>(M, T, slots, A, s) : slice_d<0>(M, T, slots, A, s);
@@ -426,6 +436,7 @@ __device__ void cov_chol_body(const Model &M, const StepArgs &A) {
         cov[pj * d + pi] = v;
     }
     if (threadIdx.x == 0 && A.active) *A.active = A.k;     // chains of the coming slice update
+    if (threadIdx.x == 0 && A.chain_ctr) *A.chain_ctr = 0;  // next chain for the work-shared update
     __syncthreads();
     if (threadIdx.x < 32) {
         const int lane = threadIdx.x;

@@ -30,6 +30,22 @@ struct RunState {
     unsigned long long eval_point_bins;  // their sum of (jcut + 1)
 };
 
+// Work-shared slice update (mixed precision, fine tiled grids): one slot per
+// persistent CTA. A round's tile groups are cut into fixed chunks of
+// ws_gchunk groups; the owner publishes the round's candidates in its slot and
+// any warp of the launch (its own, or of CTAs with no chain left) claims chunks
+// through the claim word and adds its partial sums to the slot's partials.
+struct WsSlot {
+    unsigned long long word;   // seq (bits 40..63) | chunks of the round (20..39) | next chunk (0..19)
+    int done;                  // chunks of the round whose partials are written
+    int ns;                    // candidates of the round
+    int jc[4];                 // their last bins
+    int pad[2];
+    CoefMixed cm[4];           // their mixed-precision coefficients
+};
+
+constexpr int WS_PART_PER_CHUNK = 4 * MAXDET * 2;   // doubles: [candidate][detector][re, im]
+
 struct StepArgs {
     double *live_u;       // [n][d]
     double *live_logl;    // [n]
@@ -50,6 +66,12 @@ struct StepArgs {
                           // always the same split, so results do not depend on timing)
     int kernel;           // 0 slice sampling, 1 random walk
     double walk_scale;    // random walk: y = x + walk_scale L z
+    // work-shared slice update (ws != nullptr): persistent CTAs take chains from
+    // chain_ctr; ws_nslot slots, partials [ws_nslot][ws_maxchunk][WS_PART_PER_CHUNK]
+    int *chain_ctr;
+    WsSlot *ws;
+    double *ws_part;
+    int ws_nslot, ws_gchunk, ws_maxchunk;
 };
 
 // One analysis' iteration arguments, for the multi-analysis launches.
@@ -105,6 +127,10 @@ template <int PREC, int NDET>
 cudaError_t slice_launch(const Model &M, const Tables &T, int slots, const StepArgs &A, cudaStream_t s);
 template <int PREC, int NDET>
 cudaError_t slice_multi_launch(const Desc *D, const int2 *map, int nblocks, int slots, cudaStream_t s);
+template <int PREC, int NDET>
+int slice_ws_blocks_per_sm();
+// CTAs of the work-shared slice update per SM for this precision and detector count.
+int ws_blocks_per_sm(int precision, int ndet);
 
 // Launchers (return cudaGetLastError()).
 cudaError_t launch_build_tables(const Model &M, const double *data_re, const double *data_im,

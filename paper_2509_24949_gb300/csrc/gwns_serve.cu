@@ -40,19 +40,31 @@ struct Request {
     std::vector<double> s_u, s_logl, s_logw, s_theta;
 };
 
-size_t footprint(const Request &r) {
-    // tables: FP64 basis, f, weighted data, prefix, data and PSD copies; the
-    // mixed form's tiled increments, weighted data and tile anchors (grid
-    // padded by less than 1024 bins); live, final and dead sets; fixed overhead
+int sampled_dim(const Request &r) {
     int d = 0;
     for (int p = 0; p < NS_NPARAM; p++) d += r.prior.kind[p] != NS_PRIOR_FIXED;
-    const size_t N = r.N, D = r.n_det, n = r.opts.n_live;
+    return d;
+}
+
+// Device bytes of an analysis apart from its dead list: FP64 basis, f,
+// weighted data, prefix, data and PSD copies; the mixed form's tiled
+// increments, weighted data and tile anchors (grid padded by less than 1024
+// bins); live and final sets; relative-binning tables; fixed overhead.
+size_t footprint_base(const Request &r) {
+    const size_t N = r.N, D = r.n_det, n = r.opts.n_live, d = sampled_dim(r);
     size_t b = (72 + 48 * D) * N + (37 + 8 * D) * (N + 1024);
     b += n * (16 * d + 40);
-    b += 64 * n * (size_t)(d + 3) * 8;
     if (r.coarse_bins > 0) b += (size_t)(r.coarse_bins + 1) * (160 + 64 * D) + 16 * D * N;
     return b + (1u << 20);
 }
+
+// Dead-list bytes at a capacity of cap entries (u, log L, log w, n_live).
+size_t dead_bytes(const Request &r, long long cap) { return (size_t)cap * (size_t)(sampled_dim(r) + 3) * 8; }
+
+// Estimated device bytes at admission: the dead list starts at 64 n entries
+// and doubles when the run outgrows it; the server then adds the growth to the
+// analysis' footprint and to the memory in use (see iterate_all).
+size_t footprint(const Request &r) { return footprint_base(r) + dead_bytes(r, 64LL * r.opts.n_live); }
 
 }  // namespace
 
@@ -167,10 +179,22 @@ int iterate_all(ns_server *s) {
     // analysis always runs at its own width, whatever the mix
     std::map<std::pair<int, int>, std::vector<int2>> groups;
     for (int a = 0; a < na; a++) {
-        ns_ctx *c = s->reqs[s->running[a]].ctx;
+        Request &r = s->reqs[s->running[a]];
+        ns_ctx *c = r.ctx;
         const int k = c->k_default;
+        const long long cap0 = c->dead_cap;
         int rc = ensure_dead_capacity(c, c->n_dead + k);
         if (rc) return rc;
+        if (c->dead_cap != cap0) {
+            // the dead list doubled: count the new size (memory in use is the
+            // running analyses' actual footprints, so admission stays within
+            // the budget however long the runs grow)
+            const size_t fp = footprint_base(r) + dead_bytes(r, c->dead_cap);
+            if (fp > r.st.footprint) {
+                s->used += fp - r.st.footprint;
+                r.st.footprint = fp;
+            }
+        }
         desc[a].M = c->M;
         desc[a].T = c->T;
         desc[a].A = step_args(c, k);

@@ -480,10 +480,184 @@ __device__ int walk_plan(const Model &M, const StepArgs &A, const Chain &c, int 
     return ns;
 }
 
+// ------------------------------------------------- work-shared slice update
+// Mixed precision on fine tiled grids (the 519,169-bin workload): when fewer
+// chains remain than CTA slots, the update's last chains would run alone on
+// otherwise idle SMs. Instead, persistent CTAs take chains from a counter, and
+// each round's candidates are evaluated in fixed chunks of ws_gchunk tile
+// groups. The owner publishes the round in its slot (coefficients, then the
+// claim word); its own warps and the warps of CTAs without a chain claim
+// chunks through the word, each chunk's sums are computed by one warp and
+// written to the slot's partials, and the owner adds them in chunk order. The
+// decomposition does not depend on who computes a chunk, so results do not
+// depend on timing. No warp waits on a CTA that has not claimed work: the
+// owner waits only for chunks already claimed (their warps are running), and
+// helpers stop once no chain is running. Both waits are bounded; on a timeout
+// the run state's status gets bit 1 and the host reports NS_ERR_TIMEOUT.
+constexpr long long WS_WAIT_LIMIT = 1ll << 24;   // owner polls of the done count (~100 ns apart)
+constexpr long long WS_IDLE_LIMIT = 1ll << 22;   // consecutive helper polls without work (~1 us each)
+
+__device__ __forceinline__ unsigned long long ws_word(unsigned long long seq, int n, int next) {
+    return (seq << 40) | ((unsigned long long)n << 20) | (unsigned long long)next;
+}
+
+// Lane 0: claim the next chunk of a slot's round; -1 if none is left. A stale
+// view of the word is harmless: the atomic's return value names the round and
+// chunk actually claimed, and a round's data stay in place until all its
+// claimed chunks are done.
+__device__ __forceinline__ int ws_claim(WsSlot *s) {
+    const unsigned long long w = *((volatile unsigned long long *)&s->word);
+    if ((w & 0xFFFFFull) >= ((w >> 20) & 0xFFFFFull)) return -1;
+    const unsigned long long old = atomicAdd(&s->word, 1ull);
+    const int n = (int)((old >> 20) & 0xFFFFFull), nx = (int)(old & 0xFFFFFull);
+    return nx < n ? nx : -1;
+}
+
+// One warp: the sums of chunk c (tile groups c G .. c G + G - 1) for the ns
+// candidates, reduced over the warp; lane 0 writes out[candidate][detector][re, im].
+template <int NDET>
+__device__ __forceinline__ void ws_chunk(const Model &M, const Tables &T, const CoefMixed *cm, const int *jc,
+                                         int ns, int c, int G, double *out) {
+    const int lane = threadIdx.x & 31;
+    const int g0 = c * G, g1 = g0 + G;
+    for (int c0 = 0; c0 < ns; c0 += 2) {
+        float zh[2][NDET][2], zl[2][NDET][2];
+        const int nc = ns - c0 < 2 ? ns - c0 : 2;
+        tile_bins<NDET, 2, true>(T, M.tlg, M.np, cm + c0, jc + c0, nc, g0, 1, zh, zl, g1);
+#pragma unroll
+        for (int sc = 0; sc < 2; sc++)
+#pragma unroll
+            for (int dd = 0; dd < NDET; dd++) {
+                warp_sum_df(zh[sc][dd][0], zl[sc][dd][0]);
+                warp_sum_df(zh[sc][dd][1], zl[sc][dd][1]);
+                if (lane == 0 && c0 + sc < ns) {
+                    out[((c0 + sc) * MAXDET + dd) * 2] = (double)zh[sc][dd][0] + (double)zl[sc][dd][0];
+                    out[((c0 + sc) * MAXDET + dd) * 2 + 1] = (double)zh[sc][dd][1] + (double)zl[sc][dd][1];
+                }
+            }
+    }
+}
+
+// Owner CTA (all threads): publish the round's ns candidates (coefficients cm,
+// last bins jc, in shared memory), take part in its chunks, then warp 0 waits
+// for the chunks helpers took and writes the sums over chunks, in chunk order,
+// to zs[candidate][detector][re, im] (shared).
+template <int NDET, int W>
+__device__ void ws_owner_round(const Model &M, const Tables &T, const StepArgs &A, const CoefMixed *cm,
+                               const int *jc, int ns, double (*zs)[NDET][2]) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WsSlot *slot = A.ws + blockIdx.x;
+    double *part = A.ws_part + (size_t)blockIdx.x * A.ws_maxchunk * WS_PART_PER_CHUNK;
+    int jmax = -1;
+    for (int c = 0; c < ns; c++) jmax = max(jmax, jc[c]);
+    const int G = A.ws_gchunk;
+    const int ng = jmax < 0 ? 0 : (jmax >> (M.tlg + 5)) + 1;
+    const int nch = min((ng + G - 1) / G, A.ws_maxchunk);
+    const int nwords = ns * (int)(sizeof(CoefMixed) / sizeof(int));
+    for (int i = threadIdx.x; i < nwords; i += W * 32) ((int *)slot->cm)[i] = ((const int *)cm)[i];
+    if (threadIdx.x < ns) slot->jc[threadIdx.x] = jc[threadIdx.x];
+    if (threadIdx.x == 0) {
+        slot->ns = ns;
+        slot->done = 0;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned long long w = *((volatile unsigned long long *)&slot->word);
+        atomicExch(&slot->word, ws_word((w >> 40) + 1, nch, 0));
+    }
+    __syncthreads();
+    for (int guard = 0; guard < (1 << 20); guard++) {
+        int c = -1;
+        if (lane == 0) c = ws_claim(slot);
+        c = __shfl_sync(0xffffffffu, c, 0);
+        if (c < 0) break;
+        ws_chunk<NDET>(M, T, cm, jc, ns, c, G, part + (size_t)c * WS_PART_PER_CHUNK);
+        __threadfence();
+        if (lane == 0) atomicAdd(&slot->done, 1);
+    }
+    if (warp == 0) {
+        if (lane == 0) {
+            for (long long it = 0; *((volatile int *)&slot->done) < nch; it++) {
+                if (it > WS_WAIT_LIMIT) {
+                    atomicOr(&A.state->status, 2);
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __syncwarp();
+        __threadfence();
+        const int sc = lane / NDET, dd = lane - sc * NDET;
+        if (lane < ns * NDET) {
+            double zr = 0.0, zi = 0.0;
+            for (int c = 0; c < nch; c++) {
+                const double *p = part + (size_t)c * WS_PART_PER_CHUNK + (sc * MAXDET + dd) * 2;
+                zr += __ldcg(p);
+                zi += __ldcg(p + 1);
+            }
+            zs[sc][dd][0] = zr;
+            zs[sc][dd][1] = zi;
+        }
+    }
+}
+
+// A CTA without a chain left: each warp claims chunks of any running chain's
+// round until no chain is running.
+template <int NDET, int W>
+__device__ void ws_help(const Model &M, const Tables &T, const StepArgs &A) {
+    __shared__ CoefMixed hcm[W][4];
+    __shared__ int hjc[W][4];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nslot = A.ws_nslot;
+    const int start = (int)(((unsigned)blockIdx.x * 37u + (unsigned)warp * 11u) % (unsigned)nslot);
+    long long idle = 0;
+    for (;;) {
+        if (*((volatile int *)A.active) <= 0) break;
+        int found = -1;
+        for (int base = 0; base < nslot && found < 0; base += 32) {
+            const int j = base + lane;
+            int s = start + j;
+            if (s >= nslot) s -= nslot;
+            bool open = false;
+            if (j < nslot) {
+                const unsigned long long w = *((volatile unsigned long long *)&A.ws[s].word);
+                open = (w & 0xFFFFFull) < ((w >> 20) & 0xFFFFFull);
+            }
+            const unsigned b = __ballot_sync(0xffffffffu, open);
+            if (b) found = __shfl_sync(0xffffffffu, s, __ffs(b) - 1);
+        }
+        int c = -1;
+        if (found >= 0 && lane == 0) c = ws_claim(A.ws + found);
+        c = __shfl_sync(0xffffffffu, c, 0);
+        if (c < 0) {
+            if (++idle > WS_IDLE_LIMIT) {
+                if (lane == 0) atomicOr(&A.state->status, 2);
+                break;
+            }
+            __nanosleep(200);
+            continue;
+        }
+        idle = 0;
+        __threadfence();
+        WsSlot *sl = A.ws + found;
+        const int ns = __ldcg(&sl->ns);
+        const int nwords = ns * (int)(sizeof(CoefMixed) / sizeof(int));
+        for (int i = lane; i < nwords; i += 32) ((int *)hcm[warp])[i] = __ldcg(((const int *)sl->cm) + i);
+        if (lane < ns) hjc[warp][lane] = __ldcg(&sl->jc[lane]);
+        __syncwarp();
+        ws_chunk<NDET>(M, T, hcm[warp], hjc[warp], ns, c, A.ws_gchunk,
+                       A.ws_part + ((size_t)found * A.ws_maxchunk + c) * WS_PART_PER_CHUNK);
+        __threadfence();
+        if (lane == 0) atomicAdd(&sl->done, 1);
+        __syncwarp();
+    }
+}
+
 // ROTOK: the tiled mixed form sums tiles of 32 bins or more by rotation
 // (tile_bins_rot); without it every tile length takes the direct form, and
 // the kernel compiles one form only.
-template <int PREC, int NDET, int S, int W = S, bool ROTOK = true>
+template <int PREC, int NDET, int S, int W = S, bool ROTOK = true, bool WS = false>
 __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, const int chain) {
     __shared__ Coef coef[S];
     __shared__ CoefMixed cm[S];
@@ -600,7 +774,11 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
             if (warp < ns) coef_to_mixed_warp(coef[warp], M.n_det, M.df, &cm[warp], nullptr, ROTOK && M.tlg >= 5);
             if (lane == 0 && warp < ns) jc[warp] = coef[warp].jcut;
             __syncthreads();
-            if (M.tlg) {
+            if (WS) {
+                // work-shared: fixed chunks of tile groups, computed by this CTA's
+                // warps and by helper CTAs, summed in chunk order into part[0]
+                ws_owner_round<NDET, W>(M, T, A, cm, jc, ns, part[0]);
+            } else if (M.tlg) {
                 for (int c0 = 0; c0 < ns; c0 += 2) {
                     float zh[2][NDET][2], zl[2][NDET][2];
                     const int nc = ns - c0 < 2 ? ns - c0 : 2;
@@ -642,7 +820,7 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
                 const int sc = lane / NDET, dd = lane % NDET;
                 if (sc < ns && lane < S * NDET) {
                     double ZR = 0.0, ZI = 0.0;
-                    for (int w2 = 0; w2 < W; w2++) { ZR += part[w2][sc][dd][0]; ZI += part[w2][sc][dd][1]; }
+                    for (int w2 = 0; w2 < (WS ? 1 : W); w2++) { ZR += part[w2][sc][dd][0]; ZI += part[w2][sc][dd][1]; }
                     v = coef[sc].gre[dd] * ZR - coef[sc].gim[dd] * ZI;
                 }
                 for (int sc2 = 0; sc2 < ns; sc2++) {
@@ -765,6 +943,39 @@ __global__ void __launch_bounds__(W * 32, SLICE_MIN_BLOCKS(PREC, W)) k_slice(Mod
     slice_body<PREC, NDET, S, W>(M, T, A, blockIdx.x);
 }
 
+// The work-shared slice update: persistent CTAs (as many as fit on the GPU at
+// once) take chains until none is left, then help the running ones.
+template <int NDET>
+__global__ void __launch_bounds__(256, SLICE_MIN_BLOCKS(1, 8)) k_slice_ws(Model M, Tables T, StepArgs A) {
+    __shared__ int s_chain;
+    for (int guard = 0; guard < (1 << 20); guard++) {
+        if (threadIdx.x == 0) s_chain = atomicAdd(A.chain_ctr, 1);
+        __syncthreads();
+        const int chain = s_chain;
+        __syncthreads();
+        if (chain >= A.k) break;
+        slice_body<1, NDET, 4, 8, true, true>(M, T, A, chain);
+        __syncthreads();
+    }
+    ws_help<NDET, 8>(M, T, A);
+}
+
+// CTAs of the work-shared slice update that fit on one SM (0: not used for
+// this precision).
+template <int PREC, int NDET>
+int slice_ws_blocks_per_sm() {
+    if constexpr (PREC == 1) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_slice_ws<NDET>, 256, 0) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        return nb;
+    } else {
+        return 0;
+    }
+}
+
 template <int PREC, int NDET>
 cudaError_t slice_launch(const Model &M, const Tables &T, int slots, const StepArgs &A, cudaStream_t s) {
     // on grids of 262,144 bins or more in tiles of 32 bins or more the tiled
@@ -775,6 +986,12 @@ cudaError_t slice_launch(const Model &M, const Tables &T, int slots, const StepA
     // hence the threshold)
     if (PREC == 1 && slots == 4 && M.model == M_GW && M.coop && M.tlg >= 5 && !M.rb &&
         M.N >= 262144) {
+        if constexpr (PREC == 1) {
+            if (A.ws) {
+                k_slice_ws<NDET><<<A.ws_nslot, 256, 0, s>>>(M, T, A);
+                return cudaGetLastError();
+            }
+        }
         k_slice<PREC, NDET, 4, 8><<<A.k, 256, 0, s>>>(M, T, A);
         return cudaGetLastError();
     }
@@ -811,6 +1028,7 @@ cudaError_t slice_multi_launch(const Desc *D, const int2 *map, int nblocks, int 
 
 // Explicit instantiation of the launchers of one (precision, detectors) pair.
 #define GWNS_INSTANTIATE(P, D)                                                                       \
+    template int slice_ws_blocks_per_sm<P, D>();                                                     \
     template cudaError_t eval_launch<P, D>(const Model &, const Tables &, int, const double *, int, int, \
                                            double *, RunState *, cudaStream_t);                     \
     template cudaError_t slice_launch<P, D>(const Model &, const Tables &, int, const StepArgs &,     \

@@ -284,30 +284,33 @@ def test_fp64_iteration_on_the_large_grids_matches_oracle(gw, name, n_live, k, s
     assert s["evals"] == st.evals and s["status"] == 0
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_runs_at_the_benchmark_population_are_bit_identical(gw, precision):
-    """Two fresh runs of the 4017-bin workload at 1000 live points and 500
-    chains per iteration (more chains than SMs, so chains finish in a
-    timing-dependent order) give bit-identical live sets and log Z, and so does
-    a run resumed from a checkpoint taken halfway."""
-    w, pb, th = problem("c1")
+@pytest.mark.parametrize("name,precision,half", [("c1", 0, 3), ("c1", 1, 3), ("c4", 1, 1)])
+def test_runs_at_the_benchmark_population_are_bit_identical(gw, name, precision, half):
+    """Two fresh runs at the workload's own population (1000 live points and
+    500 chains on 4017 bins; 2000 and 1000 on 519,169 bins, where the mixed
+    update is work-shared: chains finish in a timing-dependent order and the
+    CTAs left without a chain help the running ones with chunks of their tile
+    groups) give bit-identical live sets and log Z, and so does a run resumed
+    from a checkpoint taken halfway."""
+    w, pb, th = problem(name)
     args = dict(n_live=w.n_live, k=w.k, steps_per_dim=w.steps_per_dim, seed=w.seed_sampler)
     runs = []
     for r in range(2):
         with sampler_from(gw, pb, precision, **args) as sp:
-            for _ in range(3):
+            for _ in range(half):
                 sp.step()
             blob = sp.checkpoint() if r == 0 else None
-            for _ in range(3):
+            for _ in range(half):
                 sp.step()
             runs.append((sp.live(), sp.stats(), blob))
+            assert runs[-1][1]["status"] == 0
     (ua, la), sa, blob = runs[0]
     (ub, lb), sb, _ = runs[1]
     assert np.array_equal(ua, ub) and np.array_equal(la, lb)
     assert sa["logZ"] == sb["logZ"] and sa["evals"] == sb["evals"]
     with sampler_from(gw, pb, precision, **args) as sp:
         sp.restore(blob)
-        for _ in range(3):
+        for _ in range(half):
             sp.step()
         uc, lc = sp.live()
         sc = sp.stats()
@@ -616,9 +619,11 @@ def test_mixed_form_choice(gw, name, over, tile):
 
 
 def test_mixed_wide_ctas_on_the_largest_grid(gw):
-    """The 519,169-bin grid runs the mixed slice update with 8-warp CTAs
-    (128-bin tiles shared out by all warps, by rotation): live points after one
-    iteration agree with the oracle per point."""
+    """The 519,169-bin grid runs the work-shared mixed slice update (8-warp
+    persistent CTAs; 128-bin tiles by rotation, in chunks of four tile groups
+    computed by the chain's own CTA and by the CTAs left without a chain, here
+    almost all of them): live points after one iteration agree with the oracle
+    per point, and no bounded wait gave up."""
     w, pb, th = problem("c4")
     with sampler_from(gw, pb, 1, n_live=24, k=12, steps_per_dim=1, seed=11) as sp:
         assert sp.stats()["mixed_tile"] == 128

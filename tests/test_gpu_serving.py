@@ -10,8 +10,10 @@ import oracle
 pytestmark = pytest.mark.gpu
 
 
-def _analysis(seed_offset, N=1200, n_live=80, n_det=3, df=None):
-    w = gi.workload("c1", n_live=n_live, k=n_live // 2)
+def _analysis(seed_offset, N=1200, n_live=80, n_det=3, df=None, k=None, snr=None):
+    w = gi.workload("c1", n_live=n_live, k=k if k else n_live // 2)
+    if snr is not None:
+        w.snr = snr
     w.N = N
     w.n_det = n_det
     if df is not None:
@@ -161,3 +163,40 @@ def test_cancel(gw):
         assert srv.poll(ids[2])["state"] == gw.NS_REQ_DONE
         with pytest.raises(gw.GWNSError):
             srv.cancel(ids[2])
+
+
+def test_footprint_counts_the_dead_list_growth(gw):
+    """An analysis that runs past 64 n dead points (8 live points, one deleted
+    per iteration, a loud SNR-40 injection and a stopping tolerance it only
+    meets once the remaining evidence underflows) doubles its dead list; the
+    server adds the growth to its footprint and to the memory in use, so a
+    request that fitted beside the analysis' admission footprint waits until
+    the analysis is done."""
+    long_req, dim = _analysis(50, n_live=8, k=1, snr=40.0)
+    long_req = dict(long_req, dlogz_stop=1e-300)
+    other, _ = _analysis(51, n_live=8, k=4)
+    with gw.Server(precision=1) as probe:
+        fa = probe.poll(probe.submit(**long_req))["footprint"]
+        fb = probe.poll(probe.submit(**other))["footprint"]
+    dead64 = 64 * 8 * (dim + 3) * 8          # the initial dead list: u, log L, log w, n_live
+    with gw.Server(precision=1, mem_budget=fa + fb + dead64 // 2, max_iter=4000) as srv:
+        ra = srv.submit(**long_req)
+        grown = False
+        for _ in range(4000):
+            srv.tick()
+            st = srv.poll(ra)
+            if st["footprint"] > fa:
+                grown = True
+                break
+            if st["state"] != gw.NS_REQ_RUNNING:
+                break
+        assert grown, st
+        assert st["state"] == gw.NS_REQ_RUNNING and st["footprint"] == fa + dead64
+        rb = srv.submit(**other)
+        srv.tick()
+        if srv.poll(ra)["state"] == gw.NS_REQ_RUNNING:
+            assert srv.poll(rb)["state"] == gw.NS_REQ_PENDING
+        srv.run_until_idle()
+        sa, sb = srv.poll(ra), srv.poll(rb)
+        assert sa["state"] == gw.NS_REQ_DONE and sb["state"] == gw.NS_REQ_DONE
+        assert sb["t_admit"] >= sa["t_done"]
