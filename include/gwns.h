@@ -133,7 +133,9 @@ typedef struct {
     int warps_per_point; /* warps cooperating on one batched likelihood (1,2,4,8) [0: rule] */
     int slots;           /* candidates one chain evaluates concurrently in the slice
                             update, one warp each (1,2,4,8) [0: rule] */
-    double dlogz_stop;   /* stop when log(Z + X Lmax) - log Z < this [0.1] */
+    double dlogz_stop;   /* stop when log(Z + X Lmax) - log Z < this [0.1]; a negative value is
+                            never met, so the run goes on to its iteration cap (ns_run's
+                            max_iter, the server's max_iter) */
     uint64_t seed;       /* Philox key */
     void *stream;        /* cudaStream_t to run on [NULL: library-owned stream] */
     int kernel;          /* inner kernel of the update: NS_KERNEL_SLICE (slice sampling along

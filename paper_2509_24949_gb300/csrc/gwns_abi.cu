@@ -436,7 +436,9 @@ int ns_init(ns_ctx **out, const ns_prior *prior, const ns_data *data, const ns_p
     c->max_sh = o->max_shrink ? o->max_shrink : 64;
     c->warps = o->warps_per_point;
     c->slots = o->slots;
-    c->dlogz = o->dlogz_stop > 0.0 ? o->dlogz_stop : 0.1;
+    // zero takes the default; a negative tolerance is never met (the run goes
+    // on to its iteration cap)
+    c->dlogz = o->dlogz_stop != 0.0 ? o->dlogz_stop : 0.1;
     c->seed = o->seed;
     if (o->kernel != NS_KERNEL_SLICE && o->kernel != NS_KERNEL_WALK) { delete c; return NS_ERR_INVALID_ARG; }
     c->kernel = o->kernel;
@@ -524,11 +526,12 @@ int ns_init(ns_ctx **out, const ns_prior *prior, const ns_data *data, const ns_p
     if (M.model == M_GW && o->precision == NS_MIXED && M.coop && M.tlg >= 5 && M.N >= 262144 &&
         !(grid && grid->coarse_bins > 0)) {
         // work-shared slice update: one slot per CTA that fits on the GPU at once;
-        // chunks of 16,384 bins (4 tile groups of 128-bin tiles)
+        // chunks of 8,192 bins (2 tile groups of 128-bin tiles; GB300, 519,169 bins:
+        // 257 ms per update against 263 ms with chunks of 4 groups)
         const int per_sm = gwns::ws_blocks_per_sm(NS_MIXED, M.n_det);
         if (per_sm > 0) {
             c->ws_nslot = per_sm * c->n_sm;
-            c->ws_gchunk = std::max(1, 16384 >> (M.tlg + 5));
+            c->ws_gchunk = std::max(1, 8192 >> (M.tlg + 5));
             const int ngroups = (M.np + (32 << M.tlg) - 1) >> (M.tlg + 5);
             c->ws_maxchunk = (ngroups + c->ws_gchunk - 1) / c->ws_gchunk;
             if ((rc = dalloc(&c->chain_ctr, 1)) || (rc = dalloc(&c->ws, c->ws_nslot)) ||

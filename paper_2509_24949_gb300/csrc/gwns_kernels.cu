@@ -873,21 +873,21 @@ cudaError_t launch_iteration_multi_head(const Desc *D, int n_an, cudaStream_t s)
 }
 
 cudaError_t launch_slice_multi(const Desc *D, const int2 *map, int nblocks, int precision, int ndet, int slots,
-                               cudaStream_t s) {
+                               int rot, cudaStream_t s) {
     if (nblocks <= 0) return cudaSuccess;
     if (precision == 1) {
         switch (ndet) {
-            case 1: return slice_multi_launch<1, 1>(D, map, nblocks, slots, s);
-            case 2: return slice_multi_launch<1, 2>(D, map, nblocks, slots, s);
-            case 3: return slice_multi_launch<1, 3>(D, map, nblocks, slots, s);
-            default: return slice_multi_launch<1, 4>(D, map, nblocks, slots, s);
+            case 1: return slice_multi_launch<1, 1>(D, map, nblocks, slots, rot, s);
+            case 2: return slice_multi_launch<1, 2>(D, map, nblocks, slots, rot, s);
+            case 3: return slice_multi_launch<1, 3>(D, map, nblocks, slots, rot, s);
+            default: return slice_multi_launch<1, 4>(D, map, nblocks, slots, rot, s);
         }
     }
     switch (ndet) {
-        case 1: return slice_multi_launch<0, 1>(D, map, nblocks, slots, s);
-        case 2: return slice_multi_launch<0, 2>(D, map, nblocks, slots, s);
-        case 3: return slice_multi_launch<0, 3>(D, map, nblocks, slots, s);
-        default: return slice_multi_launch<0, 4>(D, map, nblocks, slots, s);
+        case 1: return slice_multi_launch<0, 1>(D, map, nblocks, slots, 0, s);
+        case 2: return slice_multi_launch<0, 2>(D, map, nblocks, slots, 0, s);
+        case 3: return slice_multi_launch<0, 3>(D, map, nblocks, slots, 0, s);
+        default: return slice_multi_launch<0, 4>(D, map, nblocks, slots, 0, s);
     }
 }
 

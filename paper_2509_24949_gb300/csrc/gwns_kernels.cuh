@@ -126,7 +126,7 @@ cudaError_t eval_launch(const Model &M, const Tables &T, int warps, const double
 template <int PREC, int NDET>
 cudaError_t slice_launch(const Model &M, const Tables &T, int slots, const StepArgs &A, cudaStream_t s);
 template <int PREC, int NDET>
-cudaError_t slice_multi_launch(const Desc *D, const int2 *map, int nblocks, int slots, cudaStream_t s);
+cudaError_t slice_multi_launch(const Desc *D, const int2 *map, int nblocks, int slots, int rot, cudaStream_t s);
 template <int PREC, int NDET>
 int slice_ws_blocks_per_sm();
 // CTAs of the work-shared slice update per SM for this precision and detector count.
@@ -149,8 +149,10 @@ cudaError_t launch_final_live(const Model &M, const StepArgs &A, double *fin_u, 
                               double *fin_logw, double *fin_nlive, double *logz_total, cudaStream_t s);
 cudaError_t launch_result_stats(const ResultArgs &R, cudaStream_t s);
 cudaError_t launch_iteration_multi_head(const Desc *D, int n_an, cudaStream_t s);
+// rot = 1: the analyses of the launch are mixed, with tiles of 32 bins or more
+// (rotation-form kernel); 0: direct-form kernel.
 cudaError_t launch_slice_multi(const Desc *D, const int2 *map, int nblocks, int precision, int ndet, int slots,
-                               cudaStream_t s);
+                               int rot, cudaStream_t s);
 cudaError_t launch_iteration_multi_tail(const Desc *D, int n_an, cudaStream_t s);
 cudaError_t launch_theta(const Model &M, const double *u, long long m, double *theta, cudaStream_t s);
 cudaError_t launch_rb_setup(const Model &M, const Tables &T, int B, const double *theta_fid, int *J,

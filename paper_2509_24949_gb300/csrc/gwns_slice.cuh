@@ -538,6 +538,48 @@ __device__ __forceinline__ void ws_chunk(const Model &M, const Tables &T, const 
     }
 }
 
+// One warp: find a slot (other than skip) with an unclaimed chunk, claim it
+// and compute it into that slot's partials. Returns 1 if it did a chunk. The
+// round's coefficients are staged in this warp's shared buffer.
+template <int NDET, int W>
+__device__ int ws_take_any(const Model &M, const Tables &T, const StepArgs &A, int skip) {
+    __shared__ CoefMixed hcm[W][4];
+    __shared__ int hjc[W][4];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nslot = A.ws_nslot;
+    const int start = (int)(((unsigned)blockIdx.x * 37u + (unsigned)warp * 11u) % (unsigned)nslot);
+    int found = -1;
+    for (int base = 0; base < nslot && found < 0; base += 32) {
+        const int j = base + lane;
+        int s = start + j;
+        if (s >= nslot) s -= nslot;
+        bool open = false;
+        if (j < nslot && s != skip) {
+            const unsigned long long w = *((volatile unsigned long long *)&A.ws[s].word);
+            open = (w & 0xFFFFFull) < ((w >> 20) & 0xFFFFFull);
+        }
+        const unsigned b = __ballot_sync(0xffffffffu, open);
+        if (b) found = __shfl_sync(0xffffffffu, s, __ffs(b) - 1);
+    }
+    int c = -1;
+    if (found >= 0 && lane == 0) c = ws_claim(A.ws + found);
+    c = __shfl_sync(0xffffffffu, c, 0);
+    if (c < 0) return 0;
+    __threadfence();
+    WsSlot *sl = A.ws + found;
+    const int ns = __ldcg(&sl->ns);
+    const int nwords = ns * (int)(sizeof(CoefMixed) / sizeof(int));
+    for (int i = lane; i < nwords; i += 32) ((int *)hcm[warp])[i] = __ldcg(((const int *)sl->cm) + i);
+    if (lane < ns) hjc[warp][lane] = __ldcg(&sl->jc[lane]);
+    __syncwarp();
+    ws_chunk<NDET>(M, T, hcm[warp], hjc[warp], ns, c, A.ws_gchunk,
+                   A.ws_part + ((size_t)found * A.ws_maxchunk + c) * WS_PART_PER_CHUNK);
+    __threadfence();
+    if (lane == 0) atomicAdd(&sl->done, 1);
+    __syncwarp();
+    return 1;
+}
+
 // Owner CTA (all threads): publish the round's ns candidates (coefficients cm,
 // last bins jc, in shared memory), take part in its chunks, then warp 0 waits
 // for the chunks helpers took and writes the sums over chunks, in chunk order,
@@ -567,6 +609,10 @@ __device__ void ws_owner_round(const Model &M, const Tables &T, const StepArgs &
         atomicExch(&slot->word, ws_word((w >> 40) + 1, nch, 0));
     }
     __syncthreads();
+    // every warp claims the round's chunks; warp 0 then waits for the chunks
+    // other CTAs took (GB300, 519,169 bins: letting the other warps take other
+    // rounds' chunks meanwhile was slower, 264 -> 297 ms per update, as a
+    // chain's next round then waits for its warps to come back)
     for (int guard = 0; guard < (1 << 20); guard++) {
         int c = -1;
         if (lane == 0) c = ws_claim(slot);
@@ -576,17 +622,17 @@ __device__ void ws_owner_round(const Model &M, const Tables &T, const StepArgs &
         __threadfence();
         if (lane == 0) atomicAdd(&slot->done, 1);
     }
-    if (warp == 0) {
-        if (lane == 0) {
-            for (long long it = 0; *((volatile int *)&slot->done) < nch; it++) {
-                if (it > WS_WAIT_LIMIT) {
-                    atomicOr(&A.state->status, 2);
-                    break;
-                }
-                __nanosleep(100);
+    if (warp == 0 && lane == 0) {
+        for (long long it = 0; *((volatile int *)&slot->done) < nch; it++) {
+            if (it > WS_WAIT_LIMIT) {
+                atomicOr(&A.state->status, 2);
+                break;
             }
+            __nanosleep(100);
         }
-        __syncwarp();
+    }
+    __syncthreads();
+    if (warp == 0) {
         __threadfence();
         const int sc = lane / NDET, dd = lane - sc * NDET;
         if (lane < ns * NDET) {
@@ -602,62 +648,55 @@ __device__ void ws_owner_round(const Model &M, const Tables &T, const StepArgs &
     }
 }
 
-// A CTA without a chain left: each warp claims chunks of any running chain's
+// A CTA without a chain left: each warp takes chunks of any running chain's
 // round until no chain is running.
 template <int NDET, int W>
 __device__ void ws_help(const Model &M, const Tables &T, const StepArgs &A) {
-    __shared__ CoefMixed hcm[W][4];
-    __shared__ int hjc[W][4];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nslot = A.ws_nslot;
-    const int start = (int)(((unsigned)blockIdx.x * 37u + (unsigned)warp * 11u) % (unsigned)nslot);
+    const int lane = threadIdx.x & 31;
     long long idle = 0;
     for (;;) {
         if (*((volatile int *)A.active) <= 0) break;
-        int found = -1;
-        for (int base = 0; base < nslot && found < 0; base += 32) {
-            const int j = base + lane;
-            int s = start + j;
-            if (s >= nslot) s -= nslot;
-            bool open = false;
-            if (j < nslot) {
-                const unsigned long long w = *((volatile unsigned long long *)&A.ws[s].word);
-                open = (w & 0xFFFFFull) < ((w >> 20) & 0xFFFFFull);
-            }
-            const unsigned b = __ballot_sync(0xffffffffu, open);
-            if (b) found = __shfl_sync(0xffffffffu, s, __ffs(b) - 1);
-        }
-        int c = -1;
-        if (found >= 0 && lane == 0) c = ws_claim(A.ws + found);
-        c = __shfl_sync(0xffffffffu, c, 0);
-        if (c < 0) {
-            if (++idle > WS_IDLE_LIMIT) {
-                if (lane == 0) atomicOr(&A.state->status, 2);
-                break;
-            }
-            __nanosleep(200);
+        if (ws_take_any<NDET, W>(M, T, A, -1)) {
+            idle = 0;
             continue;
         }
-        idle = 0;
-        __threadfence();
-        WsSlot *sl = A.ws + found;
-        const int ns = __ldcg(&sl->ns);
-        const int nwords = ns * (int)(sizeof(CoefMixed) / sizeof(int));
-        for (int i = lane; i < nwords; i += 32) ((int *)hcm[warp])[i] = __ldcg(((const int *)sl->cm) + i);
-        if (lane < ns) hjc[warp][lane] = __ldcg(&sl->jc[lane]);
-        __syncwarp();
-        ws_chunk<NDET>(M, T, hcm[warp], hjc[warp], ns, c, A.ws_gchunk,
-                       A.ws_part + ((size_t)found * A.ws_maxchunk + c) * WS_PART_PER_CHUNK);
-        __threadfence();
-        if (lane == 0) atomicAdd(&sl->done, 1);
-        __syncwarp();
+        if (++idle > WS_IDLE_LIMIT) {
+            if (lane == 0) atomicOr(&A.state->status, 2);
+            break;
+        }
+        __nanosleep(200);
     }
 }
 
-// ROTOK: the tiled mixed form sums tiles of 32 bins or more by rotation
-// (tile_bins_rot); without it every tile length takes the direct form, and
-// the kernel compiles one form only.
-template <int PREC, int NDET, int S, int W = S, bool ROTOK = true, bool WS = false>
+// Forms of the tiled mixed sums a kernel compiles. FORM_BOTH chooses at run
+// time: rotation (tile_bins_rot) on tiles of 32 bins or more, direct on
+// shorter ones. FORM_DIRECT and FORM_ROT compile one form only (the serving
+// kernel, which runs many analyses per launch, spilled registers with both);
+// FORM_ROT kernels run only grids with tiles of 32 bins or more.
+enum { FORM_DIRECT = 0, FORM_BOTH = 1, FORM_ROT = 2 };
+
+template <int FORM>
+__device__ __forceinline__ bool form_rot(const Model &M) {
+    if constexpr (FORM == FORM_ROT) return true;
+    else if constexpr (FORM == FORM_DIRECT) return false;
+    else return M.tlg >= 5;
+}
+
+template <int NDET, int NC, int FORM>
+__device__ __forceinline__ void tile_bins_form(const Model &M, const Tables &T, const CoefMixed *cm,
+                                               const int *jc, int nc, int g0, int gstride,
+                                               float zh[NC][NDET][2], float zl[NC][NDET][2]) {
+    if constexpr (FORM == FORM_ROT) {
+        tile_bins<NDET, NC, true>(T, M.tlg, M.np, cm, jc, nc, g0, gstride, zh, zl);
+    } else if constexpr (FORM == FORM_DIRECT) {
+        tile_bins<NDET, NC, false>(T, M.tlg, M.np, cm, jc, nc, g0, gstride, zh, zl);
+    } else {
+        if (M.tlg >= 5) tile_bins<NDET, NC, true>(T, M.tlg, M.np, cm, jc, nc, g0, gstride, zh, zl);
+        else tile_bins<NDET, NC, false>(T, M.tlg, M.np, cm, jc, nc, g0, gstride, zh, zl);
+    }
+}
+
+template <int PREC, int NDET, int S, int W = S, int FORM = FORM_BOTH, bool WS = false>
 __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, const int chain) {
     __shared__ Coef coef[S];
     __shared__ CoefMixed cm[S];
@@ -771,7 +810,7 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
             // mixed, every warp on every candidate of the round: the tiled form
             // shares out the tile groups (two candidates per pass on one table
             // load), the per-bin form strides the bins
-            if (warp < ns) coef_to_mixed_warp(coef[warp], M.n_det, M.df, &cm[warp], nullptr, ROTOK && M.tlg >= 5);
+            if (warp < ns) coef_to_mixed_warp(coef[warp], M.n_det, M.df, &cm[warp], nullptr, form_rot<FORM>(M));
             if (lane == 0 && warp < ns) jc[warp] = coef[warp].jcut;
             __syncthreads();
             if (WS) {
@@ -782,10 +821,7 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
                 for (int c0 = 0; c0 < ns; c0 += 2) {
                     float zh[2][NDET][2], zl[2][NDET][2];
                     const int nc = ns - c0 < 2 ? ns - c0 : 2;
-                    if (ROTOK && M.tlg >= 5)
-                        tile_bins<NDET, 2, true>(T, M.tlg, M.np, cm + c0, jc + c0, nc, warp, W, zh, zl);
-                    else
-                        tile_bins<NDET, 2, false>(T, M.tlg, M.np, cm + c0, jc + c0, nc, warp, W, zh, zl);
+                    tile_bins_form<NDET, 2, FORM>(M, T, cm + c0, jc + c0, nc, warp, W, zh, zl);
 #pragma unroll
                     for (int sc = 0; sc < 2; sc++)
 #pragma unroll
@@ -876,14 +912,11 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
                     v += coef[warp].gre[dd] * ZR - coef[warp].gim[dd] * ZI;
                 }
             } else if (M.tlg) {
-                coef_to_mixed_warp(coef[warp], M.n_det, M.df, &cm[warp], nullptr, ROTOK && M.tlg >= 5);
+                coef_to_mixed_warp(coef[warp], M.n_det, M.df, &cm[warp], nullptr, form_rot<FORM>(M));
                 if (lane == 0) jc[warp] = coef[warp].jcut;
                 __syncwarp();
                 float zh[1][NDET][2], zl[1][NDET][2];
-                if (ROTOK && M.tlg >= 5)
-                    tile_bins<NDET, 1, true>(T, M.tlg, M.np, &cm[warp], &jc[warp], 1, 0, 1, zh, zl);
-                else
-                    tile_bins<NDET, 1, false>(T, M.tlg, M.np, &cm[warp], &jc[warp], 1, 0, 1, zh, zl);
+                tile_bins_form<NDET, 1, FORM>(M, T, &cm[warp], &jc[warp], 1, 0, 1, zh, zl);
 #pragma unroll
                 for (int dd = 0; dd < NDET; dd++) {
                     warp_sum_df(zh[0][dd][0], zl[0][dd][0]);
@@ -893,7 +926,7 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
                     v += coef[warp].gre[dd] * ZR - coef[warp].gim[dd] * ZI;
                 }
             } else {
-                coef_to_mixed_warp(coef[warp], M.n_det, M.df, &cm[warp], nullptr, ROTOK && M.tlg >= 5);
+                coef_to_mixed_warp(coef[warp], M.n_det, M.df, &cm[warp], nullptr, form_rot<FORM>(M));
                 __syncwarp();
                 double zr[NDET], zi[NDET];
                 bins_mixed<NDET>(T, M.N, cm[warp], coef[warp].jcut, lane, 32, zr, zi);
@@ -954,7 +987,7 @@ __global__ void __launch_bounds__(256, SLICE_MIN_BLOCKS(1, 8)) k_slice_ws(Model 
         const int chain = s_chain;
         __syncthreads();
         if (chain >= A.k) break;
-        slice_body<1, NDET, 4, 8, true, true>(M, T, A, chain);
+        slice_body<1, NDET, 4, 8, FORM_ROT, true>(M, T, A, chain);
         __syncthreads();
     }
     ws_help<NDET, 8>(M, T, A);
@@ -1004,26 +1037,35 @@ cudaError_t slice_launch(const Model &M, const Tables &T, int slots, const StepA
     return cudaGetLastError();
 }
 
-// Many analyses in one launch (serving): the tiled grids take the direct form
-// at every tile length. Compiling the rotation form too spilled registers, and
-// the serving stream slowed from p50 4.0 to 5.8 s.
-template <int PREC, int NDET, int S>
+// Many analyses in one launch (serving), one form of the tiled mixed sums per
+// kernel: the direct form for every analysis (FP64, per-bin and short-tile
+// grids) or the rotation form for mixed grids with tiles of 32 bins or more.
+// A kernel with both forms spilled registers (serving stream p50 4.0 -> 5.8 s).
+template <int PREC, int NDET, int S, int FORM>
 __global__ void __launch_bounds__(S * 32, SLICE_MIN_BLOCKS(PREC, S)) k_slice_multi(const Desc *D, const int2 *map) {
     __shared__ Desc d;
     const int2 ac = map[blockIdx.x];
     load_desc(D + ac.x, d);
-    slice_body<PREC, NDET, S, S, false>(d.M, d.T, d.A, ac.y);
+    slice_body<PREC, NDET, S, S, FORM>(d.M, d.T, d.A, ac.y);
+}
+
+template <int PREC, int NDET, int FORM>
+cudaError_t slice_multi_launch_form(const Desc *D, const int2 *map, int nblocks, int slots, cudaStream_t s) {
+    switch (slots) {
+        case 1: k_slice_multi<PREC, NDET, 1, FORM><<<nblocks, 32, 0, s>>>(D, map); break;
+        case 2: k_slice_multi<PREC, NDET, 2, FORM><<<nblocks, 64, 0, s>>>(D, map); break;
+        case 4: k_slice_multi<PREC, NDET, 4, FORM><<<nblocks, 128, 0, s>>>(D, map); break;
+        default: k_slice_multi<PREC, NDET, 8, FORM><<<nblocks, 256, 0, s>>>(D, map); break;
+    }
+    return cudaGetLastError();
 }
 
 template <int PREC, int NDET>
-cudaError_t slice_multi_launch(const Desc *D, const int2 *map, int nblocks, int slots, cudaStream_t s) {
-    switch (slots) {
-        case 1: k_slice_multi<PREC, NDET, 1><<<nblocks, 32, 0, s>>>(D, map); break;
-        case 2: k_slice_multi<PREC, NDET, 2><<<nblocks, 64, 0, s>>>(D, map); break;
-        case 4: k_slice_multi<PREC, NDET, 4><<<nblocks, 128, 0, s>>>(D, map); break;
-        default: k_slice_multi<PREC, NDET, 8><<<nblocks, 256, 0, s>>>(D, map); break;
+cudaError_t slice_multi_launch(const Desc *D, const int2 *map, int nblocks, int slots, int rot, cudaStream_t s) {
+    if constexpr (PREC == 1) {
+        if (rot) return slice_multi_launch_form<PREC, NDET, FORM_ROT>(D, map, nblocks, slots, s);
     }
-    return cudaGetLastError();
+    return slice_multi_launch_form<PREC, NDET, FORM_DIRECT>(D, map, nblocks, slots, s);
 }
 
 // Explicit instantiation of the launchers of one (precision, detectors) pair.
@@ -1033,6 +1075,6 @@ cudaError_t slice_multi_launch(const Desc *D, const int2 *map, int nblocks, int 
                                            double *, RunState *, cudaStream_t);                     \
     template cudaError_t slice_launch<P, D>(const Model &, const Tables &, int, const StepArgs &,     \
                                             cudaStream_t);                                          \
-    template cudaError_t slice_multi_launch<P, D>(const Desc *, const int2 *, int, int, cudaStream_t);
+    template cudaError_t slice_multi_launch<P, D>(const Desc *, const int2 *, int, int, int, cudaStream_t);
 
 }  // namespace gwns

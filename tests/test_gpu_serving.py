@@ -10,10 +10,12 @@ import oracle
 pytestmark = pytest.mark.gpu
 
 
-def _analysis(seed_offset, N=1200, n_live=80, n_det=3, df=None, k=None, snr=None):
+def _analysis(seed_offset, N=1200, n_live=80, n_det=3, df=None, k=None, snr=None, dl_lo=None):
     w = gi.workload("c1", n_live=n_live, k=k if k else n_live // 2)
     if snr is not None:
         w.snr = snr
+    if dl_lo is not None:
+        w.lo[gi.P_DL] = dl_lo
     w.N = N
     w.n_det = n_det
     if df is not None:
@@ -166,37 +168,32 @@ def test_cancel(gw):
 
 
 def test_footprint_counts_the_dead_list_growth(gw):
-    """An analysis that runs past 64 n dead points (8 live points, one deleted
-    per iteration, a loud SNR-40 injection and a stopping tolerance it only
-    meets once the remaining evidence underflows) doubles its dead list; the
-    server adds the growth to its footprint and to the memory in use, so a
-    request that fitted beside the analysis' admission footprint waits until
-    the analysis is done."""
-    long_req, dim = _analysis(50, n_live=8, k=1, snr=40.0)
-    long_req = dict(long_req, dlogz_stop=1e-300)
+    """An analysis that runs past 64 n dead points doubles its dead list (8
+    live points, 4 deleted per iteration, a negative stopping tolerance that is
+    never met, and the server's cap of 200 iterations: 800 dead points, the
+    list grows at iteration 129). The server adds the growth to the analysis'
+    footprint and to the memory in use, so a request that fitted beside the
+    analysis' admission footprint waits until the analysis is done."""
+    long_req, dim = _analysis(50, n_live=8, k=4)
+    long_req = dict(long_req, dlogz_stop=-1.0)
     other, _ = _analysis(51, n_live=8, k=4)
     with gw.Server(precision=1) as probe:
         fa = probe.poll(probe.submit(**long_req))["footprint"]
         fb = probe.poll(probe.submit(**other))["footprint"]
     dead64 = 64 * 8 * (dim + 3) * 8          # the initial dead list: u, log L, log w, n_live
-    with gw.Server(precision=1, mem_budget=fa + fb + dead64 // 2, max_iter=4000) as srv:
+    with gw.Server(precision=1, mem_budget=fa + fb + dead64 // 2, max_iter=200) as srv:
         ra = srv.submit(**long_req)
-        grown = False
-        for _ in range(4000):
+        for it in range(128):
             srv.tick()
             st = srv.poll(ra)
-            if st["footprint"] > fa:
-                grown = True
-                break
-            if st["state"] != gw.NS_REQ_RUNNING:
-                break
-        assert grown, st
+            assert st["state"] == gw.NS_REQ_RUNNING and st["footprint"] == fa, (it, st)
+        srv.tick()                           # iteration 129 needs room for 516 dead points
+        st = srv.poll(ra)
         assert st["state"] == gw.NS_REQ_RUNNING and st["footprint"] == fa + dead64
         rb = srv.submit(**other)
         srv.tick()
-        if srv.poll(ra)["state"] == gw.NS_REQ_RUNNING:
-            assert srv.poll(rb)["state"] == gw.NS_REQ_PENDING
+        assert srv.poll(rb)["state"] == gw.NS_REQ_PENDING
         srv.run_until_idle()
         sa, sb = srv.poll(ra), srv.poll(rb)
-        assert sa["state"] == gw.NS_REQ_DONE and sb["state"] == gw.NS_REQ_DONE
-        assert sb["t_admit"] >= sa["t_done"]
+        assert sa["state"] == gw.NS_REQ_DONE and sa["iterations"] == 200
+        assert sb["state"] == gw.NS_REQ_DONE and sb["t_admit"] >= sa["t_done"]
