@@ -62,9 +62,11 @@ int choose_warps(const ns_ctx *c) {
     if (c->precision == NS_FP64) return bins > 32768 ? 2 : 1;
     // the rotation form (tiles of 32 bins or more) prefetches its loads and
     // needs fewer warps per point (GB300, 519,169 bins in 128-bin tiles: 8 / 4 /
-    // 2 warps give 1.50 / 1.59 / 1.53 M evals/s; 64,897 bins in 32-bin tiles:
-    // 4 / 2 warps give 35.8 / 40.8 M evals/s)
-    if (c->M.tlg >= 5) return bins > 262144 ? 4 : 2;
+    // 2 warps give 1.50 / 1.59 / 1.53 M evals/s). Up to 262,144 bins the batched
+    // kernel puts 4 max(1, W/2) points in a CTA and one warp on each point's bins:
+    // 64,897 bins in 32-bin tiles, 1 / 2 / 4 / 8 warps give 65.6 / 65.7 / 68.5 /
+    // 60.7 M evals/s
+    if (c->M.tlg >= 5) return 4;
     return bins > 16384 ? 8 : (bins > 2048 ? 4 : 2);
 }
 

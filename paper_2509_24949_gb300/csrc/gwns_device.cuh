@@ -813,14 +813,16 @@ __device__ __forceinline__ void tile_one(const float4 *w4, size_t dstride, int l
 #pragma unroll
         for (int r = 0; r < 4; r++) {
             const int i = q + r;
-            const float x = (float)(i - half), x2 = x * x;
+            // C_1h x as an error-free product p + e; the rest, C_1l x + C_2 x^2 +
+            // ... + C_TK x^TK, by Horner's rule down to the C_1 low part
+            const float x = (float)(i - half);
             const float p = k.c1h * x;
-            float e = fmaf(k.c1h, x, -p);
-            e = fmaf(k.c1l, x, e);
+            const float e = fmaf(k.c1h, x, -p);
             float hq = k.ck[TK - 2];
 #pragma unroll
             for (int j = TK - 3; j >= 0; j--) hq = fmaf(hq, x, k.ck[j]);
-            const float sm = fmaf(hq, x2, e);
+            hq = fmaf(hq, x, k.c1l);
+            const float sm = fmaf(hq, x, e);
             const float P = p - rintf(p);
             float sv, cv;
             __sincosf(fmaf(P + sm, TWO_PI_F, fmaf(x, k.dt0, k.aa0)), &sv, &cv);
@@ -967,17 +969,17 @@ __device__ __forceinline__ void tile_bins_direct(const Tables &T, int lg, int np
 #pragma unroll
             for (int r = 0; r < 4; r++) {
                 const int i = q + r;
-                const float x = (float)(i - half), x2 = x * x;
+                const float x = (float)(i - half);
 #pragma unroll
                 for (int c = 0; c < NC; c++) {
                     if (i >= cnt[c]) continue;
                     const float p = c1h[c] * x;
-                    float e = fmaf(c1h[c], x, -p);
-                    e = fmaf(c1l[c], x, e);
+                    const float e = fmaf(c1h[c], x, -p);
                     float hq = ck[c][TK - 2];
 #pragma unroll
                     for (int k = TK - 3; k >= 0; k--) hq = fmaf(hq, x, ck[c][k]);
-                    const float sm = fmaf(hq, x2, e);
+                    hq = fmaf(hq, x, c1l[c]);
+                    const float sm = fmaf(hq, x, e);
                     const float P = p - rintf(p);
 #pragma unroll
                     for (int d = 0; d < NDET; d++) {
@@ -1129,6 +1131,39 @@ __device__ __forceinline__ void warp_sum_df(float &h, float &l) {
         h = s;
         l = l + ol + e;
     }
+}
+
+// Warp sums of V <= 16 double-float values at once (a transposing butterfly):
+// at each of the first four steps a lane hands half of the values it carries
+// to its partner and adds the half it keeps, so that 8 + 4 + 2 + 1 + 1
+// double-float adds replace 5 V. On return lanes 2i and 2i + 1 hold the sum of
+// value i in (rh, rl).
+template <int V>
+__device__ __forceinline__ void warp_sum_df_many(float (&h)[16], float (&l)[16], float &rh, float &rl) {
+    static_assert(V <= 16, "at most 16 values");
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int i = V; i < 16; i++) { h[i] = 0.f; l[i] = 0.f; }
+#pragma unroll
+    for (int step = 0; step < 4; step++) {
+        const int half = 8 >> step, o = 16 >> step;
+        const bool upper = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < half; i++) {
+            const float kh = upper ? h[i + half] : h[i], kl = upper ? l[i + half] : l[i];
+            const float sh = upper ? h[i] : h[i + half], sl = upper ? l[i] : l[i + half];
+            const float oh = __shfl_xor_sync(0xffffffffu, sh, o), ol = __shfl_xor_sync(0xffffffffu, sl, o);
+            float s, e;
+            two_sum(kh, oh, s, e);
+            h[i] = s;
+            l[i] = kl + ol + e;
+        }
+    }
+    const float oh = __shfl_xor_sync(0xffffffffu, h[0], 1), ol = __shfl_xor_sync(0xffffffffu, l[0], 1);
+    float s, e;
+    two_sum(h[0], oh, s, e);
+    rh = s;
+    rl = l[0] + ol + e;
 }
 
 // ------------------------------------------------------- relative binning

@@ -15,7 +15,6 @@
 #include <cstring>
 #include <deque>
 #include <map>
-#include <tuple>
 #include <utility>
 #include <new>
 #include <unordered_map>
@@ -73,10 +72,6 @@ struct ns_server {
     ns_server_options o;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    // the rotation-form slice launch runs on a second stream beside the
-    // direct-form one, so that the two launches' last chains overlap
-    cudaStream_t side = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     uint64_t next_id = 1;
     size_t budget = 0, used = 0;
     long long chains = 0;          // k of the running analyses
@@ -180,11 +175,12 @@ int iterate_all(ns_server *s) {
     const int na = (int)s->running.size();
     if (na == 0) return NS_OK;
     std::vector<Desc> desc(na);
-    // slice-update launches grouped by (detector count, warps per chain, form):
-    // every analysis always runs at its own width and form, whatever the mix;
-    // mixed grids with tiles of 32 bins or more take the rotation form, as in a
-    // single context
-    std::map<std::tuple<int, int, int>, std::vector<int2>> groups;
+    // slice-update launches grouped by (detector count, warps per chain): every
+    // analysis always runs at its own width, whatever the mix. Tiled mixed grids
+    // take the direct form at every tile length (GB300, the 64-analysis stream:
+    // p50 / p99 4.55 / 7.7 s; with the rotation form for tiles of 32 bins or more
+    // in a kernel of its own, 5.8 / 9.2 s, and 6.3 / 10.0 s on a second stream)
+    std::map<std::pair<int, int>, std::vector<int2>> groups;
     for (int a = 0; a < na; a++) {
         Request &r = s->reqs[s->running[a]];
         ns_ctx *c = r.ctx;
@@ -205,8 +201,7 @@ int iterate_all(ns_server *s) {
         desc[a].M = c->M;
         desc[a].T = c->T;
         desc[a].A = step_args(c, k);
-        const int rot = (c->precision == NS_MIXED && c->M.model == gwns::M_GW && !c->M.rb && c->M.tlg >= 5) ? 1 : 0;
-        std::vector<int2> &g = groups[std::make_tuple(c->M.n_det, slots_alloc(c), rot)];
+        std::vector<int2> &g = groups[std::make_pair(c->M.n_det, slots_alloc(c))];
         for (int ch = 0; ch < k; ch++) g.push_back(make_int2(a, ch));
     }
     if (na > s->desc_cap) {
@@ -229,21 +224,10 @@ int iterate_all(ns_server *s) {
     for (auto &kv : groups) {
         const std::vector<int2> &g = kv.second;
         SCK(cudaMemcpyAsync(s->d_map + off, g.data(), sizeof(int2) * g.size(), cudaMemcpyHostToDevice, s->stream));
+        SCK(gwns::launch_slice_multi(s->d_desc, s->d_map + off, (int)g.size(), s->o.precision, kv.first.first,
+                                     kv.first.second, 0, s->stream));
         off += g.size();
     }
-    SCK(cudaEventRecord(s->ev_fork, s->stream));
-    SCK(cudaStreamWaitEvent(s->side, s->ev_fork, 0));
-    off = 0;
-    for (auto &kv : groups) {
-        const std::vector<int2> &g = kv.second;
-        const int rot = std::get<2>(kv.first);
-        SCK(gwns::launch_slice_multi(s->d_desc, s->d_map + off, (int)g.size(), s->o.precision,
-                                     std::get<0>(kv.first), std::get<1>(kv.first), rot,
-                                     rot ? s->side : s->stream));
-        off += g.size();
-    }
-    SCK(cudaEventRecord(s->ev_join, s->side));
-    SCK(cudaStreamWaitEvent(s->stream, s->ev_join, 0));
     SCK(gwns::launch_iteration_multi_tail(s->d_desc, na, s->stream));
     for (int a = 0; a < na; a++) {
         ns_ctx *c = s->reqs[s->running[a]].ctx;
@@ -281,12 +265,6 @@ int ns_server_create(ns_server **out, const ns_server_options *o) {
     } else {
         if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) { delete s; return NS_ERR_CUDA; }
         s->own_stream = true;
-    }
-    if (cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming) != cudaSuccess) {
-        ns_server_free(s);
-        return NS_ERR_CUDA;
     }
     if (o->mem_budget) {
         s->budget = o->mem_budget;
@@ -442,12 +420,6 @@ void ns_server_free(ns_server *s) {
     for (auto &kv : s->reqs) release(s, kv.second);
     if (s->d_desc) cudaFree(s->d_desc);
     if (s->d_map) cudaFree(s->d_map);
-    if (s->side) {
-        cudaStreamSynchronize(s->side);
-        cudaStreamDestroy(s->side);
-    }
-    if (s->ev_fork) cudaEventDestroy(s->ev_fork);
-    if (s->ev_join) cudaEventDestroy(s->ev_join);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
     delete s;
 }

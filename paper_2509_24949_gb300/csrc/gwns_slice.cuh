@@ -145,10 +145,97 @@ __global__ void __launch_bounds__(W * 32) k_eval(Model M, Tables T, const double
     }
 }
 
+// Batched likelihood, mixed precision, unit-cube points on grids of up to
+// 262,144 bins (where the per-point FP64 work weighs most): 4 max(1, W/2)
+// points per CTA. The coefficient stage runs as its two halves on two warps per
+// group of four points (mass and phase on one, sky and detectors on the other,
+// independent FP64 chains on two SM sub-partitions), joined by the first; then
+// each point's bins are summed by one warp (points dealt to the warps in turn),
+// reduced in double-float, and only the final log L is formed in FP64. GB300,
+// 8192 prior draws of the 64,897-bin workload: the previous kernel (coefficients
+// of four points on one warp, the other warp waiting, every point's tile groups
+// shared by both warps and reduced in FP64) reached 5.75e7 evals/s.
+template <int NDET, int W>
+__global__ void __launch_bounds__(W * 32) k_eval_batch(Model M, Tables T, const double *in, int m, double *logl,
+                                                       RunState *st) {
+    constexpr int NG = W >= 2 ? W / 2 : 1;
+    constexpr int PPC = 4 * NG;
+    __shared__ Coef coef[PPC];
+    __shared__ CoefMixed cm[PPC];
+    __shared__ double pt[PPC][MAXD];
+    const int i0 = blockIdx.x * PPC;
+    if (i0 >= m) return;
+    const int np = m - i0 < PPC ? m - i0 : PPC;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int d = M.dim;
+    for (int t = threadIdx.x; t < np * d; t += W * 32) pt[t / d][t % d] = in[(size_t)i0 * d + t];
+    __syncthreads();
+    const int grp = W >= 2 ? warp >> 1 : warp;
+    const bool lead = W >= 2 ? (warp & 1) == 0 : true;
+    const int cnt = (grp < NG && 4 * grp < np) ? min(4, np - 4 * grp) : 0;
+    if (cnt > 0) point_coef_group(M, T, pt[4 * grp], MAXD, &coef[4 * grp], cnt, 0, W >= 2 ? 1 + (warp & 1) : 0);
+    __syncthreads();
+    if (cnt > 0 && lead) {
+        if (W >= 2) point_coef_join(M, T, &coef[4 * grp], cnt);
+        __syncwarp();
+        for (int p = 4 * grp; p < 4 * grp + cnt; p++)
+            coef_to_mixed_warp(coef[p], M.n_det, M.df, &cm[p], nullptr, M.tlg >= 5);
+    }
+    __syncthreads();
+    for (int p = warp; p < np; p += W) {
+        double ZR[NDET], ZI[NDET];
+        if (M.tlg) {
+            float zh[1][NDET][2], zl[1][NDET][2];
+            if (M.tlg >= 5)
+                tile_bins<NDET, 1, true, true>(T, M.tlg, M.np, &cm[p], &coef[p].jcut, 1, 0, 1, zh, zl);
+            else
+                tile_bins<NDET, 1, false>(T, M.tlg, M.np, &cm[p], &coef[p].jcut, 1, 0, 1, zh, zl);
+#pragma unroll
+            for (int dd = 0; dd < NDET; dd++) {
+                warp_sum_df(zh[0][dd][0], zl[0][dd][0]);
+                warp_sum_df(zh[0][dd][1], zl[0][dd][1]);
+                ZR[dd] = (double)zh[0][dd][0] + (double)zl[0][dd][0];
+                ZI[dd] = (double)zh[0][dd][1] + (double)zl[0][dd][1];
+            }
+        } else {
+            double zr[NDET], zi[NDET];
+            bins_mixed<NDET>(T, M.N, cm[p], coef[p].jcut, lane, 32, zr, zi);
+#pragma unroll
+            for (int dd = 0; dd < NDET; dd++) {
+                ZR[dd] = warp_sum(zr[dd]);
+                ZI[dd] = warp_sum(zi[dd]);
+            }
+        }
+        if (lane == 0) {
+            double v = -0.5 * coef[p].hh;
+#pragma unroll
+            for (int dd = 0; dd < NDET; dd++) v += coef[p].gre[dd] * ZR[dd] - coef[p].gim[dd] * ZI[dd];
+            logl[i0 + p] = v;
+            if (st) {
+                atomicAdd(&st->eval_points, 1ull);
+                atomicAdd(&st->eval_point_bins, (unsigned long long)(coef[p].jcut + 1));
+            }
+        }
+    }
+}
+
 template <int PREC, int NDET>
 cudaError_t eval_launch(const Model &M, const Tables &T, int warps, const double *in, int th, int m,
                         double *logl, RunState *st, cudaStream_t s) {
     const int nbins = M.rb ? T.rb.nb : M.N;
+    if constexpr (PREC == 1) {
+        if (M.model == M_GW && !th && !M.rb && nbins <= 262144) {
+            const int ppc = 4 * (warps >= 2 ? warps / 2 : 1);
+            const int gb = (m + ppc - 1) / ppc;
+            switch (warps) {
+                case 1: k_eval_batch<NDET, 1><<<gb, 32, 0, s>>>(M, T, in, m, logl, st); break;
+                case 2: k_eval_batch<NDET, 2><<<gb, 64, 0, s>>>(M, T, in, m, logl, st); break;
+                case 4: k_eval_batch<NDET, 4><<<gb, 128, 0, s>>>(M, T, in, m, logl, st); break;
+                default: k_eval_batch<NDET, 8><<<gb, 256, 0, s>>>(M, T, in, m, logl, st); break;
+            }
+            return cudaGetLastError();
+        }
+    }
     const int ppc = (PREC == 1 && M.model == M_GW && !th && nbins <= 262144) ? EVAL_PPC : 1;
     const int g = (m + ppc - 1) / ppc;
     switch (warps) {
@@ -524,17 +611,22 @@ __device__ __forceinline__ void ws_chunk(const Model &M, const Tables &T, const 
         float zh[2][NDET][2], zl[2][NDET][2];
         const int nc = ns - c0 < 2 ? ns - c0 : 2;
         tile_bins<NDET, 2, true>(T, M.tlg, M.np, cm + c0, jc + c0, nc, g0, 1, zh, zl, g1);
+        // value v = (candidate, detector, re/im) of the pair, summed over the warp at once
+        float vh[16], vl[16];
 #pragma unroll
         for (int sc = 0; sc < 2; sc++)
 #pragma unroll
-            for (int dd = 0; dd < NDET; dd++) {
-                warp_sum_df(zh[sc][dd][0], zl[sc][dd][0]);
-                warp_sum_df(zh[sc][dd][1], zl[sc][dd][1]);
-                if (lane == 0 && c0 + sc < ns) {
-                    out[((c0 + sc) * MAXDET + dd) * 2] = (double)zh[sc][dd][0] + (double)zl[sc][dd][0];
-                    out[((c0 + sc) * MAXDET + dd) * 2 + 1] = (double)zh[sc][dd][1] + (double)zl[sc][dd][1];
+            for (int dd = 0; dd < NDET; dd++)
+#pragma unroll
+                for (int ri = 0; ri < 2; ri++) {
+                    vh[(sc * NDET + dd) * 2 + ri] = zh[sc][dd][ri];
+                    vl[(sc * NDET + dd) * 2 + ri] = zl[sc][dd][ri];
                 }
-            }
+        float rh, rl;
+        warp_sum_df_many<4 * NDET>(vh, vl, rh, rl);
+        const int v = lane >> 1, sc = v / (2 * NDET), dd = (v >> 1) % NDET, ri = v & 1;
+        if ((lane & 1) == 0 && v < 4 * NDET && c0 + sc < ns)
+            out[((c0 + sc) * MAXDET + dd) * 2 + ri] = (double)rh + (double)rl;
     }
 }
 
@@ -818,10 +910,18 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
                 // warps and by helper CTAs, summed in chunk order into part[0]
                 ws_owner_round<NDET, W>(M, T, A, cm, jc, ns, part[0]);
             } else if (M.tlg) {
+                // the (candidate pair, tile group) items of the round are dealt out
+                // to the warps in turn, pair after pair, so that every warp has
+                // work when a candidate spans fewer groups than there are warps
+                int off = 0;
                 for (int c0 = 0; c0 < ns; c0 += 2) {
                     float zh[2][NDET][2], zl[2][NDET][2];
                     const int nc = ns - c0 < 2 ? ns - c0 : 2;
-                    tile_bins_form<NDET, 2, FORM>(M, T, cm + c0, jc + c0, nc, warp, W, zh, zl);
+                    const int jm = nc == 2 ? max(jc[c0], jc[c0 + 1]) : jc[c0];
+                    const int ng = jm < 0 ? 0 : (jm >> (M.tlg + 5)) + 1;
+                    const int g0 = ((warp - off) % W + W) % W;
+                    off += ng;
+                    tile_bins_form<NDET, 2, FORM>(M, T, cm + c0, jc + c0, nc, g0, W, zh, zl);
 #pragma unroll
                     for (int sc = 0; sc < 2; sc++)
 #pragma unroll
