@@ -17,6 +17,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "gwns_tables.cuh"
+
 namespace gwns {
 
 constexpr int NPARAM = 11;
@@ -156,6 +158,66 @@ __device__ __forceinline__ double u01(uint32_t a, uint32_t b) {
     return ((double)x + 0.5) * 2.220446049250313e-16;
 }
 
+// ------------------------------------------- FP64 exp and log (table-driven)
+// The per-point coefficient stage is FP64 and, on grids of a few thousand bins
+// per evaluation, its instruction count binds; these two functions follow
+// Tang's table-driven method (ACM TOMS 15 (1989) 144; 16 (1990) 378): reduce
+// against a table point, then a short polynomial. Tables: gwns_tables.cuh.
+
+// exp(x) = 2^m 2^(j/64) (1 + p(r)) with x = (64 m + j) ln2/64 + r, |r| <= ln2/128,
+// p the degree-5 Taylor polynomial of e^r - 1 (truncation below 4e-17) and
+// 2^(j/64) as hi + lo; within 1 ulp for |x| < 700 with a normal result (the
+// coefficient stage's arguments lie in [-60, 10]).
+__device__ __forceinline__ double exp_tab(double x) {
+    const double shift = 6755399441055744.0;                     // 1.5 2^52
+    const double kk = fma(x, 0x1.71547652b82fep+6, shift);       // 64 / ln 2
+    const int ki = __double2loint(kk);
+    const double k = kk - shift;
+    double r = fma(-k, 0x1.62e42fef00000p-7, x);                 // ln2/64, 33-bit head
+    r = fma(-k, 0x1.473de6af278edp-40, r);                       // and its tail
+    const int j = ki & 63, m = ki >> 6;
+    double q = fma(r, 1.0 / 120.0, 1.0 / 24.0);
+    q = fma(q, r, 1.0 / 6.0);
+    q = fma(q, r, 0.5);
+    const double p = fma(r * r, q, r);
+    const double th = __ldg(EXP_T_HI + j), tl = __ldg(EXP_T_LO + j);
+    const double res = th + fma(th, p, tl);
+    return __hiloint2double(__double2hiint(res) + (m << 20), __double2loint(res));
+}
+
+// ln x = e ln 2 - ln c + ln(1 + r) with x = 2^e m, m in [1, 2), c the table's
+// double nearest 1/(1 + (j + 1/2)/128) for the top 7 fraction bits j of m,
+// r = m c - 1 (|r| < 0.004, one rounding) and ln(1 + r) by its degree-6 Taylor
+// polynomial (truncation below 1e-17); -ln c and ln 2 as hi + lo. Within 1 ulp
+// of max(1, |ln x|) for positive normal x.
+__device__ __forceinline__ double log_tab(double x) {
+    const int hi = __double2hiint(x), lo = __double2loint(x);
+    const int e = ((hi >> 20) & 0x7ff) - 1023;
+    const int j = (hi >> 13) & 127;
+    const double m = __hiloint2double((hi & 0x000fffff) | 0x3ff00000, lo);
+    const double r = fma(m, __ldg(LOG_INV_C + j), -1.0);
+    double q = fma(r, -1.0 / 6.0, 0.2);
+    q = fma(q, r, -0.25);
+    q = fma(q, r, 1.0 / 3.0);
+    q = fma(q, r, -0.5);
+    const double p = fma(r * r, q, r);
+    const double ed = (double)e;
+    const double h = fma(ed, 0x1.62e42fef00000p-1, __ldg(LOG_NLN_HI + j));   // ln 2, 33-bit head
+    const double l = fma(ed, 0x1.473de6af278edp-34, __ldg(LOG_NLN_LO + j)) + p;
+    return h + l;
+}
+
+// 1 / x for 1 <= x <= 2 (the mass-ratio factor 1 / (1 + q)): an FP32 reciprocal
+// refined by two Newton steps y <- y + y (1 - x y) (error 2^-23 -> 2^-92, then
+// the final rounding).
+__device__ __forceinline__ double recip_12(double x) {
+    double y = (double)__frcp_rn((float)x);
+    y = fma(y, fma(-x, y, 1.0), y);
+    return fma(y, fma(-x, y, 1.0), y);
+}
+
+__device__ __forceinline__ void sincos_bf(double x, double &s, double &c);
+
 // ------------------------------------------------------------ prior transform
 __device__ __forceinline__ double prior_one(const Model &M, int p, double u) {
     double lo = M.lo[p], hi = M.hi[p];
@@ -232,8 +294,15 @@ __device__ inline void point_coef_group(const Model &M, const Tables &T, const d
         int i = 0;
 #pragma unroll
         for (int p = 0; p < NPARAM; p++) {
+            // each half transforms only the parameters it uses (mass and phase:
+            // chirp mass, q, spins, distance, phi_c; sky and detectors: cos i,
+            // psi, t_c, RA, sin dec)
+            const bool mass_p = p == P_MC || p == P_Q || p == P_CHI1 || p == P_CHI2 || p == P_DL || p == P_PHIC;
             if (M.kind[p] == K_FIXED) {
                 th[p] = M.lo[p];
+            } else if ((half == 1 && !mass_p) || (half == 2 && mass_p)) {
+                th[p] = 0.0;
+                i++;
             } else if (M.kind[p] == K_UNIFORM) {
                 th[p] = fma(M.pspan[p], u[i++], M.pbase[p]);
             } else {
@@ -249,14 +318,14 @@ __device__ inline void point_coef_group(const Model &M, const Tables &T, const d
     int jcut = -1;
     if (half != 2) {
         const double q = th[P_Q];
-        const double r1q = 1.0 / (1.0 + q);
+        const double r1q = recip_12(1.0 + q);
         const double eta = q * r1q * r1q;               // m1 m2 / M^2
         const double delta = (1.0 - q) * r1q;           // (m1 - m2)/M, m1 >= m2
         const double chis = 0.5 * (th[P_CHI1] + th[P_CHI2]);
         const double chia = 0.5 * (th[P_CHI1] - th[P_CHI2]);
         const double tmc = th[P_MC] * TSUN;
         // packed log: sub-lane 0 ln(eta), 1 ln(T_Mc), others ln(D_L) (or of D_L^3)
-        const double lg = log(sl == 0 ? eta : (sl == 1 ? tmc : dl_arg));
+        const double lg = log_tab(sl == 0 ? eta : (sl == 1 ? tmc : dl_arg));
         const double ln_eta = __shfl_sync(FULL, lg, 0, 8);
         const double ln_tmc = __shfl_sync(FULL, lg, 1, 8);
         const double ln_dlx = __shfl_sync(FULL, lg, 2, 8);
@@ -271,7 +340,7 @@ __device__ inline void point_coef_group(const Model &M, const Tables &T, const d
                             : sl == 2 ? -ln_x
                             : sl == 3 ? -3.7534179752515073 - ln_eta
                             : -33.81250354619071 + (5.0 / 6.0) * ln_tmc - ln_dl;
-        const double ex = exp(ex_arg);
+        const double ex = exp_tab(ex_arg);
         const double a = __shfl_sync(FULL, ex, 0, 8);
         const double ia = __shfl_sync(FULL, ex, 1, 8);
         const double inv_pitm = __shfl_sync(FULL, ex, 2, 8);
@@ -321,7 +390,7 @@ __device__ inline void point_coef_group(const Model &M, const Tables &T, const d
     const double ci = th[P_COSI];
     // packed sincos: sub-lane 0 ra, others psi
     double sn, cs;
-    sincos(sl == 0 ? th[P_RA] : th[P_PSI], &sn, &cs);
+    sincos_bf(sl == 0 ? th[P_RA] : th[P_PSI], sn, cs);
     const double sa = __shfl_sync(FULL, sn, 0, 8), ca = __shfl_sync(FULL, cs, 0, 8);
     const double sp = __shfl_sync(FULL, sn, 1, 8), cp = __shfl_sync(FULL, cs, 1, 8);
     double hh_part = 0.0, tau = 0.0;
