@@ -498,11 +498,20 @@ __device__ __forceinline__ void split_df(double x, float &h, float &l) {
 __device__ __forceinline__ void coef_to_mixed_warp(const Coef &c, int n_det, double df, CoefMixed *m,
                                                    const Coef *fid = nullptr, bool rot = false) {
     const int lane = threadIdx.x & 31;
-    if (lane < NB) split_df((c.a[lane] - (fid ? fid->a[lane] : 0.0)) * INV_TWO_PI_D, m->ah[lane], m->al[lane]);
-    else if (lane == NB) split_df((c.c0 - (fid ? fid->c0 : 0.0)) * INV_TWO_PI_D, m->c0h, m->c0l);
-    else if (lane >= 16 && lane < 16 + n_det)
-        split_df(c.tau[lane - 16] - (fid ? fid->tau[lane - 16] : 0.0), m->tauh[lane - 16], m->taul[lane - 16]);
-    else if (lane >= 24 && lane < 24 + n_det) {
+    // phase coefficients (lanes 0..7, in turns), constant phase (lane 8, turns)
+    // and delays (lanes 16..): one common path, so each FP64 step is one warp
+    // instruction for all three
+    const bool isa = lane < NB, isc = lane == NB, ist = lane >= 16 && lane < 16 + n_det;
+    const int ia = isa ? lane : 0, it = ist ? lane - 16 : 0;
+    double v = isa ? c.a[ia] : (isc ? c.c0 : c.tau[it]);
+    if (fid) v -= isa ? fid->a[ia] : (isc ? fid->c0 : fid->tau[it]);
+    const double y = ist ? v : v * INV_TWO_PI_D;
+    float yh, yl;
+    split_df(y, yh, yl);
+    if (isa) { m->ah[ia] = yh; m->al[ia] = yl; }
+    else if (isc) { m->c0h = yh; m->c0l = yl; }
+    else if (ist) { m->tauh[it] = yh; m->taul[it] = yl; }
+    if (lane >= 24 && lane < 24 + n_det) {
         const int d = lane - 24;
         const double td = c.tau[d] - (fid ? fid->tau[d] : 0.0), t0 = c.tau[0] - (fid ? fid->tau[0] : 0.0);
         m->dtau[d] = __double2float_rn(df * td);
@@ -645,9 +654,11 @@ __device__ __forceinline__ void df_acc(float &hi, float &lo, float x) {
     lo += e;
 }
 
+// Returns the thread's double-float sums zh/zl[d][re, im], not reduced over
+// threads.
 template <int NDET>
 __device__ __forceinline__ void bins_mixed(const Tables &T, int N, const CoefMixed &c, int jcut,
-                                           int tid, int stride, double zr[NDET], double zi[NDET]) {
+                                           int tid, int stride, float zh[NDET][2], float zl[NDET][2]) {
     float ah[NB], al[NB];
 #pragma unroll
     for (int m = 0; m < NB; m++) { ah[m] = c.ah[m]; al[m] = c.al[m]; }
@@ -700,9 +711,20 @@ __device__ __forceinline__ void bins_mixed(const Tables &T, int N, const CoefMix
     }
 #pragma unroll
     for (int d = 0; d < NDET; d++) {
-        zr[d] = (double)zrh[d] + (double)zrl[d];
-        zi[d] = (double)zih[d] + (double)zil[d];
+        zh[d][0] = zrh[d]; zl[d][0] = zrl[d];
+        zh[d][1] = zih[d]; zl[d][1] = zil[d];
     }
+}
+
+// Sum of v over the NDET consecutive lanes of a group starting at a multiple of
+// NDET (NDET * groups <= 32): the group's first lane gets v_0 + v_1 + ... in lane
+// order.
+template <int NDET>
+__device__ __forceinline__ double group_sum_down(double v) {
+    double t = v;
+#pragma unroll
+    for (int k = 1; k < NDET; k++) t += __shfl_down_sync(0xffffffffu, v, k);
+    return t;
 }
 
 // Mixed, several candidates at once: every thread of the CTA strides over the
@@ -1077,7 +1099,7 @@ __device__ __forceinline__ void tile_bins_direct(const Tables &T, int lg, int np
 // candidates (coefficients cm[c], last bins jcut[c]): zh/zl[c][d][0/1] =
 // real/imaginary part of sum_j w_dj exp(2 pi i phase_dj), not yet reduced over
 // the warp. Detector 0 direct and the others by their rotation, one candidate
-// after the other over each group.
+// after the other.
 template <int NDET, int NC, bool PF>
 __device__ __forceinline__ void tile_bins_rot(const Tables &T, int lg, int np, const CoefMixed *cm,
                                               const int *jcut, int nc, int g0, int gstride,
@@ -1089,20 +1111,23 @@ __device__ __forceinline__ void tile_bins_rot(const Tables &T, int lg, int np, c
     for (int c = 0; c < NC; c++)
 #pragma unroll
         for (int d = 0; d < NDET; d++) zh[c][d][0] = zh[c][d][1] = zl[c][d][0] = zl[c][d][1] = 0.f;
-    int jmax = -1;
-#pragma unroll
-    for (int c = 0; c < NC; c++)
-        if (c < nc) jmax = max(jmax, jcut[c]);
-    const int ngroups = min(jmax < 0 ? 0 : (jmax >> (lg + 5)) + 1, g_end);
     const float4 *wt4 = reinterpret_cast<const float4 *>(T.wt);
     const size_t dstride = (size_t)np >> 1;
-    for (int g = g0; g < ngroups; g += gstride) {
-        const int t = (g << 5) + lane, s = t << lg, gbin = g << (lg + 5);
-        const float2 fc = __ldg(T.fc + t);
-        const float4 *w4 = wt4 + ((size_t)gbin >> 1);
+    // candidates one after the other (a run-time loop: one copy of the tile
+    // code, so the kernels' hot code is smaller; GB300: 64,897 bins, slice
+    // update 14.7 -> 13.9 ms; 519,169 bins, 249 -> 244 ms), each over its own
+    // groups in order, so each candidate's sums are the same as with the
+    // candidates taken in turn over each group
+#pragma unroll 1
+    for (int c = 0; c < nc; c++) {
+        float ah[NDET][2], al[NDET][2];
 #pragma unroll
-        for (int c = 0; c < NC; c++) {
-            if (c >= nc) continue;
+        for (int d = 0; d < NDET; d++) ah[d][0] = ah[d][1] = al[d][0] = al[d][1] = 0.f;
+        const int ngroups = min(jcut[c] < 0 ? 0 : (jcut[c] >> (lg + 5)) + 1, g_end);
+        for (int g = g0; g < ngroups; g += gstride) {
+            const int t = (g << 5) + lane, s = t << lg, gbin = g << (lg + 5);
+            const float2 fc = __ldg(T.fc + t);
+            const float4 *w4 = wt4 + ((size_t)gbin >> 1);
             const int nmax = min(max(jcut[c] - gbin + 1, 0), L);
             if (nmax == 0) continue;
             const int cnt = min(max(jcut[c] - s + 1, 0), L);
@@ -1168,10 +1193,19 @@ __device__ __forceinline__ void tile_bins_rot(const Tables &T, int lg, int np, c
                 tile_one<NDET, true, PF>(w4, dstride, lane, half, (nmax + 7) & ~7, cnt, k, cm[c], zr, zi);
 #pragma unroll
             for (int d = 0; d < NDET; d++) {
-                df_acc(zh[c][d][0], zl[c][d][0], zr[d]);
-                df_acc(zh[c][d][1], zl[c][d][1], zi[d]);
+                df_acc(ah[d][0], al[d][0], zr[d]);
+                df_acc(ah[d][1], al[d][1], zi[d]);
             }
         }
+#pragma unroll
+        for (int cc = 0; cc < NC; cc++)
+            if (cc == c) {
+#pragma unroll
+                for (int d = 0; d < NDET; d++) {
+                    zh[cc][d][0] = ah[d][0]; zh[cc][d][1] = ah[d][1];
+                    zl[cc][d][0] = al[d][0]; zl[cc][d][1] = al[d][1];
+                }
+            }
     }
 }
 // The tiled form's sums, by rotation (ROT: tiles of 32 bins or more; GB300,

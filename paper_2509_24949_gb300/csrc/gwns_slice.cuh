@@ -37,11 +37,14 @@ __device__ __forceinline__ void cta_loglike_bins(const Model &M, const Tables &T
             zi[d] = (double)zh[0][d][1] + (double)zl[0][d][1];
         }
     } else {
-        bins_mixed<NDET>(T, M.N, cm, coef.jcut, threadIdx.x, W * 32, zr, zi);
+        float zh[NDET][2], zl[NDET][2];
+        bins_mixed<NDET>(T, M.N, cm, coef.jcut, threadIdx.x, W * 32, zh, zl);
 #pragma unroll
         for (int d = 0; d < NDET; d++) {
-            zr[d] = warp_sum(zr[d]);
-            zi[d] = warp_sum(zi[d]);
+            warp_sum_df(zh[d][0], zl[d][0]);
+            warp_sum_df(zh[d][1], zl[d][1]);
+            zr[d] = (double)zh[d][0] + (double)zl[d][0];
+            zi[d] = (double)zh[d][1] + (double)zl[d][1];
         }
     }
     if (lane == 0) {
@@ -183,7 +186,7 @@ __global__ void __launch_bounds__(W * 32) k_eval_batch(Model M, Tables T, const 
     }
     __syncthreads();
     for (int p = warp; p < np; p += W) {
-        double ZR[NDET], ZI[NDET];
+        double ZR[1] = {0.0}, ZI[1] = {0.0};      // lane d < NDET: detector d's sums
         if (M.tlg) {
             float zh[1][NDET][2], zl[1][NDET][2];
             if (M.tlg >= 5)
@@ -194,22 +197,30 @@ __global__ void __launch_bounds__(W * 32) k_eval_batch(Model M, Tables T, const 
             for (int dd = 0; dd < NDET; dd++) {
                 warp_sum_df(zh[0][dd][0], zl[0][dd][0]);
                 warp_sum_df(zh[0][dd][1], zl[0][dd][1]);
-                ZR[dd] = (double)zh[0][dd][0] + (double)zl[0][dd][0];
-                ZI[dd] = (double)zh[0][dd][1] + (double)zl[0][dd][1];
+                if (lane == dd) {
+                    ZR[0] = (double)zh[0][dd][0] + (double)zl[0][dd][0];
+                    ZI[0] = (double)zh[0][dd][1] + (double)zl[0][dd][1];
+                }
             }
         } else {
-            double zr[NDET], zi[NDET];
-            bins_mixed<NDET>(T, M.N, cm[p], coef[p].jcut, lane, 32, zr, zi);
+            float zh[NDET][2], zl[NDET][2];
+            bins_mixed<NDET>(T, M.N, cm[p], coef[p].jcut, lane, 32, zh, zl);
 #pragma unroll
             for (int dd = 0; dd < NDET; dd++) {
-                ZR[dd] = warp_sum(zr[dd]);
-                ZI[dd] = warp_sum(zi[dd]);
+                warp_sum_df(zh[dd][0], zl[dd][0]);
+                warp_sum_df(zh[dd][1], zl[dd][1]);
+                if (lane == dd) {
+                    ZR[0] = (double)zh[dd][0] + (double)zl[dd][0];
+                    ZI[0] = (double)zh[dd][1] + (double)zl[dd][1];
+                }
             }
         }
+        // lane d < NDET: detector d's term, summed over the detector lanes
+        double t = 0.0;
+        if (lane < NDET) t = coef[p].gre[lane] * ZR[0] - coef[p].gim[lane] * ZI[0];
+        t = group_sum_down<NDET>(t);
         if (lane == 0) {
-            double v = -0.5 * coef[p].hh;
-#pragma unroll
-            for (int dd = 0; dd < NDET; dd++) v += coef[p].gre[dd] * ZR[dd] - coef[p].gim[dd] * ZI[dd];
+            const double v = t - 0.5 * coef[p].hh;
             logl[i0 + p] = v;
             if (st) {
                 atomicAdd(&st->eval_points, 1ull);
@@ -959,11 +970,8 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
                     for (int w2 = 0; w2 < (WS ? 1 : W); w2++) { ZR += part[w2][sc][dd][0]; ZI += part[w2][sc][dd][1]; }
                     v = coef[sc].gre[dd] * ZR - coef[sc].gim[dd] * ZI;
                 }
-                for (int sc2 = 0; sc2 < ns; sc2++) {
-                    double t = (lane / NDET == sc2 && lane < S * NDET) ? v : 0.0;
-                    t = warp_sum(t);
-                    if (lane == 0) lval[sc2] = t - 0.5 * coef[sc2].hh;
-                }
+                const double t = group_sum_down<NDET>(v);
+                if (dd == 0 && sc < ns && lane < S * NDET) lval[sc] = t - 0.5 * coef[sc].hh;
             }
         } else if (PREC == 0 && W > 1 && M.model == M_GW && !M.rb && tailmode == 2) {
             // FP64 on fine grids: each candidate's bins on two warps (warps on
@@ -994,11 +1002,8 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
                     }
                     v = coef[sc].gre[dd] * ZR - coef[sc].gim[dd] * ZI;
                 }
-                for (int sc2 = 0; sc2 < ns; sc2++) {
-                    double t = (lane / NDET == sc2 && lane < S * NDET) ? v : 0.0;
-                    t = warp_sum(t);
-                    if (lane == 0) lval[sc2] = t - 0.5 * coef[sc2].hh;
-                }
+                const double t = group_sum_down<NDET>(v);
+                if (dd == 0 && sc < ns && lane < S * NDET) lval[sc] = t - 0.5 * coef[sc].hh;
             }
         } else if (warp < ns) {
             // one candidate per slot warp: bins and warp reduction
@@ -1028,11 +1033,14 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
             } else {
                 coef_to_mixed_warp(coef[warp], M.n_det, M.df, &cm[warp], nullptr, form_rot<FORM>(M));
                 __syncwarp();
-                double zr[NDET], zi[NDET];
-                bins_mixed<NDET>(T, M.N, cm[warp], coef[warp].jcut, lane, 32, zr, zi);
+                float zh[NDET][2], zl[NDET][2];
+                bins_mixed<NDET>(T, M.N, cm[warp], coef[warp].jcut, lane, 32, zh, zl);
 #pragma unroll
                 for (int dd = 0; dd < NDET; dd++) {
-                    const double ZR = warp_sum(zr[dd]), ZI = warp_sum(zi[dd]);
+                    warp_sum_df(zh[dd][0], zl[dd][0]);
+                    warp_sum_df(zh[dd][1], zl[dd][1]);
+                    const double ZR = (double)zh[dd][0] + (double)zl[dd][0];
+                    const double ZI = (double)zh[dd][1] + (double)zl[dd][1];
                     v += coef[warp].gre[dd] * ZR - coef[warp].gim[dd] * ZI;
                 }
             }
