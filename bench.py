@@ -328,7 +328,7 @@ def mixed_slice_roofline(kern, pbins, evals, steps, n_det, tile, step_kernel_ms)
     traffic, traffic_pb = recorded_traffic()
     if traffic is not None and traffic_pb:
         traffic = traffic * pb / traffic_pb     # scaled to this launch's point-bins
-    return {"bound": "alu", "kernel": f"k_slice<MIXED,{n_det} det> (fused slice update + likelihood)",
+    return {"bound": "alu", "kernel": f"k_slice_ws<MIXED,{n_det} det> (work-shared fused slice update + likelihood)",
             "pipe": pipe, "achieved": pb * per_pb / (ms / 1e3) / 1e12, "peak": peak,
             "unit": f"T {pipe} lane-instructions/s", "frac": frac,
             "traffic": traffic,
