@@ -261,6 +261,9 @@ StepArgs step_args(ns_ctx *c, int k) {
     A.ws_nslot = ws ? c->ws_nslot : 0;
     A.ws_gchunk = c->ws_gchunk;
     A.ws_maxchunk = c->ws_maxchunk;
+    // test of the timeout path: the owner waits for one chunk more than its round has,
+    // the bounded wait runs out and ns_step reports NS_ERR_TIMEOUT (no GPU fault or hang)
+    A.ws_test_extra = ws ? c->ws_test_extra : 0;
     return A;
 }
 
@@ -545,6 +548,8 @@ int ns_init(ns_ctx **out, const ns_prior *prior, const ns_data *data, const ns_p
                 ns_free(c);
                 return NS_ERR_CUDA;
             }
+            const char *stall = std::getenv("GWNS_TEST_WS_STALL");
+            c->ws_test_extra = (stall && stall[0] == '1') ? 1 : 0;
         }
     }
     if (cudaMallocHost((void **)&c->h_state, sizeof(RunState)) != cudaSuccess) { ns_free(c); return NS_ERR_OOM; }

@@ -43,6 +43,7 @@ struct ns_ctx {
     gwns::WsSlot *ws = nullptr;
     double *ws_part = nullptr;
     int ws_nslot = 0, ws_gchunk = 0, ws_maxchunk = 0;
+    int ws_test_extra = 0;           // GWNS_TEST_WS_STALL set at ns_init: see step_args
     int n_sm = 152;
     double *chol = nullptr;
     double *dead_u = nullptr, *dead_logl = nullptr, *dead_logw = nullptr, *dead_nlive = nullptr;

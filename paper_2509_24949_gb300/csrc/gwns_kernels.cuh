@@ -72,6 +72,7 @@ struct StepArgs {
     WsSlot *ws;
     double *ws_part;
     int ws_nslot, ws_gchunk, ws_maxchunk;
+    int ws_test_extra;    // test hook: chunks the owner waits for beyond its round's (0 in use)
 };
 
 // One analysis' iteration arguments, for the multi-analysis launches.

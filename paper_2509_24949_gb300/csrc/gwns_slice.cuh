@@ -726,7 +726,9 @@ __device__ void ws_owner_round(const Model &M, const Tables &T, const StepArgs &
         if (lane == 0) atomicAdd(&slot->done, 1);
     }
     if (warp == 0 && lane == 0) {
-        for (long long it = 0; *((volatile int *)&slot->done) < nch; it++) {
+        // ws_test_extra (a test hook, 0 in use) makes the owner wait for chunks
+        // nobody computes, so that the bounded wait runs out
+        for (long long it = 0; *((volatile int *)&slot->done) < nch + A.ws_test_extra; it++) {
             if (it > WS_WAIT_LIMIT) {
                 atomicOr(&A.state->status, 2);
                 break;
@@ -834,6 +836,9 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
     }
     for (;;) {
         if (warp == 0) {
+            // a bounded wait of the work-shared update gave up (status bit 1):
+            // every chain ends at its current point, so that the launch ends
+            if (WS && (*((volatile int *)&A.state->status) & 2)) c.phase = PH_DONE;
             if (A.kernel == 1) walk_run(M, A, c, chain, iter, lstar, walk_len);
             else chain_run(M, A, c, chain, iter, lstar, e_next, e_next_step);
             // plan the base depth while many chains run; the stragglers of the

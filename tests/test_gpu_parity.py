@@ -663,6 +663,30 @@ def test_mixed_wide_ctas_on_the_largest_grid(gw):
     assert np.max(np.abs(l - want)) < MIXED_ATOL
 
 
+def test_work_shared_wait_timeout_is_reported(gw, monkeypatch):
+    """The work-shared update's waits are bounded. With the test hook
+    GWNS_TEST_WS_STALL=1 (read at ns_init) each chain's owner waits for one
+    chunk more than its round has; the wait runs out after some seconds, the
+    chains end at their current points, and ns_step returns NS_ERR_TIMEOUT with
+    status bit 1 set. Nothing faults: a context created without the hook then
+    runs normally."""
+    import time
+    w, pb, th = problem("c4")
+    monkeypatch.setenv("GWNS_TEST_WS_STALL", "1")
+    sp = sampler_from(gw, pb, 1, n_live=8, k=2, steps_per_dim=1, seed=3)
+    monkeypatch.delenv("GWNS_TEST_WS_STALL")
+    t0 = time.time()
+    with pytest.raises(gw.GWNSError) as err:
+        sp.step()
+    assert err.value.code == -6          # NS_ERR_TIMEOUT
+    assert sp.stats()["status"] & 2
+    sp.close()
+    assert time.time() - t0 < 120
+    with sampler_from(gw, pb, 1, n_live=8, k=2, steps_per_dim=1, seed=3) as sp2:
+        sp2.step()
+        assert sp2.stats()["status"] == 0
+
+
 @pytest.mark.parametrize("slots", [1, 2, 4])
 def test_mixed_tiled_form_in_slice_update(gw, slots):
     """A fine grid below the cooperative size (8000 bins at 1/32 Hz, 32-bin
