@@ -119,9 +119,11 @@ struct CoefMixed {
     float dtau[MAXDET];     // df tau_d: phase advance per bin [turns]
     // tiled form, detectors d >= 1 against detector 0: beta_d = 2 pi df (tau_d - tau_0)
     // [rad per bin], rho_d = exp(-i beta_d), eps8_d = exp(-8 i beta_d) - 1 (its real part
-    // -2 sin^2(4 beta_d) kept to full relative precision)
+    // -2 sin^2(4 beta_d) kept to full relative precision); rho2_d = rho_d^2, the
+    // step between the even (odd) bins of a tile
     float beta[MAXDET];
     float rho[MAXDET][2];
+    float rho2[MAXDET][2];
     float eps8[MAXDET][2];
 };
 
@@ -517,12 +519,14 @@ __device__ __forceinline__ void coef_to_mixed_warp(const Coef &c, int n_det, dou
         m->dtau[d] = __double2float_rn(df * td);
         if (!rot) return;
         // the rotation of detector d's phase against detector 0's per bin, its
-        // unit step and eight-bin step (FP32 libm sine: within 2 ulp)
+        // unit, two-bin and eight-bin steps (FP32 libm sine: within 2 ulp)
         const float b = __double2float_rn(TWO_PI_D * df * (td - t0));
-        const float h1 = sinf(0.5f * b), h4 = sinf(4.0f * b);
+        const float h1 = sinf(0.5f * b), h2 = sinf(b), h4 = sinf(4.0f * b);
         m->beta[d] = b;
         m->rho[d][0] = 1.0f - 2.0f * h1 * h1;
-        m->rho[d][1] = -sinf(b);
+        m->rho[d][1] = -h2;
+        m->rho2[d][0] = 1.0f - 2.0f * h2 * h2;
+        m->rho2[d][1] = -sinf(2.0f * b);
         m->eps8[d][0] = -2.0f * h4 * h4;
         m->eps8[d][1] = -sinf(8.0f * b);
     }
@@ -826,144 +830,193 @@ __device__ __forceinline__ double warp_max(double v) {
 // TwoSum), C_2..C_TK plain FP32 (below a turn on 128-bin tiles, so their FP32
 // rounding stays below 4e-7 rad).
 // Detector 0, per bin: C_1 x as an error-free FP32 product reduced mod 1, the
-// rest a short Horner sum, the phase psi_0 in radians, FP32 __sincosf for
+// rest a short Horner sum (the delay term f tau_0 rides in its linear
+// coefficient), the phase psi_0 in radians, FP32 __sincosf for
 // E = exp(i psi_0) and the complex MAC with the weighted data.
 // Detector d >= 1 differs from detector 0 by alpha_d + beta_d x, linear in the
 // bin, so its tile sum  sum_x w_dx E_x exp(i (alpha_d + beta_d x))  is
 // exp(i (alpha_d + beta_d x_e)) times a Horner sum in rho_d = exp(-i beta_d)
-// anchored at the last bin x_e: S <- S rho_d + w_dx E_x within segments of
-// eight bins, T <- T + T eps8_d + S across them, eps8_d = exp(-8 i beta_d) - 1
-// (the magnitude error of a rounded unit step builds up over seven steps at
-// most). These detectors take no sine or cosine per bin. Tiles of 16 bins or
-// fewer keep a sine and cosine per detector and bin (tile_bins_direct), as does
-// the serving kernel at every tile length. Each
+// anchored at the last bin x_e. The long-tile form (tile_pairs) runs that sum
+// as two, over the even and the odd bins, each in steps of rho_d^2:
+// S <- S rho_d^2 + w_dx E_x within segments of eight bins, T <- T + T eps8_d + S
+// across them, eps8_d = exp(-8 i beta_d) - 1 (the magnitude error of a rounded
+// step builds up over three steps at most), and at the tile's end
+// T_even rho_d + T_odd. These detectors take no sine or cosine per bin. Two
+// bins (i, i + 1) travel together in the two halves of the packed FP32 pair
+// instructions (FFMA2, FMUL2): the same FP32 arithmetic on half the issue
+// slots. Tiles of 16 bins or fewer keep a sine and cosine per detector and bin
+// (tile_bins_direct), as does the serving kernel at every tile length. Each
 // tile's sums are flushed into double-float accumulators; the only per-bin
-// table is the weighted data.
+// table is the weighted data, stored per detector, tile group and bin pair as
+// float4 (Re w_i, Re w_i+1, Im w_i, Im w_i+1).
 constexpr int TK = 7;
 constexpr float TWO_PI_F = 6.28318530717958648f;
 
-// Position of bin j in the pair-tile order of the weighted data: at step i of
-// a tile, lanes read consecutive float4s (bins i, i + 1 of their tiles).
+// Position of bin j in the pair-tile order of the weighted data, in float2
+// slots: at step i of a tile, lanes read consecutive float4s (bins i, i + 1 of
+// their tiles; the float4 holds both real parts, then both imaginary parts).
 __device__ __forceinline__ int tile_pos2(int j, int lg) {
     const int t = j >> lg, i = j & ((1 << lg) - 1);
     return ((t >> 5) << (lg + 5)) + ((i >> 1) << 6) + ((t & 31) << 1) + (i & 1);
 }
 
+// Packed FP32 pairs: lane x of a float2 carries bin i, lane y bin i + 1.
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+// a - b, as one packed FMA with the pair (-1, -1)
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, bc2(-1.0f), a); }
+
 // Constants of one candidate over one lane's tile.
 template <int NDET>
 struct TileCand {
-    float c1h, c1l, ck[TK - 1];     // C_1 (double-float), C_2..C_TK [turns]
-    float aa0, dt0;                 // detector 0: 2 pi anchor, 2 pi df tau_0 [rad]
+    float c1h, c1l, ck[TK - 1];     // C_1 (double-float; c1l also holds df tau_0), C_2..C_TK [turns]
+    float aa0;                      // detector 0: 2 pi anchor [rad]
     float alpha[NDET];              // detectors d >= 1: alpha_d [rad]
 };
+
+// Four bins (two pairs) of one candidate over one lane's tile, from bin q:
+// detector 0's sums in (pr, pim), detector d's segment sums in (sr, si)[d].
+// FIRST: the segment's first bins (its sums start here). MASK: bins >= cnt
+// add nothing.
+template <int NDET, bool MASK, bool FIRST>
+__device__ __forceinline__ void pair_step(const float4 (&w)[NDET][2], int q, int cnt, float2 x0,
+                                          const TileCand<NDET> &k, const float2 (&r2)[NDET][3],
+                                          float2 &pr, float2 &pim, float2 (&sr)[NDET], float2 (&si)[NDET]) {
+    const float2 c1h = bc2(k.c1h), nc1h = bc2(-k.c1h);
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        const float2 x = h ? add2(x0, bc2(2.0f)) : x0;
+        // p + e = C_1h x exactly (ne = -e); nsm = -(rest of the phase) by Horner's
+        // rule on the negated coefficients, down to the C_1 low part
+        const float2 p = mul2(c1h, x);
+        const float2 ne = fma2(nc1h, x, p);
+        float2 nh = bc2(-k.ck[TK - 2]);
+#pragma unroll
+        for (int j = TK - 3; j >= 0; j--) nh = fma2(nh, x, bc2(-k.ck[j]));
+        nh = fma2(nh, x, bc2(-k.c1l));
+        const float2 nsm = fma2(nh, x, ne);
+        const float2 u = sub2(sub2(p, make_float2(rintf(p.x), rintf(p.y))), nsm);
+        const float2 a = fma2(u, bc2(TWO_PI_F), bc2(k.aa0));
+        float2 sv, cv;
+        __sincosf(a.x, &sv.x, &cv.x);
+        __sincosf(a.y, &sv.y, &cv.y);
+        const float2 nsv = mul2(sv, bc2(-1.0f));
+        float2 ok;
+        if (MASK) {
+            const int i = q + 2 * h;
+            ok = make_float2(i < cnt ? 1.0f : 0.0f, i + 1 < cnt ? 1.0f : 0.0f);
+        }
+#pragma unroll
+        for (int d = 0; d < NDET; d++) {
+            const float4 ww = w[d][h];
+            float2 wr = make_float2(ww.x, ww.y), wi = make_float2(ww.z, ww.w);
+            if (MASK) {
+                wr = mul2(wr, ok);
+                wi = mul2(wi, ok);
+            }
+            if (d == 0) {
+                pr = fma2(wi, nsv, fma2(wr, cv, pr));
+                pim = fma2(wi, cv, fma2(wr, sv, pim));
+            } else if (FIRST && h == 0) {
+                sr[d] = fma2(wi, nsv, mul2(wr, cv));
+                si[d] = fma2(wi, cv, mul2(wr, sv));
+            } else {
+                // S <- S rho^2 + w E  (r2[d]: Re rho^2, -Im rho^2, Im rho^2, broadcast)
+                const float2 nr = fma2(wi, nsv, fma2(wr, cv, fma2(si[d], r2[d][1], mul2(sr[d], r2[d][0]))));
+                si[d] = fma2(wi, cv, fma2(wr, sv, fma2(si[d], r2[d][0], mul2(sr[d], r2[d][2]))));
+                sr[d] = nr;
+            }
+        }
+    }
+}
 
 // One candidate over one lane's tile, bins i < nproc (a multiple of 8); with
 // MASK, bins i >= cnt add nothing (tiles at the cutoff). Returns the sums
 // sum_i w_di exp(2 pi i phase_di) per detector in zr, zi. With PF the next
 // four bins' weighted data are loaded while these four are summed (the
-// batched likelihood waits on these loads otherwise; the slice kernels, at
-// their register cap, do not).
+// batched likelihood waits on these loads otherwise; in the slice kernels, at
+// their register cap, neither this nor an L1 prefetch hint pays: GB300, c4
+// slice update 217.5 ms without, 220 ms with, 250 ms with the hint).
 template <int NDET, bool MASK, bool PF>
-__device__ __forceinline__ void tile_one(const float4 *w4, size_t dstride, int lane, int half, int nproc,
-                                         int cnt, const TileCand<NDET> &k, const CoefMixed &cm,
-                                         float (&zr)[NDET], float (&zi)[NDET]) {
-    float pr = 0.f, pim = 0.f;
-    float sr[NDET], si[NDET], tr[NDET], ti[NDET], rr[NDET], ri[NDET], er[NDET], ei[NDET];
+__device__ __forceinline__ void tile_pairs(const float4 *w4, size_t dstride, int lane, int half, int nproc,
+                                           int cnt, const TileCand<NDET> &k, const CoefMixed &cm,
+                                           float (&zr)[NDET], float (&zi)[NDET]) {
+    float2 pr = bc2(0.0f), pim = bc2(0.0f);
+    float2 sr[NDET], si[NDET], tr[NDET], ti[NDET], r2[NDET][3];
 #pragma unroll
     for (int d = 1; d < NDET; d++) {
-        sr[d] = si[d] = tr[d] = ti[d] = 0.f;
-        rr[d] = cm.rho[d][0];
-        ri[d] = cm.rho[d][1];
-        er[d] = cm.eps8[d][0];
-        ei[d] = cm.eps8[d][1];
+        tr[d] = ti[d] = bc2(0.0f);
+        r2[d][0] = bc2(cm.rho2[d][0]);
+        r2[d][1] = bc2(-cm.rho2[d][1]);
+        r2[d][2] = bc2(cm.rho2[d][1]);
     }
     float4 w[NDET][2];
+    const float4 *wp = w4 + lane;
     if (PF) {
 #pragma unroll
         for (int d = 0; d < NDET; d++) {
-            w[d][0] = __ldg(w4 + d * dstride + lane);
-            w[d][1] = __ldg(w4 + d * dstride + 32 + lane);
+            w[d][0] = __ldg(wp + d * dstride);
+            w[d][1] = __ldg(wp + d * dstride + 32);
         }
     }
-    for (int q = 0; q < nproc; q += 4) {
-        float4 wn[NDET][2];
-        if (PF) {
-            const int qn = q + 4 < nproc ? q + 4 : q;     // the last step reloads its own bins
+    float2 x0 = make_float2((float)-half, (float)(1 - half));
+    for (int q = 0; q < nproc; q += 8) {
 #pragma unroll
-            for (int d = 0; d < NDET; d++) {
-                wn[d][0] = __ldg(w4 + d * dstride + (qn << 4) + lane);
-                wn[d][1] = __ldg(w4 + d * dstride + (qn << 4) + 32 + lane);
-            }
-        } else {
+        for (int s = 0; s < 2; s++) {
+            const int qs = q + 4 * s;
+            float4 wn[NDET][2];
+            if (PF) {
+                const int qn = qs + 4 < nproc ? qs + 4 : qs;     // the last step reloads its own bins
 #pragma unroll
-            for (int d = 0; d < NDET; d++) {
-                w[d][0] = __ldg(w4 + d * dstride + (q << 4) + lane);
-                w[d][1] = __ldg(w4 + d * dstride + (q << 4) + 32 + lane);
-            }
-        }
-#pragma unroll
-        for (int r = 0; r < 4; r++) {
-            const int i = q + r;
-            // C_1h x as an error-free product p + e; the rest, C_1l x + C_2 x^2 +
-            // ... + C_TK x^TK, by Horner's rule down to the C_1 low part
-            const float x = (float)(i - half);
-            const float p = k.c1h * x;
-            const float e = fmaf(k.c1h, x, -p);
-            float hq = k.ck[TK - 2];
-#pragma unroll
-            for (int j = TK - 3; j >= 0; j--) hq = fmaf(hq, x, k.ck[j]);
-            hq = fmaf(hq, x, k.c1l);
-            const float sm = fmaf(hq, x, e);
-            const float P = p - rintf(p);
-            float sv, cv;
-            __sincosf(fmaf(P + sm, TWO_PI_F, fmaf(x, k.dt0, k.aa0)), &sv, &cv);
-            const bool ok = !MASK || i < cnt;
-#pragma unroll
-            for (int d = 0; d < NDET; d++) {
-                const float4 ww = w[d][r >> 1];
-                float wr = (r & 1) ? ww.z : ww.x, wi = (r & 1) ? ww.w : ww.y;
-                if (MASK) {
-                    wr = ok ? wr : 0.f;
-                    wi = ok ? wi : 0.f;
+                for (int d = 0; d < NDET; d++) {
+                    wn[d][0] = __ldg(wp + d * dstride + (qn << 4));
+                    wn[d][1] = __ldg(wp + d * dstride + (qn << 4) + 32);
                 }
-                if (d == 0) {
-                    pr = fmaf(wr, cv, fmaf(-wi, sv, pr));
-                    pim = fmaf(wr, sv, fmaf(wi, cv, pim));
-                } else {
-                    const float cr = fmaf(wr, cv, -wi * sv), ci = fmaf(wr, sv, wi * cv);
-                    const float nr = fmaf(sr[d], rr[d], fmaf(-si[d], ri[d], cr));
-                    si[d] = fmaf(sr[d], ri[d], fmaf(si[d], rr[d], ci));
-                    sr[d] = nr;
+            } else {
+#pragma unroll
+                for (int d = 0; d < NDET; d++) {
+                    w[d][0] = __ldg(wp + d * dstride + (qs << 4));
+                    w[d][1] = __ldg(wp + d * dstride + (qs << 4) + 32);
+                }
+            }
+            if (s == 0)
+                pair_step<NDET, MASK, true>(w, qs, cnt, x0, k, r2, pr, pim, sr, si);
+            else
+                pair_step<NDET, MASK, false>(w, qs, cnt, x0, k, r2, pr, pim, sr, si);
+            x0 = add2(x0, bc2(4.0f));
+            if (PF) {
+#pragma unroll
+                for (int d = 0; d < NDET; d++) {
+                    w[d][0] = wn[d][0];
+                    w[d][1] = wn[d][1];
                 }
             }
         }
-        if (PF) {
+        // the eight-bin segment ends: T <- T + T eps8 + S
 #pragma unroll
-            for (int d = 0; d < NDET; d++) {
-                w[d][0] = wn[d][0];
-                w[d][1] = wn[d][1];
-            }
-        }
-        if (q & 4) {        // an eight-bin segment ends
-#pragma unroll
-            for (int d = 1; d < NDET; d++) {
-                const float ur = fmaf(tr[d], er[d], fmaf(-ti[d], ei[d], sr[d]));
-                const float ui = fmaf(tr[d], ei[d], fmaf(ti[d], er[d], si[d]));
-                tr[d] += ur;
-                ti[d] += ui;
-                sr[d] = si[d] = 0.f;
-            }
+        for (int d = 1; d < NDET; d++) {
+            const float2 er = bc2(cm.eps8[d][0]), ei = bc2(cm.eps8[d][1]), nei = bc2(-cm.eps8[d][1]);
+            const float2 ur = fma2(tr[d], er, fma2(ti[d], nei, sr[d]));
+            const float2 ui = fma2(tr[d], ei, fma2(ti[d], er, si[d]));
+            tr[d] = add2(tr[d], ur);
+            ti[d] = add2(ti[d], ui);
         }
     }
-    zr[0] = pr;
-    zi[0] = pim;
+    zr[0] = pr.x + pr.y;
+    zi[0] = pim.x + pim.y;
     const float xe = (float)(nproc - 1 - half);
 #pragma unroll
     for (int d = 1; d < NDET; d++) {
+        // the even bins' sum is anchored one bin before the last: T = T_even rho + T_odd
+        const float rr = cm.rho[d][0], ri = cm.rho[d][1];
+        const float Tr = fmaf(tr[d].x, rr, fmaf(-ti[d].x, ri, tr[d].y));
+        const float Ti = fmaf(tr[d].x, ri, fmaf(ti[d].x, rr, ti[d].y));
         float as, ac;
         __sincosf(fmaf(cm.beta[d], xe, k.alpha[d]), &as, &ac);
-        zr[d] = fmaf(ac, tr[d], -as * ti[d]);
-        zi[d] = fmaf(ac, ti[d], as * tr[d]);
+        zr[d] = fmaf(ac, Tr, -as * Ti);
+        zi[d] = fmaf(ac, Ti, as * Tr);
     }
 }
 
@@ -1079,7 +1132,7 @@ __device__ __forceinline__ void tile_bins_direct(const Tables &T, int lg, int np
                         float sv, cv;
                         __sincosf(red * 6.283185307179586f, &sv, &cv);
                         const float4 ww = w[d][r >> 1];
-                        const float wr = (r & 1) ? ww.z : ww.x, wi = (r & 1) ? ww.w : ww.y;
+                        const float wr = (r & 1) ? ww.y : ww.x, wi = (r & 1) ? ww.w : ww.z;
                         pr[c][d] = fmaf(wr, cv, fmaf(-wi, sv, pr[c][d]));
                         pim[c][d] = fmaf(wr, sv, fmaf(wi, cv, pim[c][d]));
                     }
@@ -1162,7 +1215,7 @@ __device__ __forceinline__ void tile_bins_rot(const Tables &T, int lg, int np, c
                     k.ck[j] = fmaf(ah, __ldg(T.tbk + ((size_t)j * NB + m) * nt + t), k.ck[j]);
             }
             k.c1h = h1 + l1;
-            k.c1l = l1 - (k.c1h - h1);
+            k.c1l = (l1 - (k.c1h - h1)) + cm[c].dtau[0];
             sh -= rintf(sh);
             // detector anchors A_d = anchor + f_c tau_d (turns, reduced), high and low parts
             float Ah[NDET], Al[NDET];
@@ -1179,7 +1232,6 @@ __device__ __forceinline__ void tile_bins_rot(const Tables &T, int lg, int np, c
                 Al[d] = sl + (e2 + e);
             }
             k.aa0 = TWO_PI_F * (Ah[0] + Al[0]);
-            k.dt0 = TWO_PI_F * cm[c].dtau[0];
 #pragma unroll
             for (int d = 1; d < NDET; d++) {
                 float a = (Ah[d] - Ah[0]) + (Al[d] - Al[0]);
@@ -1188,9 +1240,9 @@ __device__ __forceinline__ void tile_bins_rot(const Tables &T, int lg, int np, c
             }
             float zr[NDET], zi[NDET];
             if (jcut[c] >= gbin + (32 << lg) - 1)      // every tile of the group below the cutoff
-                tile_one<NDET, false, PF>(w4, dstride, lane, half, L, L, k, cm[c], zr, zi);
+                tile_pairs<NDET, false, PF>(w4, dstride, lane, half, L, L, k, cm[c], zr, zi);
             else
-                tile_one<NDET, true, PF>(w4, dstride, lane, half, (nmax + 7) & ~7, cnt, k, cm[c], zr, zi);
+                tile_pairs<NDET, true, PF>(w4, dstride, lane, half, (nmax + 7) & ~7, cnt, k, cm[c], zr, zi);
 #pragma unroll
             for (int d = 0; d < NDET; d++) {
                 df_acc(ah[d][0], al[d][0], zr[d]);

@@ -169,8 +169,15 @@ __global__ void k_build_tables(Model M, const double *dre, const double *dim, co
             const double wi = 4.0 * M.df * f76 * dim[o] / sd;
             w64[o] = make_double2(wr, wi);
             const float2 wf = make_float2(__double2float_rn(wr), __double2float_rn(wi));
-            if (lg) wt[(size_t)d * M.np + tile_pos2(j, lg)] = wf;
-            else w32[o] = wf;
+            if (lg) {
+                // float2 slot pos of the pair order -> float4 (Re, Re, Im, Im) of its bin pair
+                const size_t pos = (size_t)d * M.np + tile_pos2(j, lg);
+                float *wq = reinterpret_cast<float *>(wt) + ((pos >> 1) << 2) + (pos & 1);
+                wq[0] = wf.x;
+                wq[2] = wf.y;
+            } else {
+                w32[o] = wf;
+            }
             prefix[o] = 4.0 * M.df * f76 * f76 / sd;
         }
     }
