@@ -923,9 +923,11 @@ __device__ __forceinline__ void pair_step(const float4 (&w)[NDET][2], int q, int
                 sr[d] = fma2(wi, nsv, mul2(wr, cv));
                 si[d] = fma2(wi, cv, mul2(wr, sv));
             } else {
-                // S <- S rho^2 + w E  (r2[d]: Re rho^2, -Im rho^2, Im rho^2, broadcast)
-                const float2 nr = fma2(wi, nsv, fma2(wr, cv, fma2(si[d], r2[d][1], mul2(sr[d], r2[d][0]))));
-                si[d] = fma2(wi, cv, fma2(wr, sv, fma2(si[d], r2[d][0], mul2(sr[d], r2[d][2]))));
+                // S <- S rho^2 + w E  (r2[d]: Re rho^2, -Im rho^2, Im rho^2, broadcast); w E
+                // first, so the chain through S is two instructions per step
+                const float2 cr = fma2(wi, nsv, mul2(wr, cv)), ci = fma2(wi, cv, mul2(wr, sv));
+                const float2 nr = fma2(sr[d], r2[d][0], fma2(si[d], r2[d][1], cr));
+                si[d] = fma2(sr[d], r2[d][2], fma2(si[d], r2[d][0], ci));
                 sr[d] = nr;
             }
         }

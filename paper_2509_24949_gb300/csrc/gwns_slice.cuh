@@ -618,26 +618,23 @@ __device__ __forceinline__ void ws_chunk(const Model &M, const Tables &T, const 
                                          int ns, int c, int G, double *out) {
     const int lane = threadIdx.x & 31;
     const int g0 = c * G, g1 = g0 + G;
-    for (int c0 = 0; c0 < ns; c0 += 2) {
-        float zh[2][NDET][2], zl[2][NDET][2];
-        const int nc = ns - c0 < 2 ? ns - c0 : 2;
-        tile_bins<NDET, 2, true>(T, M.tlg, M.np, cm + c0, jc + c0, nc, g0, 1, zh, zl, g1);
-        // value v = (candidate, detector, re/im) of the pair, summed over the warp at once
+    for (int c0 = 0; c0 < ns; c0++) {
+        float zh[1][NDET][2], zl[1][NDET][2];
+        tile_bins<NDET, 1, true, true>(T, M.tlg, M.np, cm + c0, jc + c0, 1, g0, 1, zh, zl, g1);
+        // value v = (detector, re/im), summed over the warp at once
         float vh[16], vl[16];
 #pragma unroll
-        for (int sc = 0; sc < 2; sc++)
+        for (int dd = 0; dd < NDET; dd++)
 #pragma unroll
-            for (int dd = 0; dd < NDET; dd++)
-#pragma unroll
-                for (int ri = 0; ri < 2; ri++) {
-                    vh[(sc * NDET + dd) * 2 + ri] = zh[sc][dd][ri];
-                    vl[(sc * NDET + dd) * 2 + ri] = zl[sc][dd][ri];
-                }
+            for (int ri = 0; ri < 2; ri++) {
+                vh[dd * 2 + ri] = zh[0][dd][ri];
+                vl[dd * 2 + ri] = zl[0][dd][ri];
+            }
         float rh, rl;
-        warp_sum_df_many<4 * NDET>(vh, vl, rh, rl);
-        const int v = lane >> 1, sc = v / (2 * NDET), dd = (v >> 1) % NDET, ri = v & 1;
-        if ((lane & 1) == 0 && v < 4 * NDET && c0 + sc < ns)
-            out[((c0 + sc) * MAXDET + dd) * 2 + ri] = (double)rh + (double)rl;
+        warp_sum_df_many<2 * NDET>(vh, vl, rh, rl);
+        const int v = lane >> 1, dd = v >> 1, ri = v & 1;
+        if ((lane & 1) == 0 && v < 2 * NDET)
+            out[(c0 * MAXDET + dd) * 2 + ri] = (double)rh + (double)rl;
     }
 }
 
