@@ -402,6 +402,24 @@ static void choose_tiles(Model &M) {
     }
 }
 
+// The same bound at a tile group's lowest frequency f_g, where the phase and
+// the remainder ratio h / f_g are both smaller, with the degree TK_LO (whose
+// remainder constant, 3.17, is below degree 7's 4.8): the first group from which
+// it passes takes TK_LO, and so do all above it. 519,169 bins at 20 Hz in
+// 128-bin tiles: from 263.5 Hz, 88% of the bins.
+static int low_degree_group(const Model &M) {
+    if (!M.tlg) return 0x7fffffff;
+    const double mc = M.lo[P_MC] > 0.0 ? M.lo[P_MC] : 1.0;
+    const double h = 0.5 * (double)(1 << M.tlg) * M.df;
+    const int gb = 32 << M.tlg, ng = (int)(M.np / gb);
+    for (int g = 0; g < ng; g++) {
+        const double f = M.f0 + (double)g * gb * M.df;
+        const double phin = 3.0 / 128.0 * std::pow(M_PI * TSUN * mc * f, -5.0 / 3.0);
+        if (64.0 * phin * std::pow(h / f, TK_LO + 1) <= 1e-8) return g;
+    }
+    return ng;
+}
+
 static int alloc_mixed(ns_ctx *c) {
     const Model &M = c->M;
     const size_t N = M.N, nd = M.n_det;
@@ -589,6 +607,7 @@ int ns_init(ns_ctx **out, const ns_prior *prior, const ns_data *data, const ns_p
     c->T.tbk = c->X.tbk;
     c->T.fc = c->X.fc;
     c->T.wt = c->X.wt;
+    c->T.g_lo = low_degree_group(c->M);
     if (c->rb_B > 0 && (rc = build_rb(c))) { ns_free(c); return rc; }
     RunState s0;
     std::memset(&s0, 0, sizeof(s0));

@@ -93,6 +93,7 @@ struct Tables {
     const float *tbk;        // [TK-1][NB][nt] B_m^(k)(f_c) df^k / k!, k = 2..TK
     const float2 *fc;        // [nt]      f_c as (hi, lo)
     const float2 *wt;        // [n_det][np] weighted data, pair-tile order (zero beyond N)
+    int g_lo;                // tile groups g >= g_lo take the Taylor degree TK_LO, the rest TK
     RBTables rb;             // used when Model::rb is set
 };
 
@@ -825,7 +826,8 @@ __device__ __forceinline__ double warp_max(double v) {
 //   [c0 + sum_m a_m B_m(f_c) + f_c tau_d] + sum_{k=1..TK} C_k x^k + x df tau_d,
 // C_k = sum_m a_m B_m^(k)(f_c) df^k / k!: the Taylor expansion of each basis
 // function about the tile centre, its remainder bounded on the host below 1e-8
-// rad when the tiled form is chosen. Per lane and tile, the anchor in brackets
+// rad when the tiled form is chosen: degree TK on the tile groups nearest f0,
+// TK_LO on those far enough above it. Per lane and tile, the anchor in brackets
 // and C_1 are double-float dot products (error-free FP32 products via FMA,
 // TwoSum), C_2..C_TK plain FP32 (below a turn on 128-bin tiles, so their FP32
 // rounding stays below 4e-7 rad).
@@ -850,6 +852,7 @@ __device__ __forceinline__ double warp_max(double v) {
 // table is the weighted data, stored per detector, tile group and bin pair as
 // float4 (Re w_i, Re w_i+1, Im w_i, Im w_i+1).
 constexpr int TK = 7;
+constexpr int TK_LO = 3;        // the degree of tile groups far enough above f0 (Tables::g_lo)
 constexpr float TWO_PI_F = 6.28318530717958648f;
 
 // Position of bin j in the pair-tile order of the weighted data, in float2
@@ -880,7 +883,7 @@ struct TileCand {
 // detector 0's sums in (pr, pim), detector d's segment sums in (sr, si)[d].
 // FIRST: the segment's first bins (its sums start here). MASK: bins >= cnt
 // add nothing.
-template <int NDET, bool MASK, bool FIRST>
+template <int NDET, bool MASK, bool FIRST, int K>
 __device__ __forceinline__ void pair_step(const float4 (&w)[NDET][2], int q, int cnt, float2 x0,
                                           const TileCand<NDET> &k, const float2 (&r2)[NDET][3],
                                           float2 &pr, float2 &pim, float2 (&sr)[NDET], float2 (&si)[NDET]) {
@@ -892,9 +895,9 @@ __device__ __forceinline__ void pair_step(const float4 (&w)[NDET][2], int q, int
         // rule on the negated coefficients, down to the C_1 low part
         const float2 p = mul2(c1h, x);
         const float2 ne = fma2(nc1h, x, p);
-        float2 nh = bc2(-k.ck[TK - 2]);
+        float2 nh = bc2(-k.ck[K - 2]);
 #pragma unroll
-        for (int j = TK - 3; j >= 0; j--) nh = fma2(nh, x, bc2(-k.ck[j]));
+        for (int j = K - 3; j >= 0; j--) nh = fma2(nh, x, bc2(-k.ck[j]));
         nh = fma2(nh, x, bc2(-k.c1l));
         const float2 nsm = fma2(nh, x, ne);
         const float2 u = sub2(sub2(p, make_float2(rintf(p.x), rintf(p.y))), nsm);
@@ -941,7 +944,7 @@ __device__ __forceinline__ void pair_step(const float4 (&w)[NDET][2], int q, int
 // batched likelihood waits on these loads otherwise; in the slice kernels, at
 // their register cap, neither this nor an L1 prefetch hint pays: GB300, c4
 // slice update 217.5 ms without, 220 ms with, 250 ms with the hint).
-template <int NDET, bool MASK, bool PF>
+template <int NDET, bool MASK, bool PF, int K>
 __device__ __forceinline__ void tile_pairs(const float4 *w4, size_t dstride, int lane, int half, int nproc,
                                            int cnt, const TileCand<NDET> &k, const CoefMixed &cm,
                                            float (&zr)[NDET], float (&zi)[NDET]) {
@@ -984,9 +987,9 @@ __device__ __forceinline__ void tile_pairs(const float4 *w4, size_t dstride, int
                 }
             }
             if (s == 0)
-                pair_step<NDET, MASK, true>(w, qs, cnt, x0, k, r2, pr, pim, sr, si);
+                pair_step<NDET, MASK, true, K>(w, qs, cnt, x0, k, r2, pr, pim, sr, si);
             else
-                pair_step<NDET, MASK, false>(w, qs, cnt, x0, k, r2, pr, pim, sr, si);
+                pair_step<NDET, MASK, false, K>(w, qs, cnt, x0, k, r2, pr, pim, sr, si);
             x0 = add2(x0, bc2(4.0f));
             if (PF) {
 #pragma unroll
@@ -1150,24 +1153,97 @@ __device__ __forceinline__ void tile_bins_direct(const Tables &T, int lg, int np
             }
     }
 }
+// One candidate over tile group g (its 32 tiles, one per lane) by rotation,
+// with K - 1 Taylor terms C_2..C_K: the tile's constants (anchors, C_1 in
+// double-float, C_2..C_K), then its sums zr, zi per detector.
+template <int NDET, bool PF, int K>
+__device__ __forceinline__ void rot_group(const Tables &T, int lg, int np, const CoefMixed &cm, int jcut, int g,
+                                          float (&zr)[NDET], float (&zi)[NDET]) {
+    const int lane = threadIdx.x & 31;
+    const int L = 1 << lg, half = L >> 1, nt = np >> lg;
+    const int t = (g << 5) + lane, s = t << lg, gbin = g << (lg + 5);
+    const float2 fc = __ldg(T.fc + t);
+    const float4 *w4 = reinterpret_cast<const float4 *>(T.wt) + ((size_t)gbin >> 1);
+    const size_t dstride = (size_t)np >> 1;
+    const int nmax = min(max(jcut - gbin + 1, 0), L);
+    const int cnt = min(max(jcut - s + 1, 0), L);
+    TileCand<NDET> k;
+    float sh = cm.c0h, sl = cm.c0l, h1 = 0.f, l1 = 0.f;
+#pragma unroll
+    for (int j = 0; j < TK - 1; j++) k.ck[j] = 0.f;
+#pragma unroll
+    for (int m = 0; m < NB; m++) {
+        const float ah = cm.ah[m], al = cm.al[m];
+        // anchor term a_m B_m(f_c)
+        const float2 b0 = __ldg(T.tb0 + (size_t)m * nt + t);
+        float p = ah * b0.x;
+        float e = fmaf(ah, b0.x, -p);
+        e = fmaf(ah, b0.y, e);
+        e = fmaf(al, b0.x, e);
+        float s2, e2;
+        two_sum(sh, p, s2, e2);
+        sh = s2;
+        sl += e2 + e;
+        // first-order term a_m B_m'(f_c) df
+        const float2 b1 = __ldg(T.tb1 + (size_t)m * nt + t);
+        p = ah * b1.x;
+        e = fmaf(ah, b1.x, -p);
+        e = fmaf(ah, b1.y, e);
+        e = fmaf(al, b1.x, e);
+        two_sum(h1, p, s2, e2);
+        h1 = s2;
+        l1 += e2 + e;
+#pragma unroll
+        for (int j = 0; j < K - 1; j++)
+            k.ck[j] = fmaf(ah, __ldg(T.tbk + ((size_t)j * NB + m) * nt + t), k.ck[j]);
+    }
+    k.c1h = h1 + l1;
+    k.c1l = (l1 - (k.c1h - h1)) + cm.dtau[0];
+    sh -= rintf(sh);
+    // detector anchors A_d = anchor + f_c tau_d (turns, reduced), high and low parts
+    float Ah[NDET], Al[NDET];
+#pragma unroll
+    for (int d = 0; d < NDET; d++) {
+        const float th = cm.tauh[d], tl = cm.taul[d];
+        const float p = th * fc.x;
+        float e = fmaf(th, fc.x, -p);
+        e = fmaf(th, fc.y, e);
+        e = fmaf(tl, fc.x, e);
+        float s2, e2;
+        two_sum(sh, p, s2, e2);
+        Ah[d] = s2 - rintf(s2);
+        Al[d] = sl + (e2 + e);
+    }
+    k.aa0 = TWO_PI_F * (Ah[0] + Al[0]);
+#pragma unroll
+    for (int d = 1; d < NDET; d++) {
+        float a = (Ah[d] - Ah[0]) + (Al[d] - Al[0]);
+        a -= rintf(a);
+        k.alpha[d] = TWO_PI_F * a;
+    }
+    if (jcut >= gbin + (32 << lg) - 1)      // every tile of the group below the cutoff
+        tile_pairs<NDET, false, PF, K>(w4, dstride, lane, half, L, L, k, cm, zr, zi);
+    else
+        tile_pairs<NDET, true, PF, K>(w4, dstride, lane, half, (nmax + 7) & ~7, cnt, k, cm, zr, zi);
+}
+
 // One warp's double-float sums over tile groups g0, g0 + gstride, ... for nc <= NC
 // candidates (coefficients cm[c], last bins jcut[c]): zh/zl[c][d][0/1] =
 // real/imaginary part of sum_j w_dj exp(2 pi i phase_dj), not yet reduced over
 // the warp. Detector 0 direct and the others by their rotation, one candidate
-// after the other.
-template <int NDET, int NC, bool PF>
+// after the other. With LO, groups g >= T.g_lo take the Taylor degree TK_LO and
+// the rest TK (GB300, 519,169 bins: slice update 205.8 -> 192.3 ms); without it
+// every group takes TK, one copy of the tile code (the c2 slice update, bound by
+// latency and instruction fetch, runs 13.5 ms with one copy and 14.5 with two).
+template <int NDET, int NC, bool PF, bool LO>
 __device__ __forceinline__ void tile_bins_rot(const Tables &T, int lg, int np, const CoefMixed *cm,
                                               const int *jcut, int nc, int g0, int gstride,
                                               float zh[NC][NDET][2], float zl[NC][NDET][2],
                                               int g_end = 0x7fffffff) {
-    const int lane = threadIdx.x & 31;
-    const int L = 1 << lg, half = L >> 1, nt = np >> lg;
 #pragma unroll
     for (int c = 0; c < NC; c++)
 #pragma unroll
         for (int d = 0; d < NDET; d++) zh[c][d][0] = zh[c][d][1] = zl[c][d][0] = zl[c][d][1] = 0.f;
-    const float4 *wt4 = reinterpret_cast<const float4 *>(T.wt);
-    const size_t dstride = (size_t)np >> 1;
     // candidates one after the other (a run-time loop: one copy of the tile
     // code, so the kernels' hot code is smaller; GB300: 64,897 bins, slice
     // update 14.7 -> 13.9 ms; 519,169 bins, 249 -> 244 ms), each over its own
@@ -1180,71 +1256,12 @@ __device__ __forceinline__ void tile_bins_rot(const Tables &T, int lg, int np, c
         for (int d = 0; d < NDET; d++) ah[d][0] = ah[d][1] = al[d][0] = al[d][1] = 0.f;
         const int ngroups = min(jcut[c] < 0 ? 0 : (jcut[c] >> (lg + 5)) + 1, g_end);
         for (int g = g0; g < ngroups; g += gstride) {
-            const int t = (g << 5) + lane, s = t << lg, gbin = g << (lg + 5);
-            const float2 fc = __ldg(T.fc + t);
-            const float4 *w4 = wt4 + ((size_t)gbin >> 1);
-            const int nmax = min(max(jcut[c] - gbin + 1, 0), L);
-            if (nmax == 0) continue;
-            const int cnt = min(max(jcut[c] - s + 1, 0), L);
-            TileCand<NDET> k;
-            float sh = cm[c].c0h, sl = cm[c].c0l, h1 = 0.f, l1 = 0.f;
-#pragma unroll
-            for (int j = 0; j < TK - 1; j++) k.ck[j] = 0.f;
-#pragma unroll
-            for (int m = 0; m < NB; m++) {
-                const float ah = cm[c].ah[m], al = cm[c].al[m];
-                // anchor term a_m B_m(f_c)
-                const float2 b0 = __ldg(T.tb0 + (size_t)m * nt + t);
-                float p = ah * b0.x;
-                float e = fmaf(ah, b0.x, -p);
-                e = fmaf(ah, b0.y, e);
-                e = fmaf(al, b0.x, e);
-                float s2, e2;
-                two_sum(sh, p, s2, e2);
-                sh = s2;
-                sl += e2 + e;
-                // first-order term a_m B_m'(f_c) df
-                const float2 b1 = __ldg(T.tb1 + (size_t)m * nt + t);
-                p = ah * b1.x;
-                e = fmaf(ah, b1.x, -p);
-                e = fmaf(ah, b1.y, e);
-                e = fmaf(al, b1.x, e);
-                two_sum(h1, p, s2, e2);
-                h1 = s2;
-                l1 += e2 + e;
-#pragma unroll
-                for (int j = 0; j < TK - 1; j++)
-                    k.ck[j] = fmaf(ah, __ldg(T.tbk + ((size_t)j * NB + m) * nt + t), k.ck[j]);
-            }
-            k.c1h = h1 + l1;
-            k.c1l = (l1 - (k.c1h - h1)) + cm[c].dtau[0];
-            sh -= rintf(sh);
-            // detector anchors A_d = anchor + f_c tau_d (turns, reduced), high and low parts
-            float Ah[NDET], Al[NDET];
-#pragma unroll
-            for (int d = 0; d < NDET; d++) {
-                const float th = cm[c].tauh[d], tl = cm[c].taul[d];
-                const float p = th * fc.x;
-                float e = fmaf(th, fc.x, -p);
-                e = fmaf(th, fc.y, e);
-                e = fmaf(tl, fc.x, e);
-                float s2, e2;
-                two_sum(sh, p, s2, e2);
-                Ah[d] = s2 - rintf(s2);
-                Al[d] = sl + (e2 + e);
-            }
-            k.aa0 = TWO_PI_F * (Ah[0] + Al[0]);
-#pragma unroll
-            for (int d = 1; d < NDET; d++) {
-                float a = (Ah[d] - Ah[0]) + (Al[d] - Al[0]);
-                a -= rintf(a);
-                k.alpha[d] = TWO_PI_F * a;
-            }
+            if (jcut[c] < (g << (lg + 5))) continue;
             float zr[NDET], zi[NDET];
-            if (jcut[c] >= gbin + (32 << lg) - 1)      // every tile of the group below the cutoff
-                tile_pairs<NDET, false, PF>(w4, dstride, lane, half, L, L, k, cm[c], zr, zi);
+            if (LO && g >= T.g_lo)
+                rot_group<NDET, PF, TK_LO>(T, lg, np, cm[c], jcut[c], g, zr, zi);
             else
-                tile_pairs<NDET, true, PF>(w4, dstride, lane, half, (nmax + 7) & ~7, cnt, k, cm[c], zr, zi);
+                rot_group<NDET, PF, TK>(T, lg, np, cm[c], jcut[c], g, zr, zi);
 #pragma unroll
             for (int d = 0; d < NDET; d++) {
                 df_acc(ah[d][0], al[d][0], zr[d]);
@@ -1267,13 +1284,13 @@ __device__ __forceinline__ void tile_bins_rot(const Tables &T, int lg, int np, c
 // 32-bin tiles: 14.3 -> 13.8 ms) or direct (shorter tiles, where the per-tile
 // rotation setup outweighs the saved sines: 64,897 bins in 16-bin tiles, 14.3
 // against 15.9 ms by rotation). Callers choose by the tile length.
-template <int NDET, int NC, bool ROT, bool PF = false>
+template <int NDET, int NC, bool ROT, bool PF = false, bool LO = false>
 __device__ __forceinline__ void tile_bins(const Tables &T, int lg, int np, const CoefMixed *cm,
                                           const int *jcut, int nc, int g0, int gstride,
                                           float zh[NC][NDET][2], float zl[NC][NDET][2],
                                           int g_end = 0x7fffffff) {
     if constexpr (ROT)
-        tile_bins_rot<NDET, NC, PF>(T, lg, np, cm, jcut, nc, g0, gstride, zh, zl, g_end);
+        tile_bins_rot<NDET, NC, PF, LO>(T, lg, np, cm, jcut, nc, g0, gstride, zh, zl, g_end);
     else
         tile_bins_direct<NDET, NC>(T, lg, np, cm, jcut, nc, g0, gstride, zh, zl, g_end);
 }

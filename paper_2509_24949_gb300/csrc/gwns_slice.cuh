@@ -26,7 +26,7 @@ __device__ __forceinline__ void cta_loglike_bins(const Model &M, const Tables &T
         // tiled form: warp w takes tile groups w, w + W, ...
         float zh[1][NDET][2], zl[1][NDET][2];
         if (M.tlg >= 5)
-            tile_bins<NDET, 1, true, true>(T, M.tlg, M.np, &cm, &coef.jcut, 1, warp, W, zh, zl);
+            tile_bins<NDET, 1, true, true, true>(T, M.tlg, M.np, &cm, &coef.jcut, 1, warp, W, zh, zl);
         else
             tile_bins<NDET, 1, false>(T, M.tlg, M.np, &cm, &coef.jcut, 1, warp, W, zh, zl);
 #pragma unroll
@@ -620,7 +620,7 @@ __device__ __forceinline__ void ws_chunk(const Model &M, const Tables &T, const 
     const int g0 = c * G, g1 = g0 + G;
     for (int c0 = 0; c0 < ns; c0++) {
         float zh[1][NDET][2], zl[1][NDET][2];
-        tile_bins<NDET, 1, true, true>(T, M.tlg, M.np, cm + c0, jc + c0, 1, g0, 1, zh, zl, g1);
+        tile_bins<NDET, 1, true, true, true>(T, M.tlg, M.np, cm + c0, jc + c0, 1, g0, 1, zh, zl, g1);
         // value v = (detector, re/im), summed over the warp at once
         float vh[16], vl[16];
 #pragma unroll
