@@ -214,8 +214,8 @@ def timed_first_iterations(sp, blob, stream, steps, flush):
     flush, then CUDA events on the library's stream around ns_step); returns
     per-step ms and the counters' differences over the timed steps."""
     import torch
-    ms, ev0, pb0, k0 = [], 0, 0, [0.0] * 5
-    evals, pbins, kern = 0, 0, [0.0] * 5
+    ms = []
+    evals, pbins, pbins_lo, kern = 0, 0, 0, [0.0] * 5
     for _ in range(steps):
         sp.restore(blob)
         s0 = sp.stats()
@@ -229,8 +229,9 @@ def timed_first_iterations(sp, blob, stream, steps, flush):
         ms.append(a.elapsed_time(b))
         evals += s1["evals"] - s0["evals"]
         pbins += s1["point_bins"] - s0["point_bins"]
+        pbins_lo += s1["point_bins_lo"] - s0["point_bins_lo"]
         kern = [x + (q - p) for x, p, q in zip(kern, s0["kernel_ms"], s1["kernel_ms"])]
-    return ms, evals, pbins, kern
+    return ms, evals, pbins, kern, pbins_lo
 
 
 def run_gpu(args):
@@ -260,7 +261,7 @@ def run_gpu(args):
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(dev) as clk:
-        step_ms, evals, pbins, kern = timed_first_iterations(sp, blob, stream, args.steps, flush)
+        step_ms, evals, pbins, kern, pbins_lo = timed_first_iterations(sp, blob, stream, args.steps, flush)
         torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -268,7 +269,7 @@ def run_gpu(args):
     total_ms_max, evals_all = reduce_ranks(dist, total_ms, evals)
     value = evals_all / (total_ms_max / 1e3)
     tile = sp.stats()["mixed_tile"]
-    roof = mixed_slice_roofline(kern, pbins, evals, args.steps, w.n_det, tile, sum(kern))
+    roof = mixed_slice_roofline(kern, pbins, evals, args.steps, w.n_det, tile, sum(kern), pbins_lo)
 
     extras = rank == 0 and not args.core_only
     # the whole run to the stopping rule, from the same initial state
@@ -314,12 +315,21 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-def mixed_slice_roofline(kern, pbins, evals, steps, n_det, tile, step_kernel_ms):
+def executed_count(pb, pb_lo, n_det, tile):
+    """FP32 instructions per point-bin the rotation form executes when the
+    tile groups from the low-degree threshold run the Taylor degree 3: the
+    frozen count less the 4 Horner steps of C_4..C_7 on those bins."""
+    return mixed_fp32_per_point_bin(n_det, tile) - LOW_DEGREE_SAVING * (pb_lo / pb if pb else 0.0)
+
+
+def mixed_slice_roofline(kern, pbins, evals, steps, n_det, tile, step_kernel_ms, pbins_lo=0):
     """Roofline of the fused slice update (k_slice<MIXED>) over the timed
     steps: its average launch duration from the CUDA events recorded around
     it inside the iteration's graph (on the library's stream), and its
     algorithmic instruction count = point-bins processed (device-side count of
-    jcut+1 per evaluation) x the binding pipe's instructions per point-bin."""
+    jcut+1 per evaluation) x the binding pipe's instructions per point-bin
+    (the count frozen for the degree-7 tiles); beside it the fraction at the
+    count the kernel executes (degree 3 on the bins counted in pbins_lo)."""
     ms = kern[3] / steps
     pb = pbins / steps
     frac, pipe = mixed_roofline(pb, ms / 1e3, n_det, tile)
@@ -337,7 +347,18 @@ def mixed_slice_roofline(kern, pbins, evals, steps, n_det, tile, step_kernel_ms)
             "peak_source": "derived (not measured): 128 FP32 / 16 MUFU lanes/clk/SM x 152 SMs x 2070 MHz",
             "per_launch": {"ms": ms, "evals": evals / steps, "point_bins": pb,
                            "instr_per_point_bin": per_pb, "tile": tile,
-                           "share_of_step_kernels": kern[3] / step_kernel_ms if step_kernel_ms else None}}
+                           "share_of_step_kernels": kern[3] / step_kernel_ms if step_kernel_ms else None},
+            "at_executed_count": executed_roofline(pb, pbins_lo / steps, ms / 1e3, n_det, tile, pipe)}
+
+
+def executed_roofline(pb, pb_lo, seconds, n_det, tile, pipe):
+    """The FP32 fraction at the instruction count the kernel executes (fewer
+    than the frozen count on the bins of the low-degree tile groups)."""
+    if pipe != "FP32":
+        return None
+    per = executed_count(pb, pb_lo, n_det, tile)
+    return {"instr_per_point_bin": per, "low_degree_share": pb_lo / pb if pb else 0.0,
+            "achieved": pb * per / seconds / 1e12, "frac": pb * per / seconds / FP32_LANE_OPS}
 
 
 def time_to_logz_from(sp, blob):
@@ -370,7 +391,7 @@ def fp64_first_iteration(g, w, inputs, stream, flush):
     import torch
     sp = sampler_on(g, w, inputs, g.NS_FP64, stream)
     blob = sp.checkpoint()
-    ms, ev, pb, kern = timed_first_iterations(sp, blob, stream, 1, flush)
+    ms, ev, pb, kern, _ = timed_first_iterations(sp, blob, stream, 1, flush)
     sp.close()
     t = sum(ms) / 1e3
     return {"evals_per_s": ev / t, "ms_per_step": sum(ms), "evals": ev, "point_bins_per_s": pb / t,
@@ -425,13 +446,15 @@ def mixed_likelihood_roofline(g, stream):
     for the mixed rows of the table)."""
     r = batch_eval_row(g, "c4", g.NS_MIXED, stream, points=8192, reps=3)
     peak = FP32_LANE_OPS if r["pipe"] == "FP32" else SFU_LANE_OPS
+    at_exec = executed_roofline(r["point_bins"], r["point_bins_lo"], r["seconds"], 3, r["mixed_tile"], r["pipe"])
     return {"workload": "c4: 3 detectors, 20-2048 Hz at df=1/256 (519,169 bins), 8192 prior draws, "
                         "mixed precision, 128-bin tiles", "kernel": "k_eval<MIXED,3 det>",
             "evals_per_s": r["batch_evals_per_s"], "point_bins_per_s": r["point_bins_per_s"],
             "bound": r["pipe"], "frac": r["frac"], "peak_lane_ops_per_s": peak,
             "instr_per_point_bin": (mixed_fp32_per_point_bin(3, r["mixed_tile"]) if r["pipe"] == "FP32"
                                     else mixed_mufu_per_point_bin(3, r["mixed_tile"])),
-            "peak_source": "derived (not measured): 128 FP32 / 16 MUFU lanes/clk/SM x 152 SMs x 2070 MHz"}
+            "peak_source": "derived (not measured): 128 FP32 / 16 MUFU lanes/clk/SM x 152 SMs x 2070 MHz",
+            "at_executed_count": at_exec}
 
 
 def time_to_logz(g, w, precision, stream):
@@ -690,6 +713,10 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+# Horner steps the Taylor degree 3 saves per bin against degree 7 (C_4..C_7)
+LOW_DEGREE_SAVING = 4.0
+
+
 def mixed_fp32_per_point_bin(n_det: int, tile: int) -> float:
     """FP32 instructions of the mixed form per point-bin (per-tile or per-flush
     work not counted). Tiles of 32 bins or more: x and x^2 (2), C_1 x as an
@@ -813,7 +840,8 @@ def batch_eval_row(g, name, precision, stream, points=2048, reps=3, warps=0):
     sp.close()
     pb = st1["batch_point_bins"] - st0["batch_point_bins"]
     row = {"config": name, "form": "fp64" if precision == g.NS_FP64 else "mixed", "batch_points": points,
-           "warps_per_point": warps or None,
+           "warps_per_point": warps or None, "seconds": t, "point_bins": pb,
+           "point_bins_lo": st1["batch_point_bins_lo"] - st0["batch_point_bins_lo"],
            "batch_evals_per_s": points * reps / t, "point_bins_per_s": pb / t, "bins_per_eval": pb / (points * reps)}
     if precision == g.NS_FP64:
         row["frac"], row["pipe"] = pb * fp64_flops_per_point_bin(w.n_det) / t / (FP64_PEAK_TFLOPS * 1e12), "FP64"

@@ -238,6 +238,10 @@ typedef struct {
     long long scratch_bytes;     /* device bytes of the context's staging scratch, allocated by the
                                     host-buffer entry points (ns_eval_lnl_host, ns_waveform,
                                     ns_result with theta) on first use and when a call needs more */
+    long long point_bins_lo;       /* of point_bins, the bins of the mixed tiled form's tile groups
+                                      summed at the low Taylor degree (work-shared update) */
+    long long batch_point_bins_lo; /* of batch_point_bins, the same (mixed batched likelihood on
+                                      grids above 262,144 bins) */
 } ns_stats;
 
 int ns_get_stats(ns_ctx *ctx, ns_stats *st);

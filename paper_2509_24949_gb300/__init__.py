@@ -77,7 +77,8 @@ class _Stats(ctypes.Structure):
                 ("n_live", ctypes.c_int), ("n_dead", ctypes.c_int), ("point_bins", ctypes.c_longlong),
                 ("status", ctypes.c_int), ("kernel_ms", ctypes.c_double * 5), ("mixed_tile", ctypes.c_int),
                 ("batch_evals", ctypes.c_longlong), ("batch_point_bins", ctypes.c_longlong),
-                ("scratch_bytes", ctypes.c_longlong)]
+                ("scratch_bytes", ctypes.c_longlong),
+                ("point_bins_lo", ctypes.c_longlong), ("batch_point_bins_lo", ctypes.c_longlong)]
 
 
 class _ServerOptions(ctypes.Structure):

@@ -264,6 +264,8 @@ StepArgs step_args(ns_ctx *c, int k) {
     // test of the timeout path: the owner waits for one chunk more than its round has,
     // the bounded wait runs out and ns_step reports NS_ERR_TIMEOUT (no GPU fault or hang)
     A.ws_test_extra = ws ? c->ws_test_extra : 0;
+    // the work-shared update sums the groups from T.g_lo at the low Taylor degree
+    A.lo_bin = (ws && c->M.tlg && c->T.g_lo < 0x7fffffff) ? (long long)c->T.g_lo << (c->M.tlg + 5) : (1LL << 62);
     return A;
 }
 
@@ -712,6 +714,8 @@ int ns_get_stats(ns_ctx *c, ns_stats *st) {
     st->mixed_tile = c->M.tlg ? 1 << c->M.tlg : 0;
     st->batch_evals = (long long)s.eval_points;
     st->batch_point_bins = (long long)s.eval_point_bins;
+    st->point_bins_lo = (long long)s.point_bins_lo;
+    st->batch_point_bins_lo = (long long)s.eval_point_bins_lo;
     st->scratch_bytes = (long long)c->scratch_bytes;
     return NS_OK;
 }

@@ -28,6 +28,8 @@ struct RunState {
     unsigned long long walk_acc;     // random-walk kernel: accepted moves of this iteration's walks
     unsigned long long eval_points;      // points through the batched likelihood (k_eval)
     unsigned long long eval_point_bins;  // their sum of (jcut + 1)
+    unsigned long long point_bins_lo;       // of point_bins, those in tile groups at the Taylor degree TK_LO
+    unsigned long long eval_point_bins_lo;  // of eval_point_bins, the same
 };
 
 // Work-shared slice update (mixed precision, fine tiled grids): one slot per
@@ -73,6 +75,8 @@ struct StepArgs {
     double *ws_part;
     int ws_nslot, ws_gchunk, ws_maxchunk;
     int ws_test_extra;    // test hook: chunks the owner waits for beyond its round's (0 in use)
+    long long lo_bin;     // first bin of the tile groups this launch sums at the Taylor degree TK_LO
+                          // (bin accounting only; past every grid when none)
 };
 
 // One analysis' iteration arguments, for the multi-analysis launches.

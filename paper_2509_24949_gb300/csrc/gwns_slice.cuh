@@ -141,7 +141,14 @@ __global__ void __launch_bounds__(W * 32) k_eval(Model M, Tables T, const double
             logl[i0 + p] = lval;
             if (st) {
                 atomicAdd(&st->eval_points, 1ull);
-                if (M.model != M_TOY) atomicAdd(&st->eval_point_bins, (unsigned long long)(coef[p].jcut + 1));
+                if (M.model != M_TOY) {
+                    atomicAdd(&st->eval_point_bins, (unsigned long long)(coef[p].jcut + 1));
+                    // the rotation form here sums the groups from T.g_lo at the low Taylor degree
+                    if (PREC == 1 && M.tlg >= 5) {
+                        const long long lo = (long long)coef[p].jcut + 1 - ((long long)T.g_lo << (M.tlg + 5));
+                        if (lo > 0) atomicAdd(&st->eval_point_bins_lo, (unsigned long long)lo);
+                    }
+                }
             }
         }
         __syncthreads();    // red and lval serve the next point
@@ -284,13 +291,19 @@ struct Chain {
     double lx, a, b;
     int s, phase, nl, nr, nsh, caps, left_done, right_done;
     long long evals;
-    unsigned long long bins;
+    unsigned long long bins, bins_lo;   // bins read by the consumed evaluations; of those, in low-degree groups
     // cache of evaluated, not yet consumed candidates
     int ncache;
     int ckind[CACHE_MAX], cidx[CACHE_MAX], cbins[CACHE_MAX];
     double cval[CACHE_MAX];
     double cy[CACHE_MAX];      // random walk: the evaluated proposal (lane's coordinate)
 };
+
+// A consumed evaluation's bins (jcut + 1 of them): all, and those at or past lo_bin.
+__device__ __forceinline__ void count_bins(Chain &c, int bins, long long lo_bin) {
+    c.bins += (unsigned long long)bins;
+    if ((long long)bins > lo_bin) c.bins_lo += (unsigned long long)((long long)bins - lo_bin);
+}
 
 // Lane i's coordinate of the candidate x + t e (lanes >= d: 0.5, inside the
 // box); periodic coordinates wrap into [0, 1).
@@ -403,7 +416,7 @@ static __device__ void chain_run(const Model &M, const StepArgs &A, Chain &c, in
             if (ci < 0) return;
             const bool in = c.cval[ci] > lstar;
             c.evals++;
-            c.bins += (unsigned long long)c.cbins[ci];
+            count_bins(c, c.cbins[ci], A.lo_bin);
             cache_drop(c, ci);
             if (left) { if (in) { c.a -= 1.0; c.nl++; } else end_side(c, true); }
             else { if (in) { c.b += 1.0; c.nr++; } else end_side(c, false); }
@@ -423,7 +436,7 @@ static __device__ void chain_run(const Model &M, const StepArgs &A, Chain &c, in
             if (ci < 0) return;
             const double val = c.cval[ci];
             c.evals++;
-            c.bins += (unsigned long long)c.cbins[ci];
+            count_bins(c, c.cbins[ci], A.lo_bin);
             cache_drop(c, ci);
             if (val > lstar) {
                 c.x = y;
@@ -544,7 +557,7 @@ static __device__ void walk_run(const Model &M, const StepArgs &A, Chain &c, int
         }
         const double val = c.cval[ci];
         c.evals++;
-        c.bins += (unsigned long long)c.cbins[ci];
+        count_bins(c, c.cbins[ci], A.lo_bin);
         cache_drop(c, ci);
         if (val > lstar) {
             c.x = y;
@@ -827,7 +840,7 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
         for (int j = 0; j < MAXD; j++) c.lrow[j] = (lane < d && j < d) ? A.chol[lane * d + j] : 0.0;
         c.e = 0.0; c.a = 0.0; c.b = 0.0;
         c.s = 0; c.phase = A.kernel == 1 ? PH_WALK : PH_NEWSTEP; c.nl = c.nr = c.nsh = 0; c.caps = 0;
-        c.evals = 0; c.bins = 0;
+        c.evals = 0; c.bins = 0; c.bins_lo = 0;
         c.left_done = c.right_done = 0; c.ncache = 0;
         if (lane == 0) e_next_step = -1;
     }
@@ -1070,6 +1083,7 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
             atomicAdd(&A.state->evals, (unsigned long long)c.evals);
             atomicAdd(&A.state->caps, (unsigned long long)c.caps);
             atomicAdd(&A.state->point_bins, c.bins);
+            atomicAdd(&A.state->point_bins_lo, c.bins_lo);
             if (A.kernel == 1) atomicAdd(&A.state->walk_acc, (unsigned long long)c.s);
         }
     }

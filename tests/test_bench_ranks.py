@@ -85,3 +85,18 @@ def test_both_arms_describe_the_same_configuration():
     import bench
     assert bench.config_dict(1) == bench.config_dict(1)
     assert bench.config_dict(2)["parallelism"] == "replicas2"
+
+
+def test_executed_count_drops_the_low_degree_horner_steps():
+    """The executed FP32 count per point-bin is the frozen one (rotation form,
+    degree-7 tiles) on bins of degree-7 groups and 4 fewer on bins of the
+    degree-3 groups, weighted by their share."""
+    import bench
+    frozen = bench.mixed_fp32_per_point_bin(3, 128)
+    assert frozen == 37.5
+    assert bench.executed_count(1000, 0, 3, 128) == frozen
+    assert bench.executed_count(1000, 1000, 3, 128) == frozen - 4.0
+    assert abs(bench.executed_count(1000, 250, 3, 128) - (frozen - 1.0)) < 1e-12
+    r = bench.executed_roofline(1e10, 5e9, 0.01, 3, 128, "FP32")
+    assert abs(r["frac"] - 1e10 * (frozen - 2.0) / 0.01 / bench.FP32_LANE_OPS) < 1e-12
+    assert bench.executed_roofline(1e10, 5e9, 0.01, 3, 16, "SFU") is None

@@ -649,18 +649,62 @@ def test_mixed_form_choice(gw, name, over, tile):
 
 def test_mixed_wide_ctas_on_the_largest_grid(gw):
     """The 519,169-bin grid runs the work-shared mixed slice update (8-warp
-    persistent CTAs; 128-bin tiles by rotation, in chunks of four tile groups
+    persistent CTAs; 128-bin tiles by rotation, in chunks of two tile groups
     computed by the chain's own CTA and by the CTAs left without a chain, here
-    almost all of them): live points after one iteration agree with the oracle
-    per point, and no bounded wait gave up."""
+    almost all of them; the groups above 276 Hz at Taylor degree 3): live points
+    after one iteration agree with the oracle per point, no bounded wait gave
+    up, and the update counted bins at the low degree."""
     w, pb, th = problem("c4")
     with sampler_from(gw, pb, 1, n_live=24, k=12, steps_per_dim=1, seed=11) as sp:
         assert sp.stats()["mixed_tile"] == 128
+        s0 = sp.stats()
         sp.step()
         u, l = sp.live()
-        assert sp.stats()["status"] == 0
+        s1 = sp.stats()
+        assert s1["status"] == 0
+    pbins, lo = s1["point_bins"] - s0["point_bins"], s1["point_bins_lo"] - s0["point_bins_lo"]
+    assert 0 < lo < pbins
     want = pb.loglike(u)
     assert np.max(np.abs(l - want)) < MIXED_ATOL
+
+
+def _low_degree_first_bin(w, tile):
+    """First bin of the first 32-tile group whose degree-3 Taylor remainder
+    passes the tiled form's bound at the group's lowest frequency f_g:
+    64 (3/128) (pi T_sun Mc_lo f_g)^(-5/3) (h / f_g)^4 <= 1e-8, h half a tile."""
+    tsun = 4.925490947641267e-6
+    gb, h = 32 * tile, 0.5 * tile * w.df
+    ng = -(-w.N // gb)
+    for g in range(ng):
+        f = w.f0 + g * gb * w.df
+        phin = 3.0 / 128.0 * (np.pi * tsun * w.lo[0] * f) ** (-5.0 / 3.0)
+        if 64.0 * phin * (h / f) ** 4 <= 1e-8:
+            return g * gb
+    return ng * gb
+
+
+def test_low_degree_bins_are_counted(gw):
+    """The mixed batched likelihood on the 519,169-bin grid sums the tile groups
+    from 276 Hz up at Taylor degree 3 and counts their bins: per point, the bins
+    from that group's first bin up to its f_ISCO cutoff (from the oracle), and
+    in all the bins up to the cutoff."""
+    w, pb, th = problem("c4")
+    u = gi.unit_cube(29, 64, pb.dim)
+    theta = pb.theta(u)
+    f = w.f0 + np.arange(w.N) * w.df
+    jcut = np.array([np.searchsorted(f, oracle.fisco(t), side="right") - 1 for t in theta])
+    lo_bin = _low_degree_first_bin(w, 128)
+    assert abs(w.f0 + lo_bin * w.df - 276.0) < 1e-9
+    with sampler_from(gw, pb, 1, n_live=8) as sp:
+        assert sp.stats()["mixed_tile"] == 128
+        s0 = sp.stats()
+        got = sp.eval_lnl(u)
+        s1 = sp.stats()
+    assert s1["batch_point_bins"] - s0["batch_point_bins"] == int(np.sum(jcut + 1))
+    want_lo = int(np.sum(np.maximum(jcut + 1 - lo_bin, 0)))
+    assert 0 < want_lo < int(np.sum(jcut + 1))
+    assert s1["batch_point_bins_lo"] - s0["batch_point_bins_lo"] == want_lo
+    assert np.max(np.abs(got - pb.loglike(u))) < MIXED_ATOL
 
 
 def test_work_shared_wait_timeout_is_reported(gw, monkeypatch):
