@@ -805,10 +805,15 @@ def table_row(g, name, precision, stream, max_steps=100000, coarse=False):
         pipe = "FP64"
     else:
         frac, pipe = mixed_roofline(pb, slice_ms / 1e3, w.n_det, st1["mixed_tile"])
+    exe = None
+    if not coarse and precision != g.NS_FP64 and pb:
+        exe = executed_roofline(pb, st1["point_bins_lo"] - st0["point_bins_lo"], slice_ms / 1e3, w.n_det,
+                                st1["mixed_tile"], pipe)
     return {"config": name + (" (1024 coarse bins)" if coarse else ""),
             "form": "fp64" if precision == g.NS_FP64 else "mixed", "iterations": it, "done": done,
             "evals": ev, "evals_per_s": ev / (sum(ms) / 1e3), "point_bins_per_s": pb / (sum(ms) / 1e3),
             "bins_per_eval": pb / max(ev, 1), "k_slice_frac": frac, "k_slice_pipe": pipe,
+            "k_slice_at_executed_count": exe,
             "mixed_tile": st1["mixed_tile"] if precision != g.NS_FP64 and not coarse else None,
             "time_to_logZ_s": (t2 - t1) if done else None, "setup_s": setup_s,
             "p50_step_ms": float(np.percentile(ms, 50)), "p99_step_ms": float(np.percentile(ms, 99)),

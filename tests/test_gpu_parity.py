@@ -683,6 +683,31 @@ def _low_degree_first_bin(w, tile):
     return ng * gb
 
 
+def test_every_group_at_the_low_degree(gw):
+    """A 519,169-bin grid from 300 Hz (injection at SNR 6): the degree-3 bound
+    already passes at f0, so every tile group of the batched likelihood and of
+    the work-shared update takes degree 3. Per-point log L against the oracle,
+    for prior draws and for the live set after one iteration; every counted bin
+    is a low-degree bin."""
+    w, pb, th = problem("c4", f0=300.0, snr=6.0)
+    assert _low_degree_first_bin(w, 128) == 0
+    u = gi.unit_cube(31, 16, pb.dim)
+    with sampler_from(gw, pb, 1, n_live=24, k=12, steps_per_dim=1, seed=5) as sp:
+        assert sp.stats()["mixed_tile"] == 128
+        s0 = sp.stats()
+        got = sp.eval_lnl(u)
+        s1 = sp.stats()
+        assert s1["batch_point_bins_lo"] - s0["batch_point_bins_lo"] == \
+            s1["batch_point_bins"] - s0["batch_point_bins"] > 0
+        sp.step()
+        s2 = sp.stats()
+        assert s2["status"] == 0
+        assert s2["point_bins_lo"] - s1["point_bins_lo"] == s2["point_bins"] - s1["point_bins"] > 0
+        uu, l = sp.live()
+    assert np.max(np.abs(got - pb.loglike(u))) < MIXED_ATOL
+    assert np.max(np.abs(l - pb.loglike(uu))) < MIXED_ATOL
+
+
 def test_low_degree_bins_are_counted(gw):
     """The mixed batched likelihood on the 519,169-bin grid sums the tile groups
     from 276 Hz up at Taylor degree 3 and counts their bins: per point, the bins
