@@ -388,6 +388,26 @@ static int validate(const ns_prior *prior, const ns_data *data, const ns_psd *ps
 // passes, up to 128 bins, is taken: it amortises the per-tile anchor best
 // (GB300, 519,169 bins: degree 6 on 64-bin tiles against degree 7 on 128-bin
 // tiles, batched likelihood 1.53 -> 1.59 M evals/s, slice update 326 -> 304 ms).
+// A double as a double-float: the nearest float, then the nearest float to the rest.
+static gwns::dfl host_df(double x) {
+    const float h = (float)x;
+    return gwns::dfl{h, (float)(x - (double)h)};
+}
+
+// The mixed form takes its per-point coefficients in double-float on the FP32
+// pipe (point_coef_group_mx) unless it uses relative binning or a parameter
+// other than the distance has a uniform-in-volume prior (which needs a cube
+// root). GWNS_COEF_FP64=1 keeps the FP64 stage and its conversion instead (the
+// two are compared by the GPU tests).
+static bool use_df_coefficients(const ns_ctx *c) {
+    const Model &M = c->M;
+    if (M.model != M_GW || c->precision != NS_MIXED || M.rb) return false;
+    for (int p = 0; p < NS_NPARAM; p++)
+        if (M.kind[p] == K_VOLUME && p != NS_DL) return false;
+    const char *f = std::getenv("GWNS_COEF_FP64");
+    return !(f && f[0] == '1');
+}
+
 static void choose_tiles(Model &M) {
     M.tlg = 0;
     M.np = M.N;
@@ -521,6 +541,13 @@ int ns_init(ns_ctx **out, const ns_prior *prior, const ns_data *data, const ns_p
                 M.pspan[p] = hi - lo;
             }
         }
+        // double-float copies for the mixed form's coefficient stage
+        for (int p = 0, i = 0; p < NS_NPARAM; p++) {
+            M.uidx[p] = M.kind[p] == K_FIXED ? 0 : i++;
+            M.pbase_x[p] = host_df(M.pbase[p]);
+            M.pspan_x[p] = M.kind[p] == K_FIXED ? gwns::dfl{0.0f, 0.0f} : host_df(M.pspan[p]);
+        }
+        M.df_x = host_df(M.df);
         // large grids: the mixed slice update shares each bin's table loads among
         // the round's candidates (measured faster from ~16k bins on GB300)
         M.coop = M.N >= 16384 ? 1 : 0;
@@ -611,6 +638,7 @@ int ns_init(ns_ctx **out, const ns_prior *prior, const ns_data *data, const ns_p
     c->T.wt = c->X.wt;
     c->T.g_lo = low_degree_group(c->M);
     if (c->rb_B > 0 && (rc = build_rb(c))) { ns_free(c); return rc; }
+    c->M.cdf = use_df_coefficients(c) ? 1 : 0;
     RunState s0;
     std::memset(&s0, 0, sizeof(s0));
     s0.logZ = -INFINITY;

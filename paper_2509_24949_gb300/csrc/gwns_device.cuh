@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "gwns_df.cuh"
 #include "gwns_tables.cuh"
 
 namespace gwns {
@@ -55,6 +56,13 @@ struct Model {
     double pos[MAXDET][3], xarm[MAXDET][3], yarm[MAXDET][3];
     // toy: x = toy_lo + (toy_hi - toy_lo) u, Sigma_ij = rho^|i-j|
     double toy_lo, toy_hi, toy_rho, toy_lognorm;
+    // mixed form's coefficient stage in double-float (cdf = 1): parameter p is
+    // pbase_x[p] + pspan_x[p] u[uidx[p]] (a fixed parameter: its value and a
+    // zero span), df_x the bin spacing
+    int cdf;
+    int uidx[NPARAM];
+    dfl pbase_x[NPARAM], pspan_x[NPARAM];
+    dfl df_x;
 };
 
 // Relative-binning (heterodyned) tables: coarse bins between grid indices
@@ -258,17 +266,21 @@ __device__ __forceinline__ int cutoff_index_tab(const Model &M, const double *f6
 // 1; phi_2; phi_3 without spin; phi_4 without spin; phi_5 without spin (the
 // ln v part of the 2.5PN term, 3 ln v = 3 ln a + ln f); phi_6 without its log
 // term; the f^1/3 ln f part -6848/63 of the 3PN log; phi_7.
-__device__ const double PN_POLY[NB * 4] = {
-    1.0, 0.0, 0.0, 0.0,
-    3715.0 / 756.0, 55.0 / 9.0, 0.0, 0.0,
-    -16.0 * PI_D, 0.0, 0.0, 0.0,
-    15293365.0 / 508032.0, 27145.0 / 504.0, 3085.0 / 72.0, 0.0,
-    PI_D * 38645.0 / 756.0, -PI_D * 65.0 / 9.0, 0.0, 0.0,
-    11583231236531.0 / 4694215680.0 - 640.0 / 3.0 * PI_D * PI_D - 6848.0 / 21.0 * GAMMA_E,
-    -15737765635.0 / 3048192.0 + 2255.0 / 12.0 * PI_D * PI_D, 76055.0 / 1728.0, -127825.0 / 1296.0,
-    -6848.0 / 63.0, 0.0, 0.0, 0.0,
-    PI_D * 77096675.0 / 254016.0, PI_D * 378515.0 / 1512.0, -PI_D * 74045.0 / 756.0, 0.0,
-};
+#define GWNS_PN_POLY(F)                                                                          \
+    F(1.0), F(0.0), F(0.0), F(0.0),                                                              \
+    F(3715.0 / 756.0), F(55.0 / 9.0), F(0.0), F(0.0),                                            \
+    F(-16.0 * PI_D), F(0.0), F(0.0), F(0.0),                                                     \
+    F(15293365.0 / 508032.0), F(27145.0 / 504.0), F(3085.0 / 72.0), F(0.0),                      \
+    F(PI_D * 38645.0 / 756.0), F(-PI_D * 65.0 / 9.0), F(0.0), F(0.0),                            \
+    F(11583231236531.0 / 4694215680.0 - 640.0 / 3.0 * PI_D * PI_D - 6848.0 / 21.0 * GAMMA_E),    \
+    F(-15737765635.0 / 3048192.0 + 2255.0 / 12.0 * PI_D * PI_D), F(76055.0 / 1728.0),            \
+    F(-127825.0 / 1296.0),                                                                       \
+    F(-6848.0 / 63.0), F(0.0), F(0.0), F(0.0),                                                   \
+    F(PI_D * 77096675.0 / 254016.0), F(PI_D * 378515.0 / 1512.0), F(-PI_D * 74045.0 / 756.0), F(0.0)
+#define GWNS_AS_DOUBLE(x) (x)
+__device__ const double PN_POLY[NB * 4] = {GWNS_PN_POLY(GWNS_AS_DOUBLE)};
+// the same as double-floats, for the mixed form's coefficient stage
+__device__ const dfl PN_POLY_X[NB * 4] = {GWNS_PN_POLY(DFC)};
 
 // Per-point coefficients, computed by lane groups of 8: group g of the calling
 // warp handles point g (g < count), so one warp computes up to four points at
@@ -531,6 +543,197 @@ __device__ __forceinline__ void coef_to_mixed_warp(const Coef &c, int n_det, dou
         m->eps8[d][0] = -2.0f * h4 * h4;
         m->eps8[d][1] = -sinf(8.0f * b);
     }
+}
+
+// Mixed form: the coefficients of up to four unit-cube points (lane groups of
+// 8, as point_coef_group) in double-float on the FP32 pipe, written straight
+// into the mixed view (phase coefficients and constant in turns, delays in
+// seconds, as (hi, lo) floats; the per-bin delay phase; with rot, the tiled
+// form's rotation constants) and into the FP64 fields the log L combine reads
+// (G_d, <h|h>, jcut, amp, fisco). The steps and the lane packing are those of
+// point_coef_group: the prior transform (here lane-parallel, one parameter per
+// sub-lane), one packed log (ln eta, ln T_Mc, ln D_L), one packed exp (a, 1/a,
+// 1/(pi T_M), 3/(128 eta), the amplitude), one basis coefficient per sub-lane,
+// one packed sine/cosine (RA, psi) and the detector terms on sub-lanes
+// 0 .. n_det-1. Same halves: 1 mass and phase, 2 sky and detectors (G_d without
+// the amplitude, joined by point_coef_join), 0 both. GW model, uniform priors
+// and a uniform-in-volume distance (Model::cdf); all 32 lanes must call.
+__device__ __forceinline__ dfl shfl_df(dfl v, int src) {
+    return dfl{__shfl_sync(0xffffffffu, v.h, src, 8), __shfl_sync(0xffffffffu, v.l, src, 8)};
+}
+
+__device__ inline void point_coef_group_mx(const Model &M, const Tables &T, const double *u0, int ustride,
+                                           Coef *out0, CoefMixed *cm0, int count, bool rot, int half = 0) {
+    const int lane = threadIdx.x & 31, g = lane >> 3, sl = lane & 7;
+    const bool writer = g < count;
+    const double *u = u0 + (writer ? g : 0) * ustride;
+    Coef *out = out0 + (writer ? g : 0);
+    CoefMixed *cm = cm0 + (writer ? g : 0);
+    // prior transform: sub-lane s forms parameters s and s + 8
+    dfl thp[2];
+#pragma unroll
+    for (int r = 0; r < 2; r++) {
+        const int p = sl + 8 * r < NPARAM ? sl + 8 * r : 0;
+        const dfl ux = df_from_double(u[M.uidx[p]]);
+        thp[r] = df_add(df_mul(M.pspan_x[p], ux), M.pbase_x[p]);
+    }
+    auto TH = [&](int p) { return shfl_df(p < 8 ? thp[0] : thp[1], p & 7); };
+    const dfl one = dfl{1.0f, 0.0f};
+    dfl amp = dfl{0.0f, 0.0f};
+    int jcut = -1;
+    // mass and phase part (half 0 or 1)
+    if (half != 2) {
+        const dfl q = TH(P_Q), c1 = TH(P_CHI1), c2 = TH(P_CHI2);
+        const dfl mc = TH(P_MC), dlx = TH(P_DL), phic = TH(P_PHIC);
+        const dfl r1q = df_rcp(df_add_f(q, 1.0f));
+        const dfl eta = df_mul(q, df_sqr(r1q));                     // m1 m2 / M^2
+        const dfl delta = df_mul(df_sub(one, q), r1q);              // (m1 - m2)/M
+        const dfl chis = df_scale(df_add(c1, c2), 0.5f);
+        const dfl chia = df_scale(df_sub(c1, c2), 0.5f);
+        const dfl tmc = df_mul(mc, DFC(TSUN));
+        // packed log: sub-lane 0 ln(eta), 1 ln(T_Mc), others ln(D_L) (or of D_L^3)
+        const dfl lg = df_log(sl == 0 ? eta : (sl == 1 ? tmc : dlx));
+        const dfl ln_eta = shfl_df(lg, 0), ln_tmc = shfl_df(lg, 1), ln_dlx = shfl_df(lg, 2);
+        const dfl ln_dl = M.kind[P_DL] == K_VOLUME ? df_mul(ln_dlx, DFC(1.0 / 3.0)) : ln_dlx;
+        // ln(pi T_M) with T_M = T_Mc eta^(-3/5); a = (pi T_M)^(1/3), v = a f^(1/3)
+        const dfl ln_x = df_add(df_add(DFC(1.1447298858494002), ln_tmc), df_mul(ln_eta, DFC(-0.6)));
+        const dfl ln_a = df_mul(ln_x, DFC(1.0 / 3.0));
+        // packed exp: 0 a, 1 1/a, 2 1/(pi T_M), 3 K = 3/(128 eta),
+        // others A = sqrt(5/24) pi^(-2/3) c T_Mc^(5/6) / D_L (D_L in Mpc)
+        const dfl ex_arg = sl == 0 ? ln_a
+                         : sl == 1 ? df_neg(ln_a)
+                         : sl == 2 ? df_neg(ln_x)
+                         : sl == 3 ? df_sub(DFC(-3.7534179752515073), ln_eta)
+                         : df_sub(df_add(DFC(-33.81250354619071), df_mul(ln_tmc, DFC(5.0 / 6.0))), ln_dl);
+        const dfl ex = df_exp(ex_arg);
+        const dfl a = shfl_df(ex, 0), ia = shfl_df(ex, 1), inv_pitm = shfl_df(ex, 2), K = shfl_df(ex, 3);
+        amp = shfl_df(ex, 4);
+        // f_ISCO = 1/(6^(3/2) pi T_M); the cutoff index against the FP64 frequency table
+        const double fisco = df_to_double(df_mul(inv_pitm, DFC(0.06804138174397717)));
+        jcut = cutoff_index_tab(M, T.f64, fisco);
+        // TaylorF2 phasing: sub-lane m computes basis coefficient m = K a^e_m (P_m(eta) + s_m)
+        const dfl beta = df_mul(df_add(df_add(chis, df_mul(delta, chia)), df_mul(df_mul(eta, chis), DFC(-76.0 / 113.0))),
+                                DFC(113.0 / 12.0));
+        const dfl sigma = df_mul(df_mul(df_mul(eta, c1), c2), DFC(79.0 / 8.0));
+        const dfl gamma = df_add(
+            df_mul(df_add(df_add(DFC(732985.0 / 2268.0), df_mul(eta, DFC(-24260.0 / 81.0))),
+                          df_mul(df_sqr(eta), DFC(-340.0 / 9.0))), chis),
+            df_mul(df_mul(df_add(DFC(732985.0 / 2268.0), df_mul(eta, DFC(140.0 / 9.0))), delta), chia));
+        {
+            const int m = sl;
+            // |e_m| for e = (-5, -3, -2, -1, 0, 1, 1, 2); negative powers from 1/a
+            const int e = m == 0 ? 5 : m == 1 ? 3 : (m == 2 || m == 7) ? 2 : m == 4 ? 0 : 1;
+            const dfl base = m < 4 ? ia : a;
+            const dfl b2 = df_sqr(base);
+            dfl pw = (e & 1) ? base : one;
+            if (e & 2) pw = df_mul(pw, b2);
+            if (e & 4) pw = df_mul(pw, df_sqr(b2));
+            const float2 *pc = reinterpret_cast<const float2 *>(PN_POLY_X + 4 * m);
+            const float2 p0 = __ldg(pc), p1 = __ldg(pc + 1), p2 = __ldg(pc + 2), p3 = __ldg(pc + 3);
+            dfl poly = df_add(df_mul(dfl{p3.x, p3.y}, eta), dfl{p2.x, p2.y});
+            poly = df_add(df_mul(poly, eta), dfl{p1.x, p1.y});
+            poly = df_add(df_mul(poly, eta), dfl{p0.x, p0.y});
+            const dfl sp = m == 2 ? df_scale(beta, 4.0f)
+                         : m == 3 ? df_mul(sigma, DFC(-10.0))
+                         : m == 4 ? df_neg(gamma)
+                         : m == 5 ? df_mul(df_add(DFC(1.3862943611198906), ln_a), DFC(-6848.0 / 21.0))
+                                  : dfl{0.0f, 0.0f};
+            // in turns
+            const dfl am = df_mul(df_mul(df_mul(K, pw), df_add(poly, sp)), DFC(INV_TWO_PI_D));
+            if (writer) { cm->ah[m] = am.h; cm->al[m] = am.l; }
+        }
+        if (sl == 0 && writer) {
+            // constant: -phi_c - pi/4 + K phi5 (1 + 3 ln sqrt 6 + 3 ln a), in turns, reduced mod 1
+            const dfl phi5 = df_sub(df_add(DFC(PI_D * 38645.0 / 756.0), df_mul(eta, DFC(-PI_D * 65.0 / 9.0))), gamma);
+            const dfl lnf = df_add(DFC(1.0 + 3.0 * 0.8958797346140275), df_mul(ln_a, DFC(3.0)));
+            dfl c0 = df_sub(df_mul(df_mul(K, phi5), lnf), df_add(phic, DFC(0.25 * PI_D)));
+            c0 = df_mul(c0, DFC(INV_TWO_PI_D));
+            c0 = df_add_f(c0, -rintf(c0.h));
+            cm->c0h = c0.h;
+            cm->c0l = c0.l;
+            out->jcut = jcut;
+            out->fisco = fisco;
+            out->amp = df_to_double(amp);
+        }
+    }
+    // sky and detector part (half 0 or 2)
+    if (half == 1) return;
+    const dfl ci = TH(P_COSI), tc = TH(P_TC), sd = TH(P_SINDEC);
+    // packed sine and cosine: sub-lane 0 RA, others psi (both shuffled by every lane)
+    const dfl ra = TH(P_RA), psi = TH(P_PSI);
+    dfl sn, cs;
+    df_sincos(sl == 0 ? ra : psi, sn, cs);
+    const dfl sa = shfl_df(sn, 0), ca = shfl_df(cs, 0), sp = shfl_df(sn, 1), cp = shfl_df(cs, 1);
+    const int dd = sl < M.n_det ? sl : 0;
+    dfl qre, qim, dt = dfl{0.0f, 0.0f};
+    if (M.ideal) {
+        qre = df_scale(df_add_f(df_sqr(ci), 1.0f), 0.5f);
+        qim = dfl{0.0f, 0.0f};
+    } else {
+        const dfl cd = df_sqrt(df_sub(one, df_sqr(sd)));
+        // wave-frame basis X, Y (Anderson et al. 2001) and source direction n
+        const dfl X0 = df_sub(df_mul(sa, cp), df_mul(df_mul(sp, ca), sd));
+        const dfl X1 = df_neg(df_add(df_mul(ca, cp), df_mul(df_mul(sp, sa), sd)));
+        const dfl X2 = df_mul(sp, cd);
+        const dfl Y0 = df_neg(df_add(df_mul(sa, sp), df_mul(df_mul(cp, ca), sd)));
+        const dfl Y1 = df_sub(df_mul(ca, sp), df_mul(df_mul(cp, sa), sd));
+        const dfl Y2 = df_mul(cp, cd);
+        dfl x[3], y[3], r[3];
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            x[i] = df_from_double(M.xarm[dd][i]);
+            y[i] = df_from_double(M.yarm[dd][i]);
+            r[i] = df_from_double(M.pos[dd][i]);
+        }
+        // D = (x x^T - y y^T)/2
+        const dfl xX = df_add(df_add(df_mul(x[0], X0), df_mul(x[1], X1)), df_mul(x[2], X2));
+        const dfl xY = df_add(df_add(df_mul(x[0], Y0), df_mul(x[1], Y1)), df_mul(x[2], Y2));
+        const dfl yX = df_add(df_add(df_mul(y[0], X0), df_mul(y[1], X1)), df_mul(y[2], X2));
+        const dfl yY = df_add(df_add(df_mul(y[0], Y0), df_mul(y[1], Y1)), df_mul(y[2], Y2));
+        const dfl fp = df_scale(df_sub(df_sub(df_sqr(xX), df_sqr(yX)), df_sub(df_sqr(xY), df_sqr(yY))), 0.5f);
+        const dfl fc = df_sub(df_mul(xX, xY), df_mul(yX, yY));
+        const dfl rn = df_add(df_add(df_mul(df_mul(r[0], cd), ca), df_mul(df_mul(r[1], cd), sa)), df_mul(r[2], sd));
+        dt = df_mul(rn, DFC(-1.0 / C_SI));
+        qre = df_mul(fp, df_scale(df_add_f(df_sqr(ci), 1.0f), 0.5f));
+        qim = df_neg(df_mul(fc, ci));
+    }
+    const dfl tau = df_add(tc, dt);
+    const dfl tau0 = shfl_df(tau, 0);
+    if (sl < M.n_det && writer) {
+        cm->tauh[dd] = tau.h;
+        cm->taul[dd] = tau.l;
+        cm->dtau[dd] = df_mul(tau, M.df_x).h;
+        if (half == 2) {
+            out->gre[dd] = df_to_double(qre);
+            out->gim[dd] = -df_to_double(qim);
+        } else {
+            out->gre[dd] = df_to_double(df_mul(amp, qre));
+            out->gim[dd] = -df_to_double(df_mul(amp, qim));
+        }
+        if (rot) {
+            // the rotation of detector d's phase against detector 0's per bin, its
+            // unit, two-bin and eight-bin steps (FP32 libm sine: within 2 ulp)
+            const float b = df_mul(df_mul(df_sub(tau, tau0), M.df_x), DFC(TWO_PI_D)).h;
+            const float h1 = sinf(0.5f * b), h2 = sinf(b), h4 = sinf(4.0f * b);
+            cm->beta[dd] = b;
+            cm->rho[dd][0] = 1.0f - 2.0f * h1 * h1;
+            cm->rho[dd][1] = -h2;
+            cm->rho2[dd][0] = 1.0f - 2.0f * h2 * h2;
+            cm->rho2[dd][1] = -sinf(2.0f * b);
+            cm->eps8[dd][0] = -2.0f * h4 * h4;
+            cm->eps8[dd][1] = -sinf(8.0f * b);
+        }
+    }
+    if (half == 2) return;
+    double hh_part = 0.0;
+    if (sl < M.n_det && jcut >= 0) {
+        // A^2 (~1e-42) is below the float range: square the amplitude in FP64
+        const double a = df_to_double(amp);
+        hh_part = a * a * df_to_double(df_add(df_sqr(qre), df_sqr(qim))) * T.prefix[(size_t)dd * M.N + jcut];
+    }
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) hh_part += __shfl_xor_sync(0xffffffffu, hh_part, o, 8);
+    if (sl == 0 && writer) out->hh = hh_part;
 }
 
 // ------------------------------------------------------------ bin loops

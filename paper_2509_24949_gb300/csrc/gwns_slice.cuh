@@ -74,6 +74,10 @@ __device__ __forceinline__ void warp_point_coef(const Model &M, const Tables &T,
         point_coef_warp(M, T, in, coef);
         return;
     }
+    if (precision == 1 && M.cdf && !in_is_theta) {
+        point_coef_group_mx(M, T, in, 0, coef, cm, 1, M.tlg >= 5);
+        return;
+    }
     if (in_is_theta) {
         // a model whose parameters are all FIXED at theta
         Model Mt = M;
@@ -183,13 +187,20 @@ __global__ void __launch_bounds__(W * 32) k_eval_batch(Model M, Tables T, const 
     const int grp = W >= 2 ? warp >> 1 : warp;
     const bool lead = W >= 2 ? (warp & 1) == 0 : true;
     const int cnt = (grp < NG && 4 * grp < np) ? min(4, np - 4 * grp) : 0;
-    if (cnt > 0) point_coef_group(M, T, pt[4 * grp], MAXD, &coef[4 * grp], cnt, 0, W >= 2 ? 1 + (warp & 1) : 0);
+    if (cnt > 0) {
+        if (M.cdf)
+            point_coef_group_mx(M, T, pt[4 * grp], MAXD, &coef[4 * grp], &cm[4 * grp], cnt, M.tlg >= 5,
+                                W >= 2 ? 1 + (warp & 1) : 0);
+        else
+            point_coef_group(M, T, pt[4 * grp], MAXD, &coef[4 * grp], cnt, 0, W >= 2 ? 1 + (warp & 1) : 0);
+    }
     __syncthreads();
     if (cnt > 0 && lead) {
         if (W >= 2) point_coef_join(M, T, &coef[4 * grp], cnt);
         __syncwarp();
-        for (int p = 4 * grp; p < 4 * grp + cnt; p++)
-            coef_to_mixed_warp(coef[p], M.n_det, M.df, &cm[p], nullptr, M.tlg >= 5);
+        if (!M.cdf)
+            for (int p = 4 * grp; p < 4 * grp + cnt; p++)
+                coef_to_mixed_warp(coef[p], M.n_det, M.df, &cm[p], nullptr, M.tlg >= 5);
     }
     __syncthreads();
     for (int p = warp; p < np; p += W) {
@@ -889,8 +900,12 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
             const int grp = warp >> 1;
             if (4 * grp < ns && 2 * grp + 1 < W) {
                 const int cnt = ns - 4 * grp < 4 ? ns - 4 * grp : 4;
-                point_coef_group(M, T, ysh[4 * grp], MAXD, &coef[4 * grp], cnt, PREC == 0 ? 32 : 0,
-                                 1 + (warp & 1));
+                if (PREC == 1 && M.cdf)
+                    point_coef_group_mx(M, T, ysh[4 * grp], MAXD, &coef[4 * grp], &cm[4 * grp], cnt,
+                                        form_rot<FORM>(M), 1 + (warp & 1));
+                else
+                    point_coef_group(M, T, ysh[4 * grp], MAXD, &coef[4 * grp], cnt, PREC == 0 ? 32 : 0,
+                                     1 + (warp & 1));
             } else if (warp == W - 1 && A.kernel == 0) {
                 // a warp without coefficients computes the next slice step's direction
                 const int s1 = cur_step + 1;
@@ -909,7 +924,11 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
         } else {
             if (4 * warp < ns) {
                 const int cnt = ns - 4 * warp < 4 ? ns - 4 * warp : 4;
-                point_coef_group(M, T, ysh[4 * warp], MAXD, &coef[4 * warp], cnt, PREC == 0 ? 32 : 0);
+                if (PREC == 1 && M.cdf)
+                    point_coef_group_mx(M, T, ysh[4 * warp], MAXD, &coef[4 * warp], &cm[4 * warp], cnt,
+                                        form_rot<FORM>(M));
+                else
+                    point_coef_group(M, T, ysh[4 * warp], MAXD, &coef[4 * warp], cnt, PREC == 0 ? 32 : 0);
             }
             __syncthreads();
         }
@@ -928,7 +947,7 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
             // mixed, every warp on every candidate of the round: the tiled form
             // shares out the tile groups (two candidates per pass on one table
             // load), the per-bin form strides the bins
-            if (warp < ns) coef_to_mixed_warp(coef[warp], M.n_det, M.df, &cm[warp], nullptr, form_rot<FORM>(M));
+            if (warp < ns && !M.cdf) coef_to_mixed_warp(coef[warp], M.n_det, M.df, &cm[warp], nullptr, form_rot<FORM>(M));
             if (lane == 0 && warp < ns) jc[warp] = coef[warp].jcut;
             __syncthreads();
             if (WS) {
@@ -1032,7 +1051,7 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
                     v += coef[warp].gre[dd] * ZR - coef[warp].gim[dd] * ZI;
                 }
             } else if (M.tlg) {
-                coef_to_mixed_warp(coef[warp], M.n_det, M.df, &cm[warp], nullptr, form_rot<FORM>(M));
+                if (!M.cdf) coef_to_mixed_warp(coef[warp], M.n_det, M.df, &cm[warp], nullptr, form_rot<FORM>(M));
                 if (lane == 0) jc[warp] = coef[warp].jcut;
                 __syncwarp();
                 float zh[1][NDET][2], zl[1][NDET][2];
@@ -1046,7 +1065,7 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
                     v += coef[warp].gre[dd] * ZR - coef[warp].gim[dd] * ZI;
                 }
             } else {
-                coef_to_mixed_warp(coef[warp], M.n_det, M.df, &cm[warp], nullptr, form_rot<FORM>(M));
+                if (!M.cdf) coef_to_mixed_warp(coef[warp], M.n_det, M.df, &cm[warp], nullptr, form_rot<FORM>(M));
                 __syncwarp();
                 float zh[NDET][2], zl[NDET][2];
                 bins_mixed<NDET>(T, M.N, cm[warp], coef[warp].jcut, lane, 32, zh, zl);

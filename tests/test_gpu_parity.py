@@ -130,6 +130,38 @@ def test_lnl_full_size_sampled(gw, name, precision):
         assert abs(got_inj - want_inj) < MIXED_ATOL
 
 
+@pytest.mark.parametrize("name,over", [("c0", {}), ("c1", {}), ("c1", {"N": 8000, "df": 0.03125}),
+                                       ("c1", {"N": 3001, "df": 0.0625}),
+                                       ("c1", {"N": 12000, "df": 1 / 128, "n_det": 4}), ("c2", {})])
+def test_mixed_coefficients_double_float_against_fp64_stage(gw, name, over, monkeypatch):
+    """The mixed form's per-point coefficients in double-float on the FP32 pipe
+    (the default) against the FP64 stage and its conversion to (hi, lo) floats
+    (GWNS_COEF_FP64=1), on the per-bin form, the direct and the rotation tiled
+    forms: the same log L to within 1e-4, both within 1e-3 of the oracle, and
+    the same bins read (cutoff indices) point for point. The injection too."""
+    import torch
+    w, pb, th = problem(name, **over)
+    u = pts_for(pb, th, count=512)
+    want = pb.loglike(u)
+    got = {}
+    for mode in ("df", "fp64"):
+        if mode == "fp64":
+            monkeypatch.setenv("GWNS_COEF_FP64", "1")
+        else:
+            monkeypatch.delenv("GWNS_COEF_FP64", raising=False)
+        with sampler_from(gw, pb, 1, n_live=8) as sp:
+            st0 = sp.stats()
+            v = sp.eval_lnl(u)
+            st1 = sp.stats()
+            g_inj = sp.eval_lnl_theta(torch.tensor(th[None], dtype=torch.float64, device="cuda")).item()
+        got[mode] = (v, st1["batch_point_bins"] - st0["batch_point_bins"], g_inj)
+    (a, pa, ia), (b, pbn, ib) = got["df"], got["fp64"]
+    assert pa == pbn
+    assert np.max(np.abs(a - b)) < 1e-4, np.max(np.abs(a - b))
+    assert np.max(np.abs(a - want)) < MIXED_ATOL, np.max(np.abs(a - want))
+    assert abs(ia - ib) < MIXED_ATOL
+
+
 def test_lnl_device_pointer_path(gw):
     import torch
     w, pb, th = problem("c1")
