@@ -203,6 +203,7 @@ __global__ void __launch_bounds__(W * 32) k_eval_batch(Model M, Tables T, const 
                 coef_to_mixed_warp(coef[p], M.n_det, M.df, &cm[p], nullptr, M.tlg >= 5);
     }
     __syncthreads();
+    unsigned long long n_pts = 0, n_pb = 0;     // this warp's counts, added once at the end
     for (int p = warp; p < np; p += W) {
         double ZR[1] = {0.0}, ZI[1] = {0.0};      // lane d < NDET: detector d's sums
         if (M.tlg) {
@@ -240,11 +241,13 @@ __global__ void __launch_bounds__(W * 32) k_eval_batch(Model M, Tables T, const 
         if (lane == 0) {
             const double v = t - 0.5 * coef[p].hh;
             logl[i0 + p] = v;
-            if (st) {
-                atomicAdd(&st->eval_points, 1ull);
-                atomicAdd(&st->eval_point_bins, (unsigned long long)(coef[p].jcut + 1));
-            }
+            n_pts++;
+            n_pb += (unsigned long long)(coef[p].jcut + 1);
         }
+    }
+    if (st && lane == 0 && n_pts) {
+        atomicAdd(&st->eval_points, n_pts);
+        atomicAdd(&st->eval_point_bins, n_pb);
     }
 }
 
