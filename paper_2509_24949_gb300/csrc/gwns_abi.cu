@@ -395,15 +395,18 @@ static gwns::dfl host_df(double x) {
 }
 
 // The mixed form takes its per-point coefficients in double-float on the FP32
-// pipe (point_coef_group_mx) unless it uses relative binning or a parameter
-// other than the distance has a uniform-in-volume prior (which needs a cube
-// root). GWNS_COEF_FP64=1 keeps the FP64 stage and its conversion instead (the
-// two are compared by the GPU tests).
+// pipe (point_coef_group_mx) unless it uses relative binning, a parameter other
+// than the distance has a uniform-in-volume prior (which needs a cube root), or
+// the angles psi and RA range beyond +-100 rad (the double-float sine and cosine
+// reduce arguments below 2^7 pi/2). GWNS_COEF_FP64=1 keeps the FP64 stage and its
+// conversion instead (the two are compared by the GPU tests).
 static bool use_df_coefficients(const ns_ctx *c) {
     const Model &M = c->M;
     if (M.model != M_GW || c->precision != NS_MIXED || M.rb) return false;
     for (int p = 0; p < NS_NPARAM; p++)
         if (M.kind[p] == K_VOLUME && p != NS_DL) return false;
+    for (int p : {(int)NS_PSI, (int)NS_RA})
+        if (std::fabs(M.lo[p]) > 100.0 || std::fabs(M.hi[p]) > 100.0) return false;
     const char *f = std::getenv("GWNS_COEF_FP64");
     return !(f && f[0] == '1');
 }
