@@ -61,6 +61,12 @@ enum { NS_PRIOR_FIXED = 0, NS_PRIOR_UNIFORM = 1, NS_PRIOR_VOLUME = 2 };
 
 /* Inner kernels of the update (ns_options.kernel). */
 enum { NS_KERNEL_SLICE = 0, NS_KERNEL_WALK = 1 };
+/* Arithmetic of the likelihood (ns_options.precision). NS_FP64: FP64 throughout.
+ * NS_MIXED: per-point coefficients in double-float (pairs of floats on the FP32
+ * pipe; the FP64 stage instead when the environment variable GWNS_COEF_FP64=1 is
+ * set at ns_init, or for relative binning), the per-bin phase in double-float,
+ * FP32 sine/cosine and products with compensated sums, the final log L in FP64
+ * (paper Sec. 3's likelihood; the precision split is this library's). */
 enum { NS_FP64 = 0, NS_MIXED = 1 };
 enum { NS_MODEL_GW = 0, NS_MODEL_TOY = 1 };
 
