@@ -343,11 +343,15 @@ const char *ns_strerror(int code);
  * analysis each: prior, data, PSD, grid, options) are queued by ns_submit; each
  * ns_server_tick admits queued requests in arrival order while the number of
  * running analyses is below max_active and their estimated device footprint
- * fits the memory budget, then runs ONE nested-sampling iteration of every
- * running analysis with one launch per iteration kernel (the slice updates of
- * all their chains interleaved in the same launch), and retires the analyses
- * that reached their stopping rule (their evidence, error and samples are kept
- * on the host; their device memory is released). Every analysis keeps its own
+ * fits the memory budget, then iterates the running analyses with one launch
+ * per iteration kernel (the slice updates of all their chains interleaved in
+ * the same launch), and retires the analyses that reached their stopping rule
+ * (their evidence, error and samples are kept on the host; their device memory
+ * is released). Analyses on grids of more than 32768 bins run ONE iteration per
+ * tick on the server's stream; those on smaller grids run on a second stream of
+ * the server's own (the device's highest priority), one iteration and then
+ * more while the long grids' iteration is still running, so that they do not
+ * wait every iteration for the slowest analysis. Every analysis keeps its own
  * live set, Philox key and iteration counter on the device, so its result does
  * not depend on which other analyses share the GPU. Not thread-safe. */
 typedef struct ns_server ns_server;
@@ -391,7 +395,7 @@ int ns_server_create(ns_server **out, const ns_server_options *opts);
 /* Copies the request's host inputs; *id identifies it. Validation errors are
  * returned here (INVALID_ARG, PSD_NONPOS, K_RANGE). */
 int ns_submit(ns_server *srv, const ns_request *req, uint64_t *id);
-/* Admit, iterate every running analysis once, retire finished ones.
+/* Admit, iterate the running analyses (see above), retire finished ones.
  * n_running / n_pending (may be NULL) report the queue after the tick. */
 int ns_server_tick(ns_server *srv, int *n_running, int *n_pending);
 int ns_poll(ns_server *srv, uint64_t id, ns_request_status *st);

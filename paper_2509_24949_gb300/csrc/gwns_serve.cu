@@ -2,12 +2,20 @@
 // on one GPU (ns_server_* in include/gwns.h).
 //
 // Each admitted analysis is an ordinary context (its own tables, live set,
-// dead list and run state on the device). A tick runs one iteration of every
-// running analysis with one launch per iteration kernel: the per-analysis
-// kernels (sort, evidence, covariance, stopping test) take one block per
-// analysis, and the slice update takes one block per (analysis, chain) of all
-// running analyses, grouped by detector count. Descriptors (model, tables,
-// iteration arguments) of the running analyses live in a device array.
+// dead list and run state on the device). An iteration of a set of analyses
+// takes one launch per iteration kernel: the per-analysis kernels (sort,
+// evidence, covariance, stopping test) take one block per analysis, and the
+// slice update takes one block per (analysis, chain) of all of them, grouped by
+// detector count. Descriptors (model, tables, iteration arguments) live in a
+// device array.
+//
+// Two lanes: analyses on grids of more than SHORT_LANE_BINS bins run on the
+// server's stream, those on smaller grids on a second, higher-priority stream.
+// A tick launches one iteration of the long lane and, while it runs, iterates
+// the short lane again and again (each time after the previous one finished),
+// so that a short analysis does not wait every iteration for the slowest long
+// one. Each analysis' arithmetic is its own, so its result does not depend on
+// the lanes.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -68,20 +76,29 @@ size_t footprint(const Request &r) { return footprint_base(r) + dead_bytes(r, 64
 
 }  // namespace
 
-struct ns_server {
-    ns_server_options o;
+// Grids of up to this many bins run on the short lane (the 4-, 8- and 16-s
+// analyses of a 20-2048 Hz stream; 32- and 64-s ones on the long lane).
+constexpr int SHORT_LANE_BINS = 32768;
+
+struct Lane {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    Desc *d_desc = nullptr;
+    int desc_cap = 0;
+    int2 *d_map = nullptr;
+    int map_cap = 0;
+};
+
+struct ns_server {
+    ns_server_options o;
+    cudaStream_t stream = nullptr;   // the long lane's (lane[0].stream)
     uint64_t next_id = 1;
     size_t budget = 0, used = 0;
     long long chains = 0;          // k of the running analyses
     std::deque<uint64_t> pending;
     std::vector<uint64_t> running;
     std::unordered_map<uint64_t, Request> reqs;
-    Desc *d_desc = nullptr;
-    int desc_cap = 0;
-    int2 *d_map = nullptr;
-    int map_cap = 0;
+    Lane lane[2];                  // 0: long grids, 1: short grids
     std::chrono::steady_clock::time_point t0;
 };
 
@@ -126,7 +143,7 @@ int admit(ns_server *s, Request &r) {
     ns_options o = r.opts;
     o.precision = s->o.precision;
     o.slots = s->o.slots;
-    o.stream = (void *)s->stream;
+    o.stream = (void *)s->lane[r.N <= SHORT_LANE_BINS ? 1 : 0].stream;
     ns_ctx *c = nullptr;
     int rc = ns_init(&c, &r.prior, &data, &psd, &grid, &o);
     if (rc) return rc;
@@ -170,10 +187,12 @@ int retire(ns_server *s, Request &r) {
     return NS_OK;
 }
 
-// One iteration of every running analysis, interleaved.
-int iterate_all(ns_server *s) {
-    const int na = (int)s->running.size();
+// One iteration of the analyses ids, interleaved, launched on lane L's stream
+// (not waited for). Their run states are copied to the host at its end.
+int iterate_lane(ns_server *s, int L, const std::vector<uint64_t> &ids) {
+    const int na = (int)ids.size();
     if (na == 0) return NS_OK;
+    Lane &ln = s->lane[L];
     std::vector<Desc> desc(na);
     // slice-update launches grouped by (detector count, warps per chain): every
     // analysis always runs at its own width, whatever the mix. Tiled mixed grids
@@ -182,7 +201,7 @@ int iterate_all(ns_server *s) {
     // in a kernel of its own, 5.8 / 9.2 s, and 6.3 / 10.0 s on a second stream)
     std::map<std::pair<int, int>, std::vector<int2>> groups;
     for (int a = 0; a < na; a++) {
-        Request &r = s->reqs[s->running[a]];
+        Request &r = s->reqs[ids[a]];
         ns_ctx *c = r.ctx;
         const int k = c->k_default;
         const long long cap0 = c->dead_cap;
@@ -204,37 +223,74 @@ int iterate_all(ns_server *s) {
         std::vector<int2> &g = groups[std::make_pair(c->M.n_det, slots_alloc(c))];
         for (int ch = 0; ch < k; ch++) g.push_back(make_int2(a, ch));
     }
-    if (na > s->desc_cap) {
-        cudaFree(s->d_desc);
-        s->d_desc = nullptr;
-        SCK(cudaMalloc((void **)&s->d_desc, sizeof(Desc) * (size_t)na * 2));
-        s->desc_cap = na * 2;
+    if (na > ln.desc_cap) {
+        cudaFree(ln.d_desc);
+        ln.d_desc = nullptr;
+        SCK(cudaMalloc((void **)&ln.d_desc, sizeof(Desc) * (size_t)na * 2));
+        ln.desc_cap = na * 2;
     }
     size_t nmap = 0;
     for (auto &kv : groups) nmap += kv.second.size();
-    if ((int)nmap > s->map_cap) {
-        cudaFree(s->d_map);
-        s->d_map = nullptr;
-        SCK(cudaMalloc((void **)&s->d_map, sizeof(int2) * nmap * 2));
-        s->map_cap = (int)nmap * 2;
+    if ((int)nmap > ln.map_cap) {
+        cudaFree(ln.d_map);
+        ln.d_map = nullptr;
+        SCK(cudaMalloc((void **)&ln.d_map, sizeof(int2) * nmap * 2));
+        ln.map_cap = (int)nmap * 2;
     }
-    SCK(cudaMemcpyAsync(s->d_desc, desc.data(), sizeof(Desc) * na, cudaMemcpyHostToDevice, s->stream));
-    SCK(gwns::launch_iteration_multi_head(s->d_desc, na, s->stream));
+    // pageable host sources: each copy is staged before the call returns
+    SCK(cudaMemcpyAsync(ln.d_desc, desc.data(), sizeof(Desc) * na, cudaMemcpyHostToDevice, ln.stream));
+    SCK(gwns::launch_iteration_multi_head(ln.d_desc, na, ln.stream));
     size_t off = 0;
     for (auto &kv : groups) {
         const std::vector<int2> &g = kv.second;
-        SCK(cudaMemcpyAsync(s->d_map + off, g.data(), sizeof(int2) * g.size(), cudaMemcpyHostToDevice, s->stream));
-        SCK(gwns::launch_slice_multi(s->d_desc, s->d_map + off, (int)g.size(), s->o.precision, kv.first.first,
-                                     kv.first.second, 0, s->stream));
+        SCK(cudaMemcpyAsync(ln.d_map + off, g.data(), sizeof(int2) * g.size(), cudaMemcpyHostToDevice, ln.stream));
+        SCK(gwns::launch_slice_multi(ln.d_desc, ln.d_map + off, (int)g.size(), s->o.precision, kv.first.first,
+                                     kv.first.second, 0, ln.stream));
         off += g.size();
     }
-    SCK(gwns::launch_iteration_multi_tail(s->d_desc, na, s->stream));
+    SCK(gwns::launch_iteration_multi_tail(ln.d_desc, na, ln.stream));
     for (int a = 0; a < na; a++) {
-        ns_ctx *c = s->reqs[s->running[a]].ctx;
+        ns_ctx *c = s->reqs[ids[a]].ctx;
         c->n_dead += c->k_default;
-        SCK(cudaMemcpyAsync(c->h_state, c->state, sizeof(RunState), cudaMemcpyDeviceToHost, s->stream));
+        SCK(cudaMemcpyAsync(c->h_state, c->state, sizeof(RunState), cudaMemcpyDeviceToHost, ln.stream));
     }
-    SCK(cudaStreamSynchronize(s->stream));
+    return NS_OK;
+}
+
+bool finished(const ns_server *s, const Request &r) {
+    const RunState &st = *r.ctx->h_state;
+    return st.done || st.iter >= s->o.max_iter;
+}
+
+// One tick's iterations: the long lane once; the short lane once, then again
+// while the long lane's iteration is still running.
+int iterate_all(ns_server *s) {
+    std::vector<uint64_t> ids[2];
+    for (uint64_t id : s->running) ids[s->reqs[id].N <= SHORT_LANE_BINS ? 1 : 0].push_back(id);
+    int rc = iterate_lane(s, 0, ids[0]);
+    if (rc) return rc;
+    cudaEvent_t ev = nullptr;
+    if (!ids[0].empty() && !ids[1].empty()) {
+        SCK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        if (cudaEventRecord(ev, s->lane[0].stream) != cudaSuccess) {
+            cudaEventDestroy(ev);
+            return NS_ERR_CUDA;
+        }
+    }
+    std::vector<uint64_t> act = ids[1];
+    while (!act.empty()) {
+        if ((rc = iterate_lane(s, 1, act))) break;
+        if (cudaStreamSynchronize(s->lane[1].stream) != cudaSuccess) { rc = NS_ERR_CUDA; break; }
+        std::vector<uint64_t> next;
+        for (uint64_t id : act)
+            if (!finished(s, s->reqs[id])) next.push_back(id);
+        act.swap(next);
+        // another round only while the long lane is still busy
+        if (!ev || cudaEventQuery(ev) != cudaErrorNotReady) break;
+    }
+    if (ev) cudaEventDestroy(ev);
+    if (rc) return rc;
+    SCK(cudaStreamSynchronize(s->lane[0].stream));
     return NS_OK;
 }
 
@@ -261,11 +317,24 @@ int ns_server_create(ns_server **out, const ns_server_options *o) {
         s->o.max_chains = 20 * nsm;
     }
     if (o->stream) {
-        s->stream = (cudaStream_t)o->stream;
+        s->lane[0].stream = (cudaStream_t)o->stream;
     } else {
-        if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) { delete s; return NS_ERR_CUDA; }
-        s->own_stream = true;
+        if (cudaStreamCreateWithFlags(&s->lane[0].stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete s;
+            return NS_ERR_CUDA;
+        }
+        s->lane[0].own_stream = true;
     }
+    s->stream = s->lane[0].stream;
+    // the short lane's stream: the device's highest priority, so that its blocks
+    // are scheduled first as the long lane's blocks retire
+    int lo_pri = 0, hi_pri = 0;
+    if (cudaDeviceGetStreamPriorityRange(&lo_pri, &hi_pri) != cudaSuccess) hi_pri = 0;
+    if (cudaStreamCreateWithPriority(&s->lane[1].stream, cudaStreamNonBlocking, hi_pri) != cudaSuccess) {
+        ns_server_free(s);
+        return NS_ERR_CUDA;
+    }
+    s->lane[1].own_stream = true;
     if (o->mem_budget) {
         s->budget = o->mem_budget;
     } else {
@@ -353,8 +422,7 @@ int ns_server_tick(ns_server *s, int *n_running, int *n_pending) {
     std::vector<uint64_t> keep;
     for (uint64_t id : s->running) {
         Request &r = s->reqs[id];
-        const RunState &st = *r.ctx->h_state;
-        if (st.done || st.iter >= s->o.max_iter) {
+        if (finished(s, r)) {
             if ((rc = retire(s, r))) return rc;
         } else {
             keep.push_back(id);
@@ -403,7 +471,8 @@ int ns_cancel(ns_server *s, uint64_t id) {
     if (r.st.state == NS_REQ_PENDING) {
         s->pending.erase(std::remove(s->pending.begin(), s->pending.end(), id), s->pending.end());
     } else if (r.st.state == NS_REQ_RUNNING) {
-        cudaStreamSynchronize(s->stream);
+        for (Lane &ln : s->lane)
+            if (ln.stream) cudaStreamSynchronize(ln.stream);
         release(s, r);
         s->running.erase(std::remove(s->running.begin(), s->running.end(), id), s->running.end());
     } else {
@@ -416,11 +485,14 @@ int ns_cancel(ns_server *s, uint64_t id) {
 
 void ns_server_free(ns_server *s) {
     if (!s) return;
-    if (s->stream) cudaStreamSynchronize(s->stream);
+    for (Lane &ln : s->lane)
+        if (ln.stream) cudaStreamSynchronize(ln.stream);
     for (auto &kv : s->reqs) release(s, kv.second);
-    if (s->d_desc) cudaFree(s->d_desc);
-    if (s->d_map) cudaFree(s->d_map);
-    if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+    for (Lane &ln : s->lane) {
+        if (ln.d_desc) cudaFree(ln.d_desc);
+        if (ln.d_map) cudaFree(ln.d_map);
+        if (ln.own_stream && ln.stream) cudaStreamDestroy(ln.stream);
+    }
     delete s;
 }
 

@@ -80,6 +80,38 @@ def test_tiled_forms_share_a_server(gw):
         assert np.array_equal(m["logl"], a["logl"])
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_short_and_long_lanes(gw, precision):
+    """A long grid (40,000 bins, the server's stream) and two short ones (the
+    short lane, iterated again while the long grid's iteration runs) in one
+    server: every analysis ends, with the result it has alone and the number of
+    iterations it has alone."""
+    reqs = [_analysis(60, N=40000, df=1 / 32, n_live=60), _analysis(61, N=1200, n_live=60),
+            _analysis(62, N=2000, n_live=80)]
+    alone = []
+    for r, dim in reqs:
+        with gw.Server(precision=precision, slots=2) as srv:
+            rid = srv.submit(**r)
+            srv.run_until_idle()
+            alone.append((srv.result(rid, dim), srv.poll(rid)["iterations"]))
+    with gw.Server(precision=precision, slots=2) as srv:
+        ids = [srv.submit(**r) for r, _ in reqs]
+        ticks = 0
+        while True:
+            n, p = srv.tick()
+            ticks += 1
+            if n == 0 and p == 0:
+                break
+        mixed = [(srv.result(i, dim), srv.poll(i)) for i, (_, dim) in zip(ids, reqs)]
+    for (a, it), (m, st) in zip(alone, mixed):
+        assert st["state"] == gw.NS_REQ_DONE
+        assert st["iterations"] == it
+        assert m["logZ"] == a["logZ"] and m["dlogZ"] == a["dlogZ"]
+        assert np.array_equal(m["u"], a["u"]) and np.array_equal(m["logl"], a["logl"])
+    # the server ran no more ticks than its longest analysis needs iterations
+    assert ticks <= max(it for _, it in alone) + 1
+
+
 def test_server_equals_single_context(gw):
     args, dim = _analysis(7)
     with gw.Server(precision=0, slots=2) as srv:
