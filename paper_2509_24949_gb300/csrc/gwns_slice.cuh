@@ -7,6 +7,49 @@
 
 namespace gwns {
 
+// The warp sums of one candidate's double-float sums zh/zl[d][re, im] by the
+// transposing butterfly (warp_sum_df_many; lanes 2v hold value v = 2 d + re/im),
+// written as doubles to out[v] (2 NDET entries).
+template <int NDET>
+__device__ __forceinline__ void warp_sums_df_to(const float (&zh)[NDET][2], const float (&zl)[NDET][2],
+                                                double *out) {
+    const int lane = threadIdx.x & 31;
+    float vh[16], vl[16];
+#pragma unroll
+    for (int d = 0; d < NDET; d++)
+#pragma unroll
+        for (int ri = 0; ri < 2; ri++) { vh[2 * d + ri] = zh[d][ri]; vl[2 * d + ri] = zl[d][ri]; }
+    float rh, rl;
+    warp_sum_df_many<2 * NDET>(vh, vl, rh, rl);
+    const int v = lane >> 1;
+    if ((lane & 1) == 0 && v < 2 * NDET) out[v] = (double)rh + (double)rl;
+}
+
+// The same sums combined with G_d: returns sum_d (Re G_d Re Z_d - gim_d Im Z_d)
+// on lane 0 (the detector terms of log L), from the transposed warp sums: the
+// lane holding value v multiplies it by its factor, then lanes 0, 2, .., 14 add.
+template <int NDET>
+__device__ __forceinline__ double warp_detector_terms_df(const float (&zh)[NDET][2], const float (&zl)[NDET][2],
+                                                         const Coef &c) {
+    const int lane = threadIdx.x & 31;
+    float vh[16], vl[16];
+#pragma unroll
+    for (int d = 0; d < NDET; d++)
+#pragma unroll
+        for (int ri = 0; ri < 2; ri++) { vh[2 * d + ri] = zh[d][ri]; vl[2 * d + ri] = zl[d][ri]; }
+    float rh, rl;
+    warp_sum_df_many<2 * NDET>(vh, vl, rh, rl);
+    const int v = lane >> 1, dd = v >> 1;
+    double t = 0.0;
+    if ((lane & 1) == 0 && v < 2 * NDET) {
+        const double z = (double)rh + (double)rl;
+        t = (v & 1) ? -c.gim[dd] * z : c.gre[dd] * z;
+    }
+#pragma unroll
+    for (int o = 2; o < 16; o <<= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    return t;
+}
+
 // Coefficients of one point from warp 0 (shared), then all warps run the bin
 // loop and the CTA reduces Z_d. Returns log L in *lval (shared) after the
 // second barrier; every thread of the CTA must call it.
@@ -29,25 +72,13 @@ __device__ __forceinline__ void cta_loglike_bins(const Model &M, const Tables &T
             tile_bins<NDET, 1, true, true, true>(T, M.tlg, M.np, &cm, &coef.jcut, 1, warp, W, zh, zl);
         else
             tile_bins<NDET, 1, false>(T, M.tlg, M.np, &cm, &coef.jcut, 1, warp, W, zh, zl);
-#pragma unroll
-        for (int d = 0; d < NDET; d++) {
-            warp_sum_df(zh[0][d][0], zl[0][d][0]);
-            warp_sum_df(zh[0][d][1], zl[0][d][1]);
-            zr[d] = (double)zh[0][d][0] + (double)zl[0][d][0];
-            zi[d] = (double)zh[0][d][1] + (double)zl[0][d][1];
-        }
+        warp_sums_df_to<NDET>(zh[0], zl[0], red[warp]);
     } else {
         float zh[NDET][2], zl[NDET][2];
         bins_mixed<NDET>(T, M.N, cm, coef.jcut, threadIdx.x, W * 32, zh, zl);
-#pragma unroll
-        for (int d = 0; d < NDET; d++) {
-            warp_sum_df(zh[d][0], zl[d][0]);
-            warp_sum_df(zh[d][1], zl[d][1]);
-            zr[d] = (double)zh[d][0] + (double)zl[d][0];
-            zi[d] = (double)zh[d][1] + (double)zl[d][1];
-        }
+        warp_sums_df_to<NDET>(zh, zl, red[warp]);
     }
-    if (lane == 0) {
+    if (PREC == 0 && lane == 0) {
 #pragma unroll
         for (int d = 0; d < NDET; d++) { red[warp][2 * d] = zr[d]; red[warp][2 * d + 1] = zi[d]; }
     }
@@ -205,39 +236,19 @@ __global__ void __launch_bounds__(W * 32) k_eval_batch(Model M, Tables T, const 
     __syncthreads();
     unsigned long long n_pts = 0, n_pb = 0;     // this warp's counts, added once at the end
     for (int p = warp; p < np; p += W) {
-        double ZR[1] = {0.0}, ZI[1] = {0.0};      // lane d < NDET: detector d's sums
+        double t;       // on lane 0: sum over detectors of Re(G_d Z_d)
         if (M.tlg) {
             float zh[1][NDET][2], zl[1][NDET][2];
             if (M.tlg >= 5)
                 tile_bins<NDET, 1, true, true>(T, M.tlg, M.np, &cm[p], &coef[p].jcut, 1, 0, 1, zh, zl);
             else
                 tile_bins<NDET, 1, false>(T, M.tlg, M.np, &cm[p], &coef[p].jcut, 1, 0, 1, zh, zl);
-#pragma unroll
-            for (int dd = 0; dd < NDET; dd++) {
-                warp_sum_df(zh[0][dd][0], zl[0][dd][0]);
-                warp_sum_df(zh[0][dd][1], zl[0][dd][1]);
-                if (lane == dd) {
-                    ZR[0] = (double)zh[0][dd][0] + (double)zl[0][dd][0];
-                    ZI[0] = (double)zh[0][dd][1] + (double)zl[0][dd][1];
-                }
-            }
+            t = warp_detector_terms_df<NDET>(zh[0], zl[0], coef[p]);
         } else {
             float zh[NDET][2], zl[NDET][2];
             bins_mixed<NDET>(T, M.N, cm[p], coef[p].jcut, lane, 32, zh, zl);
-#pragma unroll
-            for (int dd = 0; dd < NDET; dd++) {
-                warp_sum_df(zh[dd][0], zl[dd][0]);
-                warp_sum_df(zh[dd][1], zl[dd][1]);
-                if (lane == dd) {
-                    ZR[0] = (double)zh[dd][0] + (double)zl[dd][0];
-                    ZI[0] = (double)zh[dd][1] + (double)zl[dd][1];
-                }
-            }
+            t = warp_detector_terms_df<NDET>(zh, zl, coef[p]);
         }
-        // lane d < NDET: detector d's term, summed over the detector lanes
-        double t = 0.0;
-        if (lane < NDET) t = coef[p].gre[lane] * ZR[0] - coef[p].gim[lane] * ZI[0];
-        t = group_sum_down<NDET>(t);
         if (lane == 0) {
             const double v = t - 0.5 * coef[p].hh;
             logl[i0 + p] = v;
@@ -970,17 +981,23 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
                     const int g0 = ((warp - off) % W + W) % W;
                     off += ng;
                     tile_bins_form<NDET, 2, FORM>(M, T, cm + c0, jc + c0, nc, g0, W, zh, zl);
+                    // the pair's 4 NDET sums at once (transposing butterfly): lane 2v
+                    // holds value v = (2 (candidate NDET + detector) + re/im)
+                    float vh[16], vl[16];
 #pragma unroll
                     for (int sc = 0; sc < 2; sc++)
 #pragma unroll
-                        for (int dd = 0; dd < NDET; dd++) {
-                            warp_sum_df(zh[sc][dd][0], zl[sc][dd][0]);
-                            warp_sum_df(zh[sc][dd][1], zl[sc][dd][1]);
-                            if (lane == 0 && c0 + sc < S) {
-                                part[warp][c0 + sc][dd][0] = (double)zh[sc][dd][0] + (double)zl[sc][dd][0];
-                                part[warp][c0 + sc][dd][1] = (double)zh[sc][dd][1] + (double)zl[sc][dd][1];
+                        for (int dd = 0; dd < NDET; dd++)
+#pragma unroll
+                            for (int ri = 0; ri < 2; ri++) {
+                                vh[(sc * NDET + dd) * 2 + ri] = zh[sc][dd][ri];
+                                vl[(sc * NDET + dd) * 2 + ri] = zl[sc][dd][ri];
                             }
-                        }
+                    float rh, rl;
+                    warp_sum_df_many<4 * NDET>(vh, vl, rh, rl);
+                    const int v = lane >> 1, q = v >> 1, sc = q / NDET, dd = q - sc * NDET;
+                    if ((lane & 1) == 0 && v < 4 * NDET && c0 + sc < S)
+                        part[warp][c0 + sc][dd][v & 1] = (double)rh + (double)rl;
                 }
             } else {
                 float zrh[S][NDET], zrl[S][NDET], zih[S][NDET], zil[S][NDET];
@@ -1059,27 +1076,13 @@ __device__ void slice_body(const Model &M, const Tables &T, const StepArgs &A, c
                 __syncwarp();
                 float zh[1][NDET][2], zl[1][NDET][2];
                 tile_bins_form<NDET, 1, FORM>(M, T, &cm[warp], &jc[warp], 1, 0, 1, zh, zl);
-#pragma unroll
-                for (int dd = 0; dd < NDET; dd++) {
-                    warp_sum_df(zh[0][dd][0], zl[0][dd][0]);
-                    warp_sum_df(zh[0][dd][1], zl[0][dd][1]);
-                    const double ZR = (double)zh[0][dd][0] + (double)zl[0][dd][0];
-                    const double ZI = (double)zh[0][dd][1] + (double)zl[0][dd][1];
-                    v += coef[warp].gre[dd] * ZR - coef[warp].gim[dd] * ZI;
-                }
+                v = warp_detector_terms_df<NDET>(zh[0], zl[0], coef[warp]);
             } else {
                 if (!M.cdf) coef_to_mixed_warp(coef[warp], M.n_det, M.df, &cm[warp], nullptr, form_rot<FORM>(M));
                 __syncwarp();
                 float zh[NDET][2], zl[NDET][2];
                 bins_mixed<NDET>(T, M.N, cm[warp], coef[warp].jcut, lane, 32, zh, zl);
-#pragma unroll
-                for (int dd = 0; dd < NDET; dd++) {
-                    warp_sum_df(zh[dd][0], zl[dd][0]);
-                    warp_sum_df(zh[dd][1], zl[dd][1]);
-                    const double ZR = (double)zh[dd][0] + (double)zl[dd][0];
-                    const double ZI = (double)zh[dd][1] + (double)zl[dd][1];
-                    v += coef[warp].gre[dd] * ZR - coef[warp].gim[dd] * ZI;
-                }
+                v = warp_detector_terms_df<NDET>(zh, zl, coef[warp]);
             }
             if (lane == 0) lval[warp] = (M.model == M_TOY) ? coef[warp].toy : v - 0.5 * coef[warp].hh;
         }
