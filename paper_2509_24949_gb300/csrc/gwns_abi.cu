@@ -378,16 +378,6 @@ static int validate(const ns_prior *prior, const ns_data *data, const ns_psd *ps
     return NS_OK;
 }
 
-// Mixed form: the tiled form when the Taylor remainder of the basis about each
-// tile's centre stays below 1e-8 rad for every point of the prior, else the
-// per-bin form. The bound: the basis terms of the phase sum to at most twice
-// the Newtonian phase 3/128 (pi T_sun Mc f)^(-5/3) at the lowest chirp mass and
-// frequency (leading-order and 1.5PN terms dominate at f0); the degree-TK
-// remainder of f^(-5/3) over half a tile h is below 4.8 (h/f0)^(TK+1) times the
-// term (TK = 7); a factor 64 covers both with margin. The longest tile that
-// passes, up to 128 bins, is taken: it amortises the per-tile anchor best
-// (GB300, 519,169 bins: degree 6 on 64-bin tiles against degree 7 on 128-bin
-// tiles, batched likelihood 1.53 -> 1.59 M evals/s, slice update 326 -> 304 ms).
 // A double as a double-float: the nearest float, then the nearest float to the rest.
 static gwns::dfl host_df(double x) {
     const float h = (float)x;
@@ -411,6 +401,16 @@ static bool use_df_coefficients(const ns_ctx *c) {
     return !(f && f[0] == '1');
 }
 
+// Mixed form: the tiled form when the Taylor remainder of the basis about each
+// tile's centre stays below 1e-8 rad for every point of the prior, else the
+// per-bin form. The bound: the basis terms of the phase sum to at most twice
+// the Newtonian phase 3/128 (pi T_sun Mc f)^(-5/3) at the lowest chirp mass and
+// frequency (leading-order and 1.5PN terms dominate at f0); the degree-TK
+// remainder of f^(-5/3) over half a tile h is below 4.8 (h/f0)^(TK+1) times the
+// term (TK = 7); a factor 64 covers both with margin. The longest tile that
+// passes, up to 128 bins, is taken: it amortises the per-tile anchor best
+// (GB300, 519,169 bins: degree 6 on 64-bin tiles against degree 7 on 128-bin
+// tiles, batched likelihood 1.53 -> 1.59 M evals/s, slice update 326 -> 304 ms).
 static void choose_tiles(Model &M) {
     M.tlg = 0;
     M.np = M.N;
